@@ -1,0 +1,137 @@
+"""Energy and species balance by finite differences (Section 2.3): explicit Euler in time,
+third-order WENO for advection, centred second-order diffusion; two-step (or one-step)
+Arrhenius chemistry; thickened flame (Section 1 and 3.2.2, factor written E in the paper).
+
+Equations, lattice units of length and time (see ``units``), for phi in {T, Y_k}:
+    phi^{n+1} = phi^n - A_phi + N_phi
+    A_phi = sum_axes u_a(r) (phi_hat(r + e_a/2) - phi_hat(r - e_a/2))      (WENO3 faces)
+    N_phi = (1/rho) sum_axes [G(r+e/2)(phi(r+e) - phi(r)) - G(r-e/2)(phi(r) - phi(r-e))]
+            + chemistry (+ pressure work for T)
+with G_T = F_loc mu / Pr, G_k = F_loc mu / (Pr Le_k) and the face value G = arithmetic mean.
+Readings (the paper gives no formulas for these):
+  * WENO3 (Jiang-Shu): candidate faces -a/2 + 3b/2 and (b + c)/2, smoothness (b - a)^2 and
+    (c - b)^2, ideal weights 1/3 and 2/3, eps = 1e-6 in units of the field scale (T_ref^2 for T,
+    1 for Y); the upwind side is chosen by the sign of the face velocity (u(r) + u(r+e))/2,
+    a zero face velocity counting as positive.
+  * Chemistry: q_j = A_j T^beta_j exp(-E_j/(R T)) prod_k [X_k]^n_jk with [X_k] = rho max(Y_k,0)/W_k,
+    omega_k = W_k sum_j nu_kj q_j, heat release -sum_k h_f,k omega_k, constant c_p.
+  * Thickening (Colin type, efficiency 1): diffusivities times F_loc, rates divided by F_loc.
+    F_loc = F, or with the flame sensor F_loc = 1 + (F - 1) tanh(beta |omega_s| / omega_ref).
+  * Lambda (Eq. 3) uses the non-advective right-hand side: Lambda = N_T / T + sum (W/W_k) N_k.
+  * Thermodynamic pressure: rho = P_th W / (R T); the energy equation gains the pressure work
+    dP_th/(rho c_p) of the previous step.
+"""
+import math
+
+import torch
+
+from .units import R_GAS
+
+
+def weno3(a, b, c, eps):
+    """Face value from upwind-far a, upwind b, downwind c (Jiang-Shu WENO3)."""
+    q0 = -0.5 * a + 1.5 * b
+    q1 = 0.5 * b + 0.5 * c
+    beta0 = (b - a) ** 2
+    beta1 = (c - b) ** 2
+    a0 = (1.0 / 3.0) / (eps + beta0) ** 2
+    a1 = (2.0 / 3.0) / (eps + beta1) ** 2
+    return (a0 * q0 + a1 * q1) / (a0 + a1)
+
+
+def mean_molar_mass(p, Y):
+    return 1.0 / sum(Y[k] / p.W[k] for k in range(p.K))
+
+
+def reaction_rates(p, T, Y, rho_phys):
+    """q_j [mol/(m^3 s)] for every reaction, list of [N] tensors."""
+    out = []
+    for rx in p.reactions:
+        q = rx["A"] * T ** rx["beta"] * torch.exp(-rx["E"] / (R_GAS * T))
+        for k, n in rx["order"].items():
+            conc = rho_phys * torch.clamp(Y[k], min=0.0) / p.W[k]
+            q = q * conc ** n
+        out.append(q)
+    return out
+
+
+def species_rates(p, q):
+    """omega_k [kg/(m^3 s)] from reaction rates."""
+    om = []
+    for k in range(p.K):
+        acc = torch.zeros_like(q[0]) if q else torch.zeros(())
+        for j, rx in enumerate(p.reactions):
+            nu = rx["nu"].get(k, 0.0)
+            if nu != 0.0:
+                acc = acc + p.W[k] * nu * q[j]
+        om.append(acc)
+    return om
+
+
+def thickening(p, omega):
+    """F_loc per cell."""
+    if not p.sensor:
+        return torch.full_like(omega[0], p.F)
+    phi = torch.tanh(p.sensor_beta * omega[p.sensor_species].abs() / p.sensor_wref)
+    return 1.0 + (p.F - 1.0) * phi
+
+
+def fd_update(p, grid, nb, T, Y, u, uin_r, P_th, dP_lag):
+    """One explicit Euler step of T and Y. Returns (T1, Y1, rho_lat, lam_fd)."""
+    W = mean_molar_mass(p, Y)
+    rho_phys = P_th * W / (R_GAS * T)
+    rho = rho_phys / p.rho_ref
+    q = reaction_rates(p, T, Y, rho_phys)
+    om = [o.expand_as(T) for o in species_rates(p, q)]
+    Floc = thickening(p, om)
+    mu = p.nu_lat * (T / p.T_ref) ** p.mu_exp
+
+    fields = [T] + [Y[k] for k in range(p.K)]
+    inlet_vals = [p.T_in] + p.Y_in
+    Les = [1.0] + p.Le
+    epss = [p.weno_eps_T] + [p.weno_eps_Y] * p.K
+    N_out = []
+    A_out = []
+    for f, (phi, phin, Le, eps) in enumerate(zip(fields, inlet_vals, Les, epss)):
+        G = Floc * mu / (p.Pr * Le)
+        adv = torch.zeros_like(phi)
+        dif = torch.zeros_like(phi)
+        for a in range(grid.dim):
+            pm2 = nb.value(phi, phin, a, -1, 2)
+            pm1 = nb.value(phi, phin, a, -1, 1)
+            pp1 = nb.value(phi, phin, a, +1, 1)
+            pp2 = nb.value(phi, phin, a, +1, 2)
+            um = nb.velocity(u[a], uin_r[a], a, -1)
+            up = nb.velocity(u[a], uin_r[a], a, +1)
+            uf_p = 0.5 * (u[a] + up)
+            uf_m = 0.5 * (um + u[a])
+            face_p = torch.where(uf_p >= 0, weno3(pm1, phi, pp1, eps), weno3(pp2, pp1, phi, eps))
+            face_m = torch.where(uf_m >= 0, weno3(pm2, pm1, phi, eps), weno3(pp1, phi, pm1, eps))
+            adv = adv + u[a] * (face_p - face_m)
+            # ghost diffusion coefficients: temperature of the ghost, F_loc of the fluid cell
+            Tm = nb.value(T, p.T_in, a, -1, 1)
+            Tp = nb.value(T, p.T_in, a, +1, 1)
+            km, im = nb.kind1(a, -1), nb.index1(a, -1)
+            kp, ip = nb.kind1(a, +1), nb.index1(a, +1)
+            Fm = torch.where(km == 0, Floc[im], Floc)
+            Fp = torch.where(kp == 0, Floc[ip], Floc)
+            Gm = Fm * p.nu_lat * (Tm / p.T_ref) ** p.mu_exp / (p.Pr * Le)
+            Gp = Fp * p.nu_lat * (Tp / p.T_ref) ** p.mu_exp / (p.Pr * Le)
+            dif = dif + 0.5 * (G + Gp) * (pp1 - phi) - 0.5 * (G + Gm) * (phi - pm1)
+        dif = dif / rho
+        if f == 0:
+            qdot = -sum(p.hf[k] * om[k] for k in range(p.K)) if p.K else torch.zeros_like(T)
+            src = p.dt * qdot / (rho_phys * p.cp * Floc) + dP_lag / (rho_phys * p.cp)
+        else:
+            src = p.dt * om[f - 1] / (rho_phys * Floc) if p.reactions else torch.zeros_like(phi)
+        N_out.append(dif + src)
+        A_out.append(adv)
+    T1 = T - A_out[0] + N_out[0]
+    Y1 = torch.stack([Y[k] - A_out[k + 1] + N_out[k + 1] for k in range(p.K)])
+    lam = N_out[0] / T + sum((W / p.W[k]) * N_out[k + 1] for k in range(p.K))
+    return T1, Y1, rho, lam
+
+
+def pth_integrand(p, T, Y):
+    """W / (R T rho_ref): thermodynamic-pressure integrand per fluid cell (cell volume 1)."""
+    return mean_molar_mass(p, Y) / (R_GAS * T * p.rho_ref)

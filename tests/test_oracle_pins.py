@@ -1,0 +1,404 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics (closed forms,
+invariants, special cases, hand-derived fixtures), so that a dropped term, a wrong sign or a
+transposed index anywhere in the oracle fails one of them. CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import fd as fdm
+from oracle import geometry as geo
+from oracle import lb
+from oracle.cumulant import CumulantSpace
+from oracle.lattice import CS2, Lattice
+from oracle.step import Oracle
+from oracle.units import Params
+
+f64 = torch.float64
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------------------- lattice
+@pytest.mark.parametrize("dim", [2, 3])
+def test_lattice_quadrature(dim):
+    """Section 2.1: third-order quadrature with c_s^2 = 1/3 (isotropy up to fourth order)."""
+    L = Lattice(dim)
+    c, w = L.c, L.w
+    assert abs(w.sum().item() - 1) < 1e-15
+    for a in range(dim):
+        assert abs((w * c[:, a]).sum().item()) < 1e-15
+        for b in range(dim):
+            m2 = (w * c[:, a] * c[:, b]).sum().item()
+            assert abs(m2 - (CS2 if a == b else 0.0)) < 1e-15
+            for g in range(dim):
+                assert abs((w * c[:, a] * c[:, b] * c[:, g]).sum().item()) < 1e-15
+                for d in range(dim):
+                    m4 = (w * c[:, a] * c[:, b] * c[:, g] * c[:, d]).sum().item()
+                    iso = CS2 ** 2 * ((a == b) * (g == d) + (a == g) * (b == d) + (a == d) * (b == g))
+                    assert abs(m4 - iso) < 1e-15
+    assert torch.equal(L.c[L.opp], -L.c)
+
+
+# ------------------------------------------------------------------------------ cumulants
+@pytest.mark.parametrize("dim", [2, 3])
+def test_cumulant_round_trip(dim):
+    L = Lattice(dim)
+    cs = CumulantSpace(L)
+    g = torch.Generator().manual_seed(0)
+    h = L.w[:, None] * (1 + 0.2 * torch.randn(L.Q, 50, generator=g, dtype=f64))
+    u = 0.1 * torch.randn(dim, 50, generator=g, dtype=f64)
+    back = cs.populations_from_central(cs.central_from_cumulants(cs.cumulants_from_central(cs.central_moments(h, u))), u)
+    assert (back - h).abs().max().item() < 1e-14
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_cumulants_vanish_for_independent_axes(dim):
+    """Defining property of joint cumulants: for a product distribution (independent axes) every
+    cumulant mixing two or more axes is zero, and single-axis cumulants are the 1-D ones."""
+    L = Lattice(dim)
+    cs = CumulantSpace(L)
+    rng = np.random.default_rng(1)
+    p = [rng.uniform(0.2, 1.0, 3) for _ in range(dim)]
+    p = [v / v.sum() for v in p]
+    mean = [float(v @ np.array([-1.0, 0.0, 1.0])) for v in p]
+    var = [float(v @ (np.array([-1.0, 0.0, 1.0]) - m) ** 2) for v, m in zip(p, mean)]
+    h = torch.ones(L.Q, 1, dtype=f64)
+    for i in range(L.Q):
+        for a in range(dim):
+            h[i] *= p[a][int(L.ci[i, a]) + 1]
+    u = torch.tensor(mean, dtype=f64)[:, None]
+    C = cs.cumulants_from_central(cs.central_moments(h, u))[:, 0]
+    for j, a in enumerate(cs.idx):
+        if sum(1 for x in a if x) >= 2:
+            assert abs(C[j].item()) < 1e-15, (a, C[j].item())
+        elif sum(a) == 2:
+            assert abs(C[j].item() - var[a.index(2)]) < 1e-15
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_full_relaxation_gives_product_equilibrium(dim):
+    """With every rate 1 the cumulant collision returns the factorised equilibrium
+    prod_a phi(c_a, u_a), phi(-1) = (1/3 + u^2 - u)/2, phi(0) = 2/3 - u^2, phi(1) = (1/3 + u^2 + u)/2."""
+    L = Lattice(dim)
+    cs = CumulantSpace(L)
+    g = torch.Generator().manual_seed(2)
+    h = L.w[:, None] * (1 + 0.3 * torch.randn(L.Q, 20, generator=g, dtype=f64))
+    h = h / h.sum(0, keepdim=True)
+    u = (L.c.T @ h)  # first moment of the normalised distribution
+    C = cs.cumulants_from_central(cs.central_moments(h, u))
+    Cs = lb.relax_cumulants(cs, C, torch.ones(20, dtype=f64), 1.0, [1.0] * 4)
+    hs = cs.populations_from_central(cs.central_from_cumulants(Cs), u)
+    expect = torch.ones_like(h)
+    for i in range(L.Q):
+        for a in range(dim):
+            ua = u[a]
+            c = int(L.ci[i, a])
+            expect[i] *= {-1: (1 / 3 + ua * ua - ua) / 2, 0: 2 / 3 - ua * ua, 1: (1 / 3 + ua * ua + ua) / 2}[c]
+    assert (hs - expect).abs().max().item() < 1e-14
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("coll", ["bgk", "cumulant"])
+def test_collision_conserves_mass_and_momentum(dim, coll):
+    L = Lattice(dim)
+    cs = CumulantSpace(L)
+    g = torch.Generator().manual_seed(3)
+    N = 30
+    rho = 0.5 + torch.rand(N, generator=g, dtype=f64)
+    u = 0.05 * torch.randn(dim, N, generator=g, dtype=f64)
+    gg = lb.g_eq(L, 0.01 * torch.randn(N, generator=g, dtype=f64), rho, u) + 1e-3 * torch.randn(L.Q, N, generator=g, dtype=f64)
+    P, u = lb.moments(L, gg, rho, torch.zeros(N, dtype=f64))
+    xi = torch.zeros_like(gg)
+    params = {"smag_cs": 0.17, "collision": coll, "omega_bulk": 1.3, "omega_hi": [1.1, 0.9, 1.2, 1.0]}
+    gs = lb.collide(L, cs, gg, rho, u, xi, torch.full((N,), 0.7, dtype=f64), params)
+    assert (gs.sum(0) - gg.sum(0)).abs().max().item() < 1e-15
+    assert (L.c.T @ gs - L.c.T @ gg).abs().max().item() < 1e-15
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_equilibrium_and_source_moments(dim):
+    """Eq. 6 with Eq. 4: sum g^eq = P_h, sum c g^eq = c_s^2 rho u,
+    sum c c g^eq = c_s^2 P_h I + c_s^2 rho u u. Eq. 2: sum Xi = c_s^2 u.grad rho + rho c_s^2 Lambda,
+    sum c Xi = 0."""
+    L = Lattice(dim)
+    g = torch.Generator().manual_seed(4)
+    N = 10
+    rho = 0.3 + torch.rand(N, generator=g, dtype=f64)
+    P = torch.randn(N, generator=g, dtype=f64)
+    u = 0.1 * torch.randn(dim, N, generator=g, dtype=f64)
+    gr = torch.randn(dim, N, generator=g, dtype=f64)
+    lam = torch.randn(N, generator=g, dtype=f64)
+    ge = lb.g_eq(L, P, rho, u)
+    assert (ge.sum(0) - P).abs().max() < 1e-14
+    assert (L.c.T @ ge - CS2 * rho * u).abs().max() < 1e-15
+    for a in range(dim):
+        for b in range(dim):
+            m = (L.c[:, a, None] * L.c[:, b, None] * ge).sum(0)
+            ref = CS2 * P * (a == b) + CS2 * rho * u[a] * u[b]
+            assert (m - ref).abs().max() < 1e-14
+    xi = lb.source_xi(L, rho, u, gr, lam)
+    assert (xi.sum(0) - (CS2 * (u * gr).sum(0) + rho * CS2 * lam)).abs().max() < 1e-14
+    assert (L.c.T @ xi).abs().max() < 1e-14
+
+
+# ------------------------------------------------------------------------ flows (LB pins)
+def _tgv(coll, n=32, tau=0.8, U0=0.02, dim=2):
+    nu = (tau - 0.5) / 3
+    bc = {"x": ("periodic", "periodic"), "y": ("periodic", "periodic"), "z": ("periodic", "periodic")}
+    nz = 2 if dim == 3 else 1
+    cfg = dict(dim=dim, nx=n, ny=n, nz=nz, bc=bc, dx=1.0, dt=1.0, nu_ref=nu, collision=coll)
+    N = n * n * nz
+    o = Oracle(cfg, torch.zeros(N, dtype=torch.uint8))
+    k = 2 * math.pi / n
+    r = torch.arange(N)
+    x = (r % n).double()
+    y = ((r // n) % n).double()
+    u = torch.zeros(dim, N, dtype=f64)
+    u[0] = U0 * torch.sin(k * x) * torch.cos(k * y)
+    u[1] = -U0 * torch.cos(k * x) * torch.sin(k * y)
+    P = -(U0 ** 2 / 4) * (torch.cos(2 * k * x) + torch.cos(2 * k * y))
+    st = o.run(o.init_state(u=u, P_h=P), 100)
+    E1 = (st["u"] ** 2).sum().item()
+    st = o.run(st, 100)
+    E2 = (st["u"] ** 2).sum().item()
+    return (-math.log(E2 / E1) / 100) / (4 * k * k), nu
+
+
+@pytest.mark.parametrize("coll", ["bgk", "cumulant"])
+def test_taylor_green_decay_2d(coll):
+    """Closed form: kinetic energy decays as exp(-4 nu k^2 t) with nu = (tau - 1/2) c_s^2 (Eq. 12)."""
+    nu_m, nu = _tgv(coll)
+    assert abs(nu_m / nu - 1) < 0.01
+
+
+def test_taylor_green_decay_3d_z_invariant():
+    nu_m, nu = _tgv("cumulant", n=24, dim=3)
+    assert abs(nu_m / nu - 1) < 0.01
+
+
+def _channel_decay_rate(H, coll, tau=0.8):
+    """Periodic-in-x channel with halfway bounce-back walls at y = -1/2 and H - 1/2; the first
+    Stokes mode u = U sin(pi (y + 1/2) / H) decays as exp(-nu (pi/H)^2 t) (the nonlinear term
+    vanishes), so the measured rate pins the wall position of the bounce-back rule."""
+    nu = (tau - 0.5) / 3
+    cfg = dict(dim=2, nx=2, ny=H, bc={"x": ("periodic", "periodic"), "y": ("wall", "wall")},
+               dx=1.0, dt=1.0, nu_ref=nu, collision=coll)
+    N = 2 * H
+    o = Oracle(cfg, torch.zeros(N, dtype=torch.uint8))
+    y = (torch.arange(N) // 2).double()
+    u = torch.zeros(2, N, dtype=f64)
+    u[0] = 0.01 * torch.sin(math.pi * (y + 0.5) / H)
+    n0 = int(0.05 * H * H / nu / math.pi ** 2) + 5
+    n1 = int(0.3 * H * H / nu / math.pi ** 2)
+    st = o.run(o.init_state(u=u), n0)
+    a0 = st["u"][0].abs().max().item()
+    st = o.run(st, n1)
+    a1 = st["u"][0].abs().max().item()
+    return -math.log(a1 / a0) / n1 / (nu * (math.pi / H) ** 2) - 1.0
+
+
+@pytest.mark.parametrize("coll", ["bgk", "cumulant"])
+def test_channel_bounce_back_second_order(coll):
+    e = [abs(_channel_decay_rate(H, coll)) for H in (8, 16, 32)]
+    assert e[2] < 0.01
+    assert e[0] / e[1] > 3.0 and e[1] / e[2] > 3.0, e
+
+
+def test_poiseuille_inlet_outlet():
+    """Plane Poiseuille flow through the moving-wall inlet, walls and the pressure outlet: the
+    mid-channel profile is the parabola with walls half-way between nodes, error O(1/H^2)."""
+    errs = []
+    for H in (8, 16):
+        nx, tau, U = 4 * H, 0.8, 0.01
+        nu = (tau - 0.5) / 3
+        cfg = dict(dim=2, nx=nx, ny=H, bc={"x": ("inlet", "outlet"), "y": ("wall", "wall")},
+                   dx=1.0, dt=1.0, nu_ref=nu, collision="bgk")
+        yy = np.arange(H) + 0.5
+        prof = 4 * U * yy * (H - yy) / H ** 2
+        inlet = np.zeros((2, H))
+        inlet[0] = prof
+        N = nx * H
+        o = Oracle(cfg, torch.zeros(N, dtype=torch.uint8), inlet)
+        x = np.arange(N) % nx
+        y = np.arange(N) // nx
+        u = np.zeros((2, N))
+        u[0] = prof[y]
+        P = 8 * nu * U / H ** 2 * (nx - 0.5 - x)
+        st = o.run(o.init_state(u=u, P_h=P), int(2.0 * H * H / nu))
+        mid = st["u"][0].numpy().reshape(H, nx)[:, nx // 2]
+        errs.append(np.abs(mid - prof).max() / U)
+    assert errs[1] < 0.02 and errs[0] / errs[1] > 2.5, errs
+
+
+@pytest.mark.parametrize("dim,coll", [(2, "cumulant"), (2, "bgk"), (3, "cumulant")])
+def test_periodic_box_conserves_mass_and_momentum(dim, coll):
+    wl = W.generate.box(dim, 10 if dim == 3 else 24, collision=coll, tau=0.6, seed=5, pert=1e-3, U=0.02)
+    wl.cfg["smag_cs"] = 0.17
+    o = Oracle(wl.cfg, wl.mask, wl.inlet_u)
+    st = o.init_state(u=wl.u, P_h=wl.P_h, g_pert=wl.g_pert)
+    m0, p0 = st["g"].sum().item(), (o.lat.c.T @ st["g"]).sum(1)
+    st = o.run(st, 30)
+    assert abs(st["g"].sum().item() - m0) < 1e-13 * max(1.0, abs(m0)) + 1e-13
+    assert ((o.lat.c.T @ st["g"]).sum(1) - p0).abs().max().item() < 1e-13
+
+
+def test_links_hand_derived():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "links_3x3.txt")) if l.strip() and l[0] != "#"]
+    L = Lattice(2)
+    for case, x, y, word, fluid in rows:
+        mask = np.zeros(9, np.uint8)
+        bc = {"x": ("wall", "wall"), "y": ("wall", "wall")}
+        if case in ("walls_solid", "periodic_solid"):
+            mask[4] = 1
+        if case == "periodic_solid":
+            bc["x"] = ("periodic", "periodic")
+        g = geo.Grid({"dim": 2, "nx": 3, "ny": 3, "nz": 1, "bc": bc}, mask)
+        code, _ = geo.lb_links(L, g)
+        words = geo.pack_links(code, g)
+        r = int(x) + 3 * int(y)
+        expect = (int(word) | (1 << 31)) if int(fluid) else 0
+        assert int(words[r]) == expect, (case, x, y, int(words[r]), expect)
+
+
+# --------------------------------------------------------------------- FD and chemistry pins
+def test_weno3_exact_on_linear_and_ideal_weights():
+    a, b, c = torch.tensor([1.0], dtype=f64), torch.tensor([2.0], dtype=f64), torch.tensor([3.0], dtype=f64)
+    # linear data: both candidate faces coincide with the exact face value 2.5
+    assert abs(fdm.weno3(a, b, c, 1e-6).item() - 2.5) < 1e-15
+    # equal smoothness -> ideal weights 1/3, 2/3 (third-order upwind face -a/6 + 5b/6 + c/3)
+    x = torch.tensor([0.0], dtype=f64)
+    val = fdm.weno3(x - 1.0, x, x + 1.0, 1e-6)  # linear, equal beta
+    assert abs(val.item() - 0.5) < 1e-15
+    vals = torch.tensor([0.3, 0.1, 0.2], dtype=f64)
+    # symmetric beta (|b - a| = |c - b|) -> ideal combination
+    a, b, c = torch.tensor([0.0], dtype=f64), torch.tensor([1.0], dtype=f64), torch.tensor([0.0], dtype=f64)
+    ideal = -a / 6 + 5 * b / 6 + c / 3
+    assert abs(fdm.weno3(a, b, c, 1e-6).item() - ideal.item()) < 1e-12
+    del vals
+
+
+def test_weno3_non_oscillatory_at_a_jump():
+    """ENO property: across a unit jump the face value stays inside the data range."""
+    for a, b, c in [(0.0, 0.0, 1.0), (0.0, 1.0, 1.0), (1.0, 0.0, 0.0)]:
+        v = fdm.weno3(torch.tensor([a], dtype=f64), torch.tensor([b], dtype=f64), torch.tensor([c], dtype=f64), 1e-6).item()
+        assert -1e-6 <= v <= 1 + 1e-6
+
+
+def test_weno3_convergence_on_smooth_data():
+    """Advection derivative (face difference) of a smooth monotone profile converges at >= 2nd order."""
+    errs = []
+    for n in (32, 64, 128):
+        h = 1.0 / n
+        x = (torch.arange(-2, n + 3, dtype=f64)) * h
+        phi = torch.tanh(2 * (x - 0.5))
+        fp = fdm.weno3(phi[1:-3], phi[2:-2], phi[3:-1], 1e-6)  # faces i+1/2 for i = 2..n+2
+        fm = fdm.weno3(phi[0:-4], phi[1:-3], phi[2:-2], 1e-6)  # faces i-1/2
+        d = (fp - fm) / h
+        exact = 2 / torch.cosh(2 * (x[2:-2] - 0.5)) ** 2
+        errs.append((d - exact).abs().max().item())
+    assert math.log2(errs[0] / errs[1]) > 1.8 and math.log2(errs[1] / errs[2]) > 1.8, errs
+
+
+def test_reaction_mechanism_conserves_mass():
+    """sum_k omega_k = 0 for every reaction (element and mass balance of both mechanisms)."""
+    for names, rx in ((W.SPECIES["6sp"], W.chemistry_2step()), (W.SPECIES["4sp"], W.chemistry_1step())):
+        cfg = {"dim": 2, "nx": 1, "ny": 1, "dx": 1.0, "dt": 1.0, "nu_ref": 1.0,
+               "species": W.configs.species(names), "reactions": rx}
+        p = Params(cfg)
+        for j in range(len(rx)):
+            q = [torch.zeros(1, dtype=f64) for _ in rx]
+            q[j] = torch.ones(1, dtype=f64)
+            om = fdm.species_rates(p, q)
+            total = sum(o.item() for o in om)
+            scale = sum(abs(o.item()) for o in om)
+            assert abs(total) < 1e-14 * scale
+
+
+def _closed_form_T_ad(names, phi, T0, cp):
+    """Complete combustion at constant pressure with constant c_p: T0 + sum_k h_f,k (Y_k,0 - Y_k,b) / c_p."""
+    thermo = W.configs._THERMO
+    Yu = W.mixture_phi(names, phi)
+    moles = {"O2": 2.0 - 2.0 * phi, "N2": 7.52}
+    if "CO2" in names:
+        moles.update({"CO2": phi, "H2O": 2.0 * phi})
+    else:
+        moles["P"] = 3.0 * phi
+    mass = {k: v * thermo[k][0] for k, v in moles.items()}
+    tot = sum(mass.values())
+    Yb = [mass.get(n, 0.0) / tot for n in names]
+    hf = [thermo[n][1] / thermo[n][0] for n in names]
+    return T0 + sum(h * (a - b) for h, a, b in zip(hf, Yu, Yb)) / cp, Yb
+
+
+def _homogeneous_burn(names, rx, T0, dt, steps):
+    """Explicit Euler energy/species update of the oracle on a uniform periodic patch at rest
+    (no transport), i.e. homogeneous combustion at constant pressure."""
+    cfg = W.generate._base_cfg(2, 2, 2, 1, "f64")
+    cfg.update({"bc": {"x": ("periodic", "periodic"), "y": ("periodic", "periodic")}, "dx": 1e-3, "dt": dt,
+                "nu_ref": 1.5e-5, "thermal": True, "species": W.configs.species(names, unity_lewis=True),
+                "reactions": rx, "T_in": T0, "Y_in": W.mixture_phi(names, 0.83)})
+    p = Params(cfg)
+    grid = geo.Grid(cfg, np.zeros(4, np.uint8))
+    nb = geo.FDNeighbours(grid)
+    T = torch.full((4,), T0, dtype=f64)
+    Y = torch.tensor(W.mixture_phi(names, 0.83), dtype=f64)[:, None].repeat(1, 4)
+    u = torch.zeros(2, 4, dtype=f64)
+    hf = torch.tensor([s["hf"] for s in cfg["species"]], dtype=f64)
+    H0 = (p.cp * T + (hf[:, None] * Y).sum(0)).mean().item()
+    for _ in range(steps):
+        T, Y, _, _ = fdm.fd_update(p, grid, nb, T, Y, u, u, p.P_th0, 0.0)
+    H1 = (p.cp * T + (hf[:, None] * Y).sum(0)).mean().item()
+    return T.mean().item(), H0, H1, p.cp
+
+
+@pytest.mark.parametrize("mech", ["2step", "1step"])
+def test_adiabatic_flame_temperature(mech):
+    """Homogeneous constant-pressure combustion: each explicit step keeps c_p T + sum h_f Y
+    exactly, and as dt -> 0 the burnt state reaches the closed-form adiabatic temperature of
+    complete combustion (Euler overshoots the fuel through zero by O(dt) in the last step)."""
+    names = W.SPECIES["6sp"] if mech == "2step" else W.SPECIES["4sp"]
+    rx = W.chemistry_2step() if mech == "2step" else W.chemistry_1step()
+    T0, t_end = 1800.0, 2.0e-5
+    errs = []
+    for dt in (1e-7, 2.5e-8):
+        T, H0, H1, cp = _homogeneous_burn(names, rx, T0, dt, int(round(t_end / dt)))
+        assert abs(H1 - H0) < 1e-11 * abs(H0)
+        T_ad, _ = _closed_form_T_ad(names, 0.83, T0, cp)
+        errs.append(abs(T - T_ad) / T_ad)
+    assert errs[1] < 2e-3 and errs[0] / errs[1] > 2.5, errs
+
+
+def test_species_sum_and_conservation():
+    """One step from rest with equal Lewis numbers keeps sum_k Y_k = 1 per cell (diffusion is
+    linear and shared, sum_k omega_k = 0); with equal molar masses, uniform T and a uniform
+    velocity in a periodic box, sum_r Y_k is conserved (WENO faces and diffusion fluxes
+    telescope)."""
+    wl = W.generate.chamber_2d(nx=24, ny=12, dt=5e-7, seed=7)
+    for s in wl.cfg["species"]:
+        s["Le"] = 1.0
+    rng = np.random.default_rng(0)
+    wl.Y = wl.Y * (1 + 0.05 * rng.standard_normal(wl.Y.shape))
+    wl.Y /= wl.Y.sum(0, keepdims=True)
+    o = Oracle(wl.cfg, wl.mask, wl.inlet_u)
+    st = o.run(o.init_state(T=wl.T, Y=wl.Y, u=np.zeros((2, wl.N))), 1)
+    fluid = wl.mask == 0
+    assert np.abs(st["Y"].numpy()[:, fluid].sum(0) - 1).max() < 1e-14
+
+    cfg = W.generate._base_cfg(2, 16, 12, 1, "f64")
+    cfg.update({"bc": {"x": ("periodic", "periodic"), "y": ("periodic", "periodic")}, "dx": 1e-4, "dt": 5e-7,
+                "nu_ref": 1.5e-5, "thermal": True,
+                "species": [{"name": "A", "W": 0.028, "Le": 1.0, "hf": 0.0}, {"name": "B", "W": 0.028, "Le": 1.0, "hf": 0.0}],
+                "reactions": [], "T_in": 300.0, "Y_in": [0.5, 0.5]})
+    N = 16 * 12
+    YA = 0.5 + 0.2 * rng.standard_normal(N)
+    Y = np.stack([YA, 1 - YA])
+    u = np.zeros((2, N))
+    u[0], u[1] = 0.02, -0.01
+    o = Oracle(cfg, np.zeros(N, np.uint8))
+    st = o.init_state(T=np.full(N, 300.0), Y=Y, u=u)
+    s0 = st["Y"].sum(1)
+    st = o.run(st, 20)
+    assert (st["Y"].sum(1) - s0).abs().max().item() < 1e-12

@@ -1,0 +1,247 @@
+"""Seeded generators of the synthetic workloads (masks, inlet profiles, initial fields).
+
+Shapes follow the paper's cases (Section 3): a 2-D chamber with rows of rectangular
+obstacles and a burnt-gas semicircle at the closed end (Section 3.1), and a swirl burner with an
+annular swirling inlet, a square confined chamber and a contracting exhaust (Section 3.2), plus
+a planar premixed flame. The paper's own geometry files and measurements are not available; these
+inputs stand in for them. Randomness: numpy PCG64 seeded by the ``seed`` argument.
+
+Units: lengths in cells, velocities and pressures in lattice units, temperatures in kelvin, mass
+fractions dimensionless. The ``cfg`` dictionary carries the SI parameters of the run.
+Cell index r = x + nx (y + ny z); fields are [..., N] with x fastest.
+"""
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .configs import SPECIES, burnt_mixture, chemistry_1step, chemistry_2step, mixture_phi, species
+
+
+@dataclass
+class Workload:
+    name: str
+    cfg: dict
+    mask: np.ndarray
+    inlet_u: np.ndarray
+    u: np.ndarray
+    P_h: np.ndarray
+    T: np.ndarray = None
+    Y: np.ndarray = None
+    g_pert: np.ndarray = None
+    steps: int = 0
+    info: dict = field(default_factory=dict)
+
+    @property
+    def N(self):
+        return self.mask.size
+
+    @property
+    def Q(self):
+        return 3 ** self.cfg["dim"]
+
+
+def _base_cfg(dim, nx, ny, nz, storage, collision="cumulant"):
+    return {"dim": dim, "nx": nx, "ny": ny, "nz": nz if dim == 3 else 1,
+            "storage": storage, "collision": collision,
+            "T_ref": 300.0, "mu_exp": 0.7, "Pr": 0.7, "cp": 1400.0, "rho_ref": 1.17,
+            "P_th0": 101325.0, "P_ref": 0.0, "omega_bulk": 1.0, "omega_hi": [1.0, 1.0, 1.0, 1.0],
+            "smag_cs": 0.0, "thicken_F": 1.0, "flame_sensor": False, "sensor_beta": 10.0,
+            "sensor_wref": 1.0, "sensor_species": 0, "closed_domain": False, "thermal": False,
+            "species": [], "reactions": [], "T_in": 300.0, "Y_in": []}
+
+
+def _tanh_blend(s, width):
+    return 0.5 * (1.0 + np.tanh(s / width))
+
+
+def _coords(nx, ny, nz):
+    r = np.arange(nx * ny * nz)
+    return r % nx, (r // nx) % ny, r // (nx * ny)
+
+
+def perturbation(rng, Q, N, amp):
+    """Seeded non-equilibrium perturbation added to the initial populations (both sides)."""
+    return amp * rng.standard_normal((Q, N))
+
+
+# --------------------------------------------------------------------------- planar flame
+def flame_2d(nx=256, ny=8, storage="f64", seed=0, collision="cumulant", u_in=0.0034,
+             A=1.0e9, steps=2000, dx=5e-5, dt=5e-7, width_cells=20.0, T_u=300.0, T_hot=1950.0,
+             unity_lewis=True):
+    """Planar premixed flame: inflow at low x, outflow at high x, periodic in y; one-step
+    chemistry with 4 species; tanh profile of T and Y over ``width_cells`` cells, position
+    jittered by the seed within +-2 cells."""
+    rng = np.random.default_rng(seed)
+    names = SPECIES["4sp"]
+    cfg = _base_cfg(2, nx, ny, 1, storage, collision)
+    cfg.update({"bc": {"x": ("inlet", "outlet"), "y": ("periodic", "periodic")},
+                "dx": dx, "dt": dt, "nu_ref": 1.8e-5 / 1.17, "thermal": True,
+                "species": species(names, unity_lewis), "reactions": chemistry_1step(A),
+                "T_in": T_u, "Y_in": mixture_phi(names, 0.83)})
+    x, y, _ = _coords(nx, ny, 1)
+    x0 = nx / 4.0 + rng.uniform(-2.0, 2.0)
+    b = _tanh_blend(x + 0.5 - x0, width_cells / 4.0)
+    Yu, Yb = np.array(mixture_phi(names, 0.83)), np.array(burnt_mixture(names, 0.83))
+    T = T_u + (T_hot - T_u) * b
+    Y = Yu[:, None] * (1 - b)[None, :] + Yb[:, None] * b[None, :]
+    u = np.zeros((2, nx * ny))
+    u[0] = u_in * T / T_u
+    inlet = np.zeros((2, ny))
+    inlet[0] = u_in
+    return Workload("flame_2d", cfg, np.zeros(nx * ny, np.uint8), inlet, u, np.zeros(nx * ny),
+                    T=T, Y=Y, steps=steps, info={"x0": x0})
+
+
+# ------------------------------------------------------------------------ 2-D chamber
+def chamber_2d(nx=1024, ny=256, storage="f32", seed=0, collision="cumulant", F=5.0, smag=0.17,
+               obstacle=(16, 48), n_rows=3, per_row=3, inlet=False, u_in=0.02, steps=20000,
+               dx=1e-4, dt=5e-8, A1=1.0e9, A2=5.0e6, hot_radius=10.0, T_u=300.0, T_hot=1950.0):
+    """Confined 2-D chamber: closed left end (or an inlet when ``inlet``), open right end, walls
+    top and bottom, ``n_rows`` rows of ``per_row`` rectangular obstacles at seeded positions,
+    hot burnt-gas semicircle at the left end; 2-step chemistry, 6 species, phi = 0.83."""
+    rng = np.random.default_rng(seed)
+    names = SPECIES["6sp"]
+    cfg = _base_cfg(2, nx, ny, 1, storage, collision)
+    cfg.update({"bc": {"x": ("inlet" if inlet else "wall", "outlet"), "y": ("wall", "wall")},
+                "dx": dx, "dt": dt, "nu_ref": 1.8e-5 / 1.17, "thermal": True, "smag_cs": smag,
+                "thicken_F": F, "species": species(names), "reactions": chemistry_2step(A1, A2),
+                "T_in": T_u, "Y_in": mixture_phi(names, 0.83)})
+    x, y, _ = _coords(nx, ny, 1)
+    mask = np.zeros(nx * ny, np.uint8)
+    ow = max(2, round(obstacle[0] * nx / 1024))
+    oh = max(2, round(obstacle[1] * ny / 256))
+    rows = []
+    for k in range(n_rows):
+        xc = int(nx * (0.25 + 0.22 * k) + rng.integers(-nx // 32, nx // 32 + 1))
+        band = ny / per_row
+        for j in range(per_row):
+            lo = int(j * band + 1)
+            hi = int((j + 1) * band - oh - 1)
+            yc = int(rng.integers(lo, max(lo, hi) + 1))
+            sel = (x >= xc) & (x < xc + ow) & (y >= yc) & (y < yc + oh)
+            mask[sel] = 1
+            rows.append((xc, yc))
+    rad = max(3.0, hot_radius * ny / 256)
+    dist = np.sqrt((x + 0.5) ** 2 + (y + 0.5 - ny / 2.0) ** 2)
+    b = _tanh_blend(rad - dist, 1.0)
+    Yu, Yb = np.array(mixture_phi(names, 0.83)), np.array(burnt_mixture(names, 0.83))
+    T = T_u + (T_hot - T_u) * b
+    Y = Yu[:, None] * (1 - b)[None, :] + Yb[:, None] * b[None, :]
+    u = np.zeros((2, nx * ny))
+    inlet_u = np.zeros((2, ny))
+    if inlet:
+        yy = np.arange(ny) + 0.5
+        inlet_u[0] = u_in * 4.0 * yy * (ny - yy) / ny ** 2
+    return Workload("chamber_2d", cfg, mask, inlet_u, u, np.zeros(nx * ny), T=T, Y=Y,
+                    steps=steps, info={"obstacles": rows})
+
+
+# -------------------------------------------------------------------------- 3-D swirl
+def swirl_k(S, Ri, Ro):
+    """Tangential/axial velocity ratio giving swirl number S for uniform axial and tangential
+    velocity across an annulus Ri < r < Ro: S = k * 2 (Ro^3 - Ri^3) / (3 Ro (Ro^2 - Ri^2))."""
+    return S * 3.0 * Ro * (Ro ** 2 - Ri ** 2) / (2.0 * (Ro ** 3 - Ri ** 3))
+
+
+def swirl_3d(nx=256, ny=128, nz=128, reactive=False, storage="f32", seed=0,
+             collision="cumulant", u_axial=0.05, swirl=0.6, noise=0.05, smag=0.17, F=8.0,
+             steps=None, dx=None, dt=None, A1=1.0e9, A2=5.0e6, T_in=320.0, T_hot=1970.0,
+             sensor_wref=50.0):
+    """Swirl-burner-like domain along x: annular swirling inlet (radii 8 and 16 cells at the
+    128-cell scale) through an injector duct, square confined chamber, contracting exhaust to
+    an outlet; cold (LB only) or reactive (2-step chemistry, thickened flame with sensor,
+    closed-domain thermodynamic pressure)."""
+    rng = np.random.default_rng(seed)
+    s = ny / 128.0
+    cfg = _base_cfg(3, nx, ny, nz, storage, collision)
+    if dx is None:
+        dx = 1e-3 if not reactive else 5e-4
+    if dt is None:
+        dt = 3e-6 if not reactive else 1e-6
+    cfg.update({"bc": {"x": ("inlet", "outlet"), "y": ("wall", "wall"), "z": ("wall", "wall")},
+                "dx": dx, "dt": dt, "nu_ref": 1.8e-5 / 1.17, "smag_cs": smag})
+    x, y, z = _coords(nx, ny, nz)
+    yc, zc = ny / 2.0, nz / 2.0
+    r = np.sqrt((y + 0.5 - yc) ** 2 + (z + 0.5 - zc) ** 2)
+    Ri, Ro = 8.0 * s, 16.0 * s
+    L1 = int(round(24 * s * nx / (2 * ny))) + int(rng.integers(-2, 3))
+    L2 = int(round(nx * 0.8)) + int(rng.integers(-4, 5))
+    Re = 24.0 * s + rng.uniform(-2.0, 2.0) * s
+    Rc = min(ny, nz) / 2.0 - 1.0
+    mask = np.zeros(nx * ny * nz, np.uint8)
+    inj = x < L1
+    mask[inj & ((r < Ri) | (r > Ro))] = 1
+    cone = x >= L2
+    frac = (x - L2) / max(1, nx - 1 - L2)
+    Rx = Rc + (Re - Rc) * frac
+    mask[cone & (r > Rx)] = 1
+    # inlet face (y, z) values
+    fy = (np.arange(ny * nz) % ny) + 0.5 - yc
+    fz = (np.arange(ny * nz) // ny) + 0.5 - zc
+    fr = np.sqrt(fy ** 2 + fz ** 2)
+    ann = (fr >= Ri) & (fr <= Ro)
+    k = swirl_k(swirl, Ri, Ro)
+    inlet = np.zeros((3, ny * nz))
+    inlet[0] = np.where(ann, u_axial, 0.0)
+    ut = k * u_axial
+    safe = np.where(fr > 0, fr, 1.0)
+    inlet[1] = np.where(ann, -ut * fz / safe, 0.0)
+    inlet[2] = np.where(ann, ut * fy / safe, 0.0)
+    inlet += np.where(ann, 1.0, 0.0)[None, :] * noise * u_axial * rng.standard_normal((3, ny * nz))
+    N = nx * ny * nz
+    u = np.zeros((3, N))
+    wl = Workload("swirl_3d", cfg, mask, inlet, u, np.zeros(N),
+                  steps=steps or (5000 if reactive else 10000),
+                  info={"L1": L1, "L2": L2, "Re": Re, "swirl_k": k})
+    if reactive:
+        names = SPECIES["6sp"]
+        Yu, Yb = np.array(mixture_phi(names, 0.83)), np.array(burnt_mixture(names, 0.83))
+        xf = L1 + 16 * s
+        b = _tanh_blend(x + 0.5 - xf, 4.0 * s)
+        cfg.update({"thermal": True, "thicken_F": F, "flame_sensor": True,
+                    "sensor_beta": 10.0, "sensor_wref": sensor_wref, "sensor_species": 0,
+                    "closed_domain": True, "species": species(names),
+                    "reactions": chemistry_2step(A1, A2), "T_in": T_in, "T_ref": 300.0,
+                    "Y_in": list(Yu)})
+        wl.T = T_in + (T_hot - T_in) * b
+        wl.Y = Yu[:, None] * (1 - b)[None, :] + Yb[:, None] * b[None, :]
+    return wl
+
+
+# ------------------------------------------------------------------------ periodic box
+def box(dim, n, storage="f64", collision="cumulant", tau=0.8, seed=0, pert=0.0, U=0.0):
+    """Isothermal periodic box with a seeded random velocity field and population noise."""
+    rng = np.random.default_rng(seed)
+    ns = [n] * dim if np.isscalar(n) else list(n)
+    nx, ny = ns[0], ns[1]
+    nz = ns[2] if dim == 3 else 1
+    cfg = _base_cfg(dim, nx, ny, nz, storage, collision)
+    bc = {"x": ("periodic", "periodic"), "y": ("periodic", "periodic")}
+    if dim == 3:
+        bc["z"] = ("periodic", "periodic")
+    cfg.update({"bc": bc, "dx": 1.0, "dt": 1.0, "nu_ref": (tau - 0.5) / 3.0})
+    N = nx * ny * nz
+    u = U * rng.standard_normal((dim, N))
+    wl = Workload("box", cfg, np.zeros(N, np.uint8), np.zeros((dim, ny * nz)), u,
+                  np.zeros(N), steps=100)
+    if pert:
+        wl.g_pert = perturbation(rng, 3 ** dim, N, pert)
+    return wl
+
+
+_NAMED = {
+    "c1_flame_2d": lambda seed=0: flame_2d(seed=seed),
+    "c2_chamber_2d": lambda seed=0: chamber_2d(seed=seed),
+    "c3_swirl_cold_3d": lambda seed=0: swirl_3d(seed=seed),
+    "c4_swirl_reactive_3d": lambda seed=0: swirl_3d(384, 192, 192, reactive=True, seed=seed),
+    "c5_adjoint_2d": lambda seed=0: chamber_2d(512, 128, inlet=True, steps=2000, seed=seed),
+}
+
+
+def names():
+    return list(_NAMED)
+
+
+def make(name, seed=0):
+    return _NAMED[name](seed)
