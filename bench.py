@@ -1,0 +1,260 @@
+"""Benchmark of one full hybrid LB/FD step (FD update + flame sensor + thermodynamic pressure +
+LB stream/collide) on the reactive swirl-burner workload (384 x 192 x 192 cells, D3Q27,
+6 species, 2-step chemistry, thickened flame with sensor, closed-domain thermodynamic pressure).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Metric: million lattice-cell updates per second of the full
+step (MLUPS), FP32 populations and arithmetic; the same step with FP16 shifted population
+storage is reported beside it. N > 1 runs independent replicas (one per GPU, weak scaling).
+The state (~4.3 GB FP32) is larger than L2, so no flush is needed between steps.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "c4_swirl_reactive_3d"
+METRIC = "MLUPS per full hybrid step (LB + FD + chemistry + P_th), % of HBM roofline"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = max(mx, float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _timed_steps(solver, steps, torch):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    solver.synchronize()
+    e0.record(solver.stream)
+    solver.step(steps)
+    e1.record(solver.stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_variant(wl, storage, steps, warmup, torch, profile_steps):
+    from paper_2207_11567_gb300 import from_workload
+    wl.cfg["storage"] = storage
+    s = from_workload(wl)
+    s.step(warmup)
+    s.synchronize()
+    ms = _timed_steps(s, steps, torch)
+    # per-kernel CUDA-event timing on the library's stream (direct launches)
+    s.profile(True)
+    s.step(profile_steps)
+    kt = s.kernel_times()
+    s.profile(False)
+    kb = s.kernel_bytes()
+    out = {"ms": ms, "kernels": {k: {"ms_avg": (t / n if n else 0.0), "launches": n, "bytes": kb[k]}
+                                 for k, (t, n) in kt.items()}}
+    s.close()
+    return out
+
+
+def e2e_run(wl, steps, torch):
+    """User call sequence through the C ABI with host buffers: initial fields uploaded from host
+    memory, K steps, fields read back to host memory; all inside the timed region."""
+    from paper_2207_11567_gb300 import Solver
+    from paper_2207_11567_gb300 import _lib as L
+    wl.cfg["storage"] = "f32"
+    s = Solver(wl.cfg, wl.mask, wl.inlet_u)
+    bits = L.F_T | L.F_Y | L.F_U | L.F_PH
+    s.synchronize()
+    t0 = time.perf_counter()
+    s.set_fields(T=wl.T, Y=wl.Y, u=wl.u, P_h=wl.P_h)
+    s.step(steps)
+    out = s.fields(bits)
+    t1 = time.perf_counter()
+    h2d = 8 * (wl.T.size + wl.Y.size + wl.u.size + wl.P_h.size)
+    d2h = 8 * sum(v.size for v in out.values())
+    s.close()
+    return t1 - t0, h2d, d2h
+
+
+def oracle_sample(max_seconds=20.0):
+    """The FP64 CPU oracle as it stands on a bounded sample of the same workload: a reduced
+    reactive swirl domain (48 x 24 x 24 cells, same physics and parameters), timed per step."""
+    import torch
+    import workloads as W
+    from oracle.step import Oracle
+    wl = W.generate.swirl_3d(48, 24, 24, reactive=True, seed=0)
+    o = Oracle(wl.cfg, wl.mask, wl.inlet_u)
+    st = o.init_state(T=wl.T, Y=wl.Y, u=wl.u, P_h=wl.P_h)
+    st = o.step(st)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < max_seconds:
+        st = o.step(st)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": wl.N * n / dt / 1e6, "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle, reactive swirl {wl.cfg['nx']}x{wl.cfg['ny']}x{wl.cfg['nz']} "
+                      f"({wl.N} cells) cut from the same workload family, {n} steps in {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = oracle_sample(max_seconds=max(5.0, min(60.0, 2.0 * args.steps)))
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+                "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                                            "d2h_bytes_per_step": 0}, "vs_baseline": None}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import workloads as W
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    else:
+        torch.cuda.set_device(0)
+    dev_index = torch.cuda.current_device()
+
+    wl = W.make(WORKLOAD)
+    # FP16-storage variant first (its own solver), then the FP32 headline
+    f16 = run_variant(W.make(WORKLOAD), "f16", args.steps, args.warmup, torch, profile_steps=10)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(dev_index) as clk:
+        f32 = run_variant(wl, "f32", args.steps, args.warmup, torch, profile_steps=10)
+    ms = f32["ms"]
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    e2e_s, h2d, d2h = e2e_run(W.make(WORKLOAD), args.steps, torch)
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+
+    N = wl.N
+    value = N * args.steps * world / (ms * 1e-3) / 1e6
+    peak, peak_kind = _peaks()
+    kern = f32["kernels"]
+    dominant = max(kern, key=lambda k: kern[k]["ms_avg"] * kern[k]["launches"])
+    dk = kern[dominant]
+    achieved = dk["bytes"] / (dk["ms_avg"] * 1e-3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            tr = json.load(f).get(f"{dominant}:{WORKLOAD}:f32")
+            traffic = tr if tr else None
+    except Exception:
+        traffic = None
+    per_step_launches = sum(1 for k in kern.values() if k["launches"])
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [wl.cfg["nx"], wl.cfg["ny"], wl.cfg["nz"]], "cells": N,
+                   "lattice": "D3Q27", "collision": "cumulant+smagorinsky", "species": 6, "reactions": 2,
+                   "thicken_F": 8, "flame_sensor": True, "closed_domain": True, "storage": "f32",
+                   "parallelism": f"replicas{world}", "l2": "state 4.3 GB > L2, no flush needed"},
+        "e2e": {"value": N * args.steps / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
+                "d2h_bytes_per_step": d2h / args.steps,
+                "note": "set_fields from host + K steps + get_fields to host, through the C ABI"},
+        "gpu_launches": per_step_launches * args.steps,
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                     "bytes_per_launch": dk["bytes"], "ms_per_launch": dk["ms_avg"]},
+        "kernels": {k: {"ms": v["ms_avg"], "GB/s": (v["bytes"] / (v["ms_avg"] * 1e-3) / 1e9) if v["ms_avg"] else 0.0}
+                    for k, v in kern.items() if v["launches"]},
+        "fp16_storage": {"value": N * args.steps * world / (f16["ms"] * 1e-3) / 1e6, "unit": "MLUPS",
+                         "ms_per_step": f16["ms"] / args.steps,
+                         "lb_ms": f16["kernels"]["lb_stream_collide"]["ms_avg"],
+                         "lb_GB/s": f16["kernels"]["lb_stream_collide"]["bytes"]
+                         / (f16["kernels"]["lb_stream_collide"]["ms_avg"] * 1e-3) / 1e9},
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample()
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * hlbm.h - C ABI of the GB300 library for one full time step of the hybrid low-Mach
+ * lattice Boltzmann / finite-difference combustion solver of Hosseini, Darabiha and Thevenin,
+ * "Low Mach number lattice Boltzmann model for turbulent combustion: flow in confined
+ * geometries" (Section 2).
+ *
+ * One step (lbm_step) is, for every cell:
+ *   1. the finite-difference update of temperature and species (Section 2.3: explicit Euler,
+ *      third-order WENO advection, centred second-order diffusion) with Arrhenius chemistry and
+ *      the thickened-flame factor, producing rho and the dilatation Lambda of Eq. 3;
+ *   2. in a closed domain, the thermodynamic-pressure update (a reduction over all cells);
+ *   3. the lattice Boltzmann pull-stream and collide of Eq. 1, with the source Xi of Eq. 2,
+ *      the moments of Eq. 7, the pre-conditioning of Eq. 13, the cumulant collision of
+ *      Eq. 9-12 (or the single-rate special case) with a Smagorinsky eddy viscosity, and the
+ *      post-collision populations of Eq. 8; bounce-back on solid cells.
+ *
+ * Conventions
+ *   - Grid: nx * ny * nz cells (nz = 1 when dim == 2); cell index r = x + nx*(y + ny*z).
+ *     Every field is structure-of-arrays, x fastest.
+ *   - Lattice: D2Q9 (dim 2) or D3Q27 (dim 3). Direction i has velocity (cx, cy[, cz]) with
+ *     i = (cx+1) + 3*(cy+1) [+ 9*(cz+1)]; the opposite of i is Q-1-i; weights are tensor
+ *     products of (1/6, 2/3, 1/6).
+ *   - Units: the configuration is SI; internally lattice units (dr = dt = 1, c_s^2 = 1/3).
+ *     Velocities, pressures P_h and population values exchanged through this ABI are in lattice
+ *     units; temperatures in kelvin; densities in units of cfg.rho_ref; P_th in pascal.
+ *   - Masks: uint8 per cell, 0 = fluid, anything else = solid (never updated).
+ *   - Boundaries per face: LBM_BC_PERIODIC, LBM_BC_WALL (halfway bounce-back, zero-gradient
+ *     scalars), LBM_BC_INLET (low-x face only: bounce-back from a wall moving with the inlet
+ *     velocity, Dirichlet T_in / Y_in), LBM_BC_OUTLET (high-x face only: zero-gradient copy of
+ *     the populations and scalars).
+ *   - Ownership: the caller owns every pointer it passes; the library copies inputs during the
+ *     call and owns its internal device buffers (allocated through cfg.alloc/cfg.free when given,
+ *     else cudaMalloc/cudaFree).
+ *   - Streams: all work is enqueued on cfg.stream. With NULL the library creates its own blocking
+ *     stream (which orders itself with the legacy default stream); step pairs are captured in
+ *     CUDA graphs, which the legacy default stream does not allow. Calls that return data to
+ *     host memory synchronise the stream.
+ *   - Errors: nothing aborts or traps. Every call returns an lbm_status; lbm_last_error gives
+ *     a one-line message. A context that returned LBM_ERR_CUDA should be destroyed.
+ */
+#ifndef HLBM_H
+#define HLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = 1,         /* invalid argument or configuration                       */
+  LBM_ERR_ALLOC = 2,       /* device allocation failed (or the allocator returned NULL) */
+  LBM_ERR_CUDA = 3,        /* a CUDA runtime call failed                               */
+  LBM_ERR_STATE = 4,       /* call out of order (e.g. step before set_fields)          */
+  LBM_ERR_NONFINITE = 5,   /* a non-finite velocity was produced by a step             */
+  LBM_ERR_UNSUPPORTED = 6  /* valid request this build does not implement              */
+} lbm_status;
+
+enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_INLET = 2, LBM_BC_OUTLET = 3 };
+/* population storage: all arithmetic is FP64 for LBM_STORE_F64, FP32 otherwise. Populations are
+ * stored shifted, h_i = (g_i - w_i P_ref) / w_i. */
+enum { LBM_STORE_F64 = 0, LBM_STORE_F32 = 1, LBM_STORE_F16 = 2 };
+enum { LBM_COLL_BGK = 0, LBM_COLL_CUMULANT = 1 };
+
+#define LBM_MAX_SPECIES 8
+#define LBM_MAX_REACTIONS 4
+
+typedef struct {
+  double W;   /* molar mass, kg/mol                     */
+  double Le;  /* Lewis number (constant)                */
+  double hf;  /* enthalpy of formation, J/kg            */
+} lbm_species;
+
+/* Irreversible Arrhenius step: q = A T^beta exp(-E/(R T)) prod_k [X_k]^order[k], [X] in mol/m^3,
+ * q in mol/(m^3 s); omega_k = W_k nu[k] q (kg/(m^3 s)). Unused entries are 0. */
+typedef struct {
+  double A, beta, E;
+  double nu[LBM_MAX_SPECIES];
+  double order[LBM_MAX_SPECIES];
+} lbm_reaction;
+
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* user);
+typedef void (*lbm_free_fn)(void* ptr, void* user);
+
+typedef struct {
+  int dim, nx, ny, nz;
+  int storage;    /* LBM_STORE_* */
+  int collision;  /* LBM_COLL_*  */
+  int bc_lo[3], bc_hi[3];
+  int thermal;    /* 0: isothermal lattice Boltzmann only (rho = 1, Lambda = 0)           */
+  double dx, dt;  /* grid spacing (m) and time step (s)                                  */
+  double nu_ref;  /* kinematic viscosity at T_ref and density rho_ref, m^2/s               */
+  double T_ref, mu_exp, Pr, cp, rho_ref; /* mu = rho_ref nu_ref (T/T_ref)^mu_exp; J/(kg K)  */
+  double P_th0;   /* initial thermodynamic pressure, Pa                                  */
+  double P_ref;   /* lattice pressure gauge of the shifted population storage            */
+  double smag_cs; /* Smagorinsky constant (0 = off)                                      */
+  double omega_bulk;  /* relaxation rate of the second-order trace                        */
+  double omega_hi[4]; /* rates of cumulant orders 3, 4, 5, 6                              */
+  double thicken_F;   /* thickened-flame factor                                           */
+  int flame_sensor;   /* 1: F_loc = 1 + (F-1) tanh(beta Omega / wref), Omega =
+                         max(Y_fuel,0) max(Y_ox,0) exp(-sensor_Ta / T)                      */
+  int sensor_species, sensor_oxidizer;  /* fuel and oxidizer indices                        */
+  double sensor_beta, sensor_wref, sensor_Ta; /* -, -, K                                    */
+  int closed_domain;  /* 1: thermodynamic pressure from the global mass constraint           */
+  int n_species, n_reactions;
+  lbm_species sp[LBM_MAX_SPECIES];
+  lbm_reaction rx[LBM_MAX_REACTIONS];
+  double T_in;                   /* inlet temperature, K                                   */
+  double Y_in[LBM_MAX_SPECIES];  /* inlet mass fractions                                   */
+  void* stream;                  /* cudaStream_t, NULL = a stream owned by the library      */
+  lbm_alloc_fn alloc;            /* optional device allocator                              */
+  lbm_free_fn free;
+  void* alloc_user;
+} lbm_config;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Validate cfg, convert to lattice units (Eq. 12: tau = nu/c_s^2 + 1/2) and allocate the state.
+ * Returns LBM_ERR_ARG for an invalid configuration, LBM_ERR_ALLOC if allocation fails. */
+lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out);
+void lbm_destroy(lbm_ctx* ctx);
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Geometry (Section 3: solid walls, obstacles, inlets). mask: N bytes. inlet_u: dim * ny * nz
+ * doubles, the lattice velocity of each element (y + ny z) of the low-x inlet face, component
+ * major; may be NULL when there is no inlet. on_device: 1 if both pointers are device memory.
+ * Builds the per-cell link words (see lbm_get_links). */
+lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* mask, const double* inlet_u, int on_device);
+
+/* Initial fields: T [N] (K), Y [n_species][N], u [dim][N], P_h [N] (lattice), g_pert [Q][N]
+ * (lattice, may be NULL). Populations are set to the equilibrium of Eq. 6 plus g_pert. T and Y
+ * are ignored (may be NULL) when cfg.thermal == 0. Requires lbm_set_geometry first. */
+lbm_status lbm_set_fields(lbm_ctx* ctx, const double* T, const double* Y, const double* u,
+                          const double* P_h, const double* g_pert, int on_device);
+
+/* Advance n_steps full steps, asynchronously on the context's stream. */
+lbm_status lbm_step(lbm_ctx* ctx, int n_steps);
+
+/* Field selection bits for lbm_get_fields. Output is FP64, concatenated in bit order:
+ * T [N], Y [n_species][N], u [dim][N], P_h [N] (Eq. 7a, last step), rho [N], Lambda [N]
+ * (both at the level used by the last step), g [Q][N] (post-collision populations, unshifted).
+ * Solid cells hold unspecified values. */
+enum { LBM_F_T = 1, LBM_F_Y = 2, LBM_F_U = 4, LBM_F_PH = 8, LBM_F_RHO = 16, LBM_F_LAM = 32,
+       LBM_F_G = 64 };
+/* Number of doubles lbm_get_fields writes for these bits. */
+size_t lbm_fields_size(const lbm_ctx* ctx, unsigned bits);
+/* Reports LBM_ERR_NONFINITE if any step since the last check produced a non-finite velocity. */
+lbm_status lbm_get_fields(lbm_ctx* ctx, unsigned bits, double* dst, int dst_on_device);
+
+/* Thermodynamic pressure state: out[0] = P_th (Pa), out[1] = last increment of P_th (Pa per
+ * step), out[2] = mass M (lattice units), out[3] = steps taken. Synchronises the stream. */
+lbm_status lbm_get_scalars(lbm_ctx* ctx, double out[4]);
+
+/* Per-cell link words (uint32, N): for a fluid cell bit i is set when direction i is a
+ * bounce-back link (solid, wall or inlet source) and bit 31 is set; solid cells hold 0. */
+lbm_status lbm_get_links(lbm_ctx* ctx, uint32_t* dst, int dst_on_device);
+
+/* Checkpoint: bytes of device memory needed, save into / load from caller-owned device memory. */
+size_t lbm_state_bytes(const lbm_ctx* ctx);
+lbm_status lbm_save_state(lbm_ctx* ctx, void* dst_device);
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* src_device);
+
+/* Kernel timing (CUDA events on the context's stream). enable=1 starts recording each
+ * kernel launch of lbm_step; lbm_kernel_times returns, per kernel kind, the summed device time
+ * in ms and the launch count since the last reset:
+ *   kind 0 finite-difference update, 1 flame sensor, 2 thermodynamic pressure, 3 lattice
+ *   Boltzmann stream-collide. Synchronises the stream. */
+#define LBM_KERNEL_KINDS 4
+lbm_status lbm_profile(lbm_ctx* ctx, int enable);
+lbm_status lbm_kernel_times(lbm_ctx* ctx, double ms[LBM_KERNEL_KINDS], long long launches[LBM_KERNEL_KINDS]);
+
+/* Algorithmic bytes of one launch of each kernel kind (each array touched once). */
+lbm_status lbm_kernel_bytes(const lbm_ctx* ctx, double bytes[LBM_KERNEL_KINDS]);
+
+/* 1: capture pairs of steps in CUDA graphs (default), 0: launch directly. */
+lbm_status lbm_use_graphs(lbm_ctx* ctx, int enable);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HLBM_H */

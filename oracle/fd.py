@@ -16,7 +16,11 @@ Readings (the paper gives no formulas for these):
   * Chemistry: q_j = A_j T^beta_j exp(-E_j/(R T)) prod_k [X_k]^n_jk with [X_k] = rho max(Y_k,0)/W_k,
     omega_k = W_k sum_j nu_kj q_j, heat release -sum_k h_f,k omega_k, constant c_p.
   * Thickening (Colin type, efficiency 1): diffusivities times F_loc, rates divided by F_loc.
-    F_loc = F, or with the flame sensor F_loc = 1 + (F - 1) tanh(beta |omega_s| / omega_ref).
+    F_loc = F, or with the flame sensor F_loc = 1 + (F - 1) tanh(beta Omega / Omega_0) with
+    Omega = max(Y_F, 0) max(Y_O, 0) exp(-T_s / T) (fuel and oxidizer mass fractions, reduced
+    activation temperature T_s): a sensor linear in the reactants, which stays smooth where
+    the fuel vanishes (a sensor built on the fractional-order rate would switch F_loc on fuel
+    residues at round-off level).
   * Lambda (Eq. 3) uses the non-advective right-hand side: Lambda = N_T / T + sum (W/W_k) N_k.
   * Thermodynamic pressure: rho = P_th W / (R T); the energy equation gains the pressure work
     dP_th/(rho c_p) of the previous step.
@@ -68,12 +72,13 @@ def species_rates(p, q):
     return om
 
 
-def thickening(p, omega):
+def thickening(p, T, Y):
     """F_loc per cell."""
     if not p.sensor:
-        return torch.full_like(omega[0], p.F)
-    phi = torch.tanh(p.sensor_beta * omega[p.sensor_species].abs() / p.sensor_wref)
-    return 1.0 + (p.F - 1.0) * phi
+        return torch.full_like(T, p.F)
+    om = torch.clamp(Y[p.sensor_species], min=0.0) * torch.clamp(Y[p.sensor_oxidizer], min=0.0) \
+        * torch.exp(-p.sensor_Ta / T)
+    return 1.0 + (p.F - 1.0) * torch.tanh(p.sensor_beta * om / p.sensor_wref)
 
 
 def fd_update(p, grid, nb, T, Y, u, uin_r, P_th, dP_lag):
@@ -83,7 +88,7 @@ def fd_update(p, grid, nb, T, Y, u, uin_r, P_th, dP_lag):
     rho = rho_phys / p.rho_ref
     q = reaction_rates(p, T, Y, rho_phys)
     om = [o.expand_as(T) for o in species_rates(p, q)]
-    Floc = thickening(p, om)
+    Floc = thickening(p, T, Y)
     mu = p.nu_lat * (T / p.T_ref) ** p.mu_exp
 
     fields = [T] + [Y[k] for k in range(p.K)]

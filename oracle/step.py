@@ -25,8 +25,17 @@ from .units import R_GAS, Params
 
 
 class Oracle:
-    def __init__(self, cfg, mask, inlet_u=None):
+    """FP64 oracle of the full step.
+
+    ``store_round`` (None, "f32" or "f16") rounds the state after every step to the storage
+    precision of a GPU configuration (populations in the shifted form (g - w P_ref) / w, fields
+    T, Y, u in FP32 for both): the arithmetic stays FP64, so the difference from the unrounded
+    oracle is the error floor that storage precision alone imposes.
+    """
+
+    def __init__(self, cfg, mask, inlet_u=None, store_round=None):
         self.cfg = cfg
+        self.store_round = store_round
         self.p = Params(cfg)
         self.lat = Lattice(cfg["dim"])
         self.cs = CumulantSpace(self.lat)
@@ -138,7 +147,20 @@ class Oracle:
         new["P_h"] = torch.where(fluid, P_h, st["P_h"])
         return new
 
+    def round_state(self, st):
+        if self.store_round is None:
+            return st
+        pop_t = torch.float16 if self.store_round == "f16" else torch.float32
+        P_ref = self.cfg.get("P_ref", 0.0)
+        w = self.lat.w[:, None]
+        out = dict(st)
+        out["g"] = w * ((st["g"] / w - P_ref).to(pop_t).to(torch.float64) + P_ref)
+        for k in ("T", "Y", "u"):
+            if k in st:
+                out[k] = st[k].to(torch.float32).to(torch.float64)
+        return out
+
     def run(self, st, n):
         for _ in range(n):
-            st = self.step(st)
+            st = self.round_state(self.step(st))
         return st

@@ -34,6 +34,8 @@ class Params:
         self.sensor_beta = cfg.get("sensor_beta", 10.0)
         self.sensor_wref = cfg.get("sensor_wref", 1.0)
         self.sensor_species = cfg.get("sensor_species", 0)
+        self.sensor_oxidizer = cfg.get("sensor_oxidizer", 1)
+        self.sensor_Ta = cfg.get("sensor_Ta", 8400.0)
         sp = cfg.get("species", [])
         self.K = len(sp)
         self.W = [s["W"] for s in sp]

@@ -1,0 +1,776 @@
+// C-ABI runtime of the library (declared in include/hlbm.h): configuration checks, unit
+// conversion, device state, the per-step launch sequence (FD -> thermodynamic pressure -> LB,
+// Section 2), CUDA-graph replay of step pairs, kernel timing and checkpoints.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/hlbm.h"
+#include "launch.h"
+
+using namespace hlbm;
+
+namespace {
+constexpr double R_GAS = 8.314462618;
+enum { KIND_FD = 0, KIND_SENSOR = 1, KIND_PTH = 2, KIND_LB = 3 };
+}  // namespace
+
+struct lbm_ctx {
+  lbm_config cfg;
+  std::string err;
+  int dev = 0;
+  int D = 2, Q = 9, K = 0;
+  size_t N = 0;
+  bool f64 = false;  // FP64 fields and arithmetic
+  size_t S = 4, F = 4;  // bytes per population / per field value
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  Geo geo{};
+  // device buffers
+  void* g[2] = {nullptr, nullptr};
+  void* T[2] = {nullptr, nullptr};
+  void* Y[2] = {nullptr, nullptr};
+  void* u = nullptr;
+  void* rho = nullptr;
+  void* lam = nullptr;
+  void* ph = nullptr;
+  void* Floc = nullptr;
+  uint32_t* links = nullptr;
+  uint8_t* mask = nullptr;
+  void* inlet_u = nullptr;
+  void* partials = nullptr;
+  int nblocks_fd = 0;
+  PthState* pth = nullptr;
+  int* flag = nullptr;
+  double* scratch_out = nullptr;  // staging for get_fields
+  size_t scratch_out_n = 0;
+  std::vector<void*> allocs;
+  // lattice-unit constants
+  FDConst<float> fdc_f{};
+  FDConst<double> fdc_d{};
+  PthUpdate pu{};
+  double nu_lat = 0, W_in = 0;
+  size_t n_fluid = 0;
+  int cur = 0;
+  long long steps = 0;
+  bool have_geo = false, have_fields = false;
+  // graphs
+  bool use_graphs = true;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // profiling
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+  double ms[LBM_KERNEL_KINDS] = {0, 0, 0, 0};
+  long long cnt[LBM_KERNEL_KINDS] = {0, 0, 0, 0};
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* c, lbm_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                               \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+void* dalloc(lbm_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (c->cfg.alloc) {
+    p = c->cfg.alloc(bytes, c->cfg.alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c->allocs.push_back(p);
+  return p;
+}
+
+void dfree_all(lbm_ctx* c) {
+  for (void* p : c->allocs) {
+    if (c->cfg.free) c->cfg.free(p, c->cfg.alloc_user);
+    else cudaFree(p);
+  }
+  c->allocs.clear();
+}
+
+void drop_graphs(lbm_ctx* c) {
+  for (auto& ge : c->gexec)
+    if (ge) {
+      cudaGraphExecDestroy(ge);
+      ge = nullptr;
+    }
+}
+
+lbm_status validate(const lbm_config* cfg, std::string& msg) {
+  auto bad = [&](const char* m) {
+    msg = m;
+    return LBM_ERR_ARG;
+  };
+  if (cfg->dim != 2 && cfg->dim != 3) return bad("dim must be 2 or 3");
+  if (cfg->nx < 1 || cfg->ny < 1 || (cfg->dim == 3 && cfg->nz < 1)) return bad("grid sizes must be >= 1");
+  const double N = (double)cfg->nx * cfg->ny * (cfg->dim == 3 ? cfg->nz : 1);
+  if (N * (cfg->dim == 2 ? 9 : 27) > 2147483000.0) return bad("Q * cells must stay below 2^31");
+  if (cfg->storage < LBM_STORE_F64 || cfg->storage > LBM_STORE_F16) return bad("unknown storage");
+  if (cfg->collision != LBM_COLL_BGK && cfg->collision != LBM_COLL_CUMULANT) return bad("unknown collision");
+  for (int a = 0; a < cfg->dim; ++a) {
+    const int lo = cfg->bc_lo[a], hi = cfg->bc_hi[a];
+    if (lo < 0 || lo > 3 || hi < 0 || hi > 3) return bad("unknown boundary code");
+    if (lo == LBM_BC_OUTLET || hi == LBM_BC_INLET) return bad("inlet only on low x, outlet only on high x");
+    if (a > 0 && (lo >= LBM_BC_INLET || hi >= LBM_BC_INLET)) return bad("inlet/outlet only on the x faces");
+    if ((lo == LBM_BC_PERIODIC) != (hi == LBM_BC_PERIODIC)) return bad("periodic must pair with periodic");
+  }
+  if (!(cfg->dx > 0) || !(cfg->dt > 0) || !(cfg->nu_ref > 0)) return bad("dx, dt, nu_ref must be > 0");
+  if (cfg->smag_cs < 0) return bad("smag_cs must be >= 0");
+  if (cfg->thermal) {
+    if (cfg->n_species < 1 || cfg->n_species > LBM_MAX_SPECIES) return bad("thermal needs 1..8 species");
+    if (cfg->n_reactions < 0 || cfg->n_reactions > LBM_MAX_REACTIONS) return bad("at most 4 reactions");
+    if (!(cfg->P_th0 > 0) || !(cfg->T_ref > 0) || !(cfg->cp > 0) || !(cfg->rho_ref > 0) || !(cfg->Pr > 0))
+      return bad("P_th0, T_ref, cp, rho_ref, Pr must be > 0");
+    for (int k = 0; k < cfg->n_species; ++k)
+      if (!(cfg->sp[k].W > 0) || !(cfg->sp[k].Le > 0)) return bad("species W and Le must be > 0");
+    if (cfg->flame_sensor && (cfg->sensor_species < 0 || cfg->sensor_species >= cfg->n_species ||
+                              cfg->sensor_oxidizer < 0 || cfg->sensor_oxidizer >= cfg->n_species ||
+                              !(cfg->sensor_wref > 0) || !(cfg->sensor_Ta >= 0)))
+      return bad("invalid flame sensor parameters");
+    if (!(cfg->thicken_F >= 1.0)) return bad("thicken_F must be >= 1");
+  } else if (cfg->closed_domain || cfg->flame_sensor) {
+    return bad("closed_domain and flame_sensor need thermal");
+  }
+  return LBM_OK;
+}
+
+template <typename R> LBArgs<R> make_lb_args(lbm_ctx* c, int cur, bool want_out) {
+  LBArgs<R> a{};
+  a.geo = c->geo;
+  a.g_in = c->g[cur];
+  a.g_out = c->g[1 - cur];
+  a.links = c->links;
+  a.rho = (const R*)c->rho;
+  a.lam = (const R*)c->lam;
+  a.T = (const R*)c->T[cur];
+  a.inlet_u = (const R*)c->inlet_u;
+  a.u = (R*)c->u;
+  a.write_u = (c->cfg.thermal || want_out) ? 1 : 0;
+  a.ph_out = want_out ? (R*)c->ph : nullptr;
+  a.pth = c->pth;
+  a.flag = c->flag;
+  a.nu_lat = (R)c->nu_lat;
+  a.T_ref_inv = (R)(1.0 / c->cfg.T_ref);
+  a.mu_exp = (R)c->cfg.mu_exp;
+  a.smag_k = (R)(18.0 * std::sqrt(2.0) * c->cfg.smag_cs * c->cfg.smag_cs);
+  a.omega_b = (R)c->cfg.omega_bulk;
+  a.om3 = (R)c->cfg.omega_hi[0];
+  a.om4 = (R)c->cfg.omega_hi[1];
+  a.om5 = (R)c->cfg.omega_hi[2];
+  a.om6 = (R)c->cfg.omega_hi[3];
+  a.P_ref = (R)c->cfg.P_ref;
+  return a;
+}
+
+template <typename R> const FDConst<R>& fdconst(const lbm_ctx* c);
+template <> const FDConst<float>& fdconst<float>(const lbm_ctx* c) { return c->fdc_f; }
+template <> const FDConst<double>& fdconst<double>(const lbm_ctx* c) { return c->fdc_d; }
+
+// Lattice-unit constants of the finite-difference update in the arithmetic type R.
+template <typename R> void fill_fdconst(FDConst<R>& f, const lbm_config& c, int K, double nu_lat, double I_unit) {
+  f.K = K;
+  f.nrx = c.thermal ? c.n_reactions : 0;
+  f.sensor = c.flame_sensor;
+  f.sensor_species = c.sensor_species;
+  f.sensor_oxidizer = c.sensor_oxidizer;
+  f.sensor_Ta = (R)c.sensor_Ta;
+  f.closed = c.closed_domain;
+  f.nu_lat = (R)nu_lat;
+  f.T_ref_inv = (R)(1.0 / c.T_ref);
+  f.mu_exp = (R)c.mu_exp;
+  f.inv_Pr = (R)(1.0 / c.Pr);
+  f.dt_phys = (R)c.dt;
+  f.inv_cp = (R)(1.0 / c.cp);
+  f.inv_rho_ref = (R)(1.0 / c.rho_ref);
+  f.F = (R)c.thicken_F;
+  f.sensor_beta = (R)c.sensor_beta;
+  f.inv_wref = (R)(c.sensor_wref > 0 ? 1.0 / c.sensor_wref : 0.0);
+  f.eps_T = (R)(1e-6 * c.T_ref * c.T_ref);
+  f.eps_Y = (R)1e-6;
+  f.T_in = (R)c.T_in;
+  for (int k = 0; k < K; ++k) {
+    f.inv_Le[k] = (R)(1.0 / c.sp[k].Le);
+    f.inv_W[k] = (R)(1.0 / c.sp[k].W);
+    f.W[k] = (R)c.sp[k].W;
+    f.hf_W[k] = (R)(c.sp[k].hf * c.sp[k].W);
+    f.Y_in[k] = (R)c.Y_in[k];
+  }
+  for (int j = 0; j < f.nrx; ++j) {
+    const lbm_reaction& rx = c.rx[j];
+    f.A[j] = (R)rx.A;
+    f.beta[j] = (R)rx.beta;
+    const double ER = rx.E / R_GAS;
+    f.ER_hi[j] = (R)ER;
+    f.ER_lo[j] = (R)(ER - (double)f.ER_hi[j]);
+    for (int k = 0; k < K; ++k) {
+      f.nu[j][k] = (R)rx.nu[k];
+      f.order[j][k] = (R)rx.order[k];
+    }
+  }
+  f.I_scale = (R)I_unit;
+  f.M_scale = (R)16.0;
+}
+
+template <typename R> FDArgs<R> make_fd_args(lbm_ctx* c, int cur) {
+  FDArgs<R> a{};
+  a.geo = c->geo;
+  a.mask = c->mask;
+  a.T = (const R*)c->T[cur];
+  a.Y = (const R*)c->Y[cur];
+  a.T_out = (R*)c->T[1 - cur];
+  a.Y_out = (R*)c->Y[1 - cur];
+  a.u = (const R*)c->u;
+  a.inlet_u = (const R*)c->inlet_u;
+  a.Floc = c->cfg.flame_sensor ? (R*)c->Floc : nullptr;
+  a.rho_out = (R*)c->rho;
+  a.lam_out = (R*)c->lam;
+  a.partials = c->partials;
+  a.pth = c->pth;
+  a.c = fdconst<R>(c);
+  return a;
+}
+
+cudaError_t run_lb(lbm_ctx* c, int cur, bool want_out) {
+  const int th = c->cfg.thermal, co = c->cfg.collision;
+  if (c->f64) {
+    auto a = make_lb_args<double>(c, cur, want_out);
+    return c->D == 2 ? launch_lb<2, double, double>(a, th, co, c->st) : launch_lb<3, double, double>(a, th, co, c->st);
+  }
+  auto a = make_lb_args<float>(c, cur, want_out);
+  if (c->cfg.storage == LBM_STORE_F16)
+    return c->D == 2 ? launch_lb<2, __half, float>(a, th, co, c->st) : launch_lb<3, __half, float>(a, th, co, c->st);
+  return c->D == 2 ? launch_lb<2, float, float>(a, th, co, c->st) : launch_lb<3, float, float>(a, th, co, c->st);
+}
+
+cudaError_t run_fd(lbm_ctx* c, int cur, bool sensor_pass) {
+  if (c->f64) {
+    auto a = make_fd_args<double>(c, cur);
+    return c->D == 2 ? launch_fd<2, double>(a, c->st, sensor_pass) : launch_fd<3, double>(a, c->st, sensor_pass);
+  }
+  auto a = make_fd_args<float>(c, cur);
+  return c->D == 2 ? launch_fd<2, float>(a, c->st, sensor_pass) : launch_fd<3, float>(a, c->st, sensor_pass);
+}
+
+cudaError_t timed(lbm_ctx* c, int kind, cudaError_t (*fn)(lbm_ctx*, int, int), int cur, int arg) {
+  if (!c->prof) return fn(c, cur, arg);
+  cudaEvent_t e0, e1;
+  if (c->ev_pool.size() >= 2) {
+    e0 = c->ev_pool.back(); c->ev_pool.pop_back();
+    e1 = c->ev_pool.back(); c->ev_pool.pop_back();
+  } else {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+  }
+  cudaEventRecord(e0, c->st);
+  cudaError_t e = fn(c, cur, arg);
+  cudaEventRecord(e1, c->st);
+  c->ev_used.push_back({kind, {e0, e1}});
+  return e;
+}
+
+cudaError_t fd_thunk(lbm_ctx* c, int cur, int sensor) { return run_fd(c, cur, sensor != 0); }
+cudaError_t lb_thunk(lbm_ctx* c, int cur, int want) { return run_lb(c, cur, want != 0); }
+cudaError_t pth_thunk(lbm_ctx* c, int, int) {
+  return launch_pth_update(c->pu, c->partials, c->nblocks_fd, c->pth, 0, c->st);
+}
+
+// One full step from parity `cur`: FD (+ sensor) -> P_th -> LB.
+cudaError_t enqueue_step(lbm_ctx* c, int cur, bool want_out) {
+  cudaError_t e;
+  if (c->cfg.thermal) {
+    if (c->cfg.flame_sensor && (e = timed(c, KIND_SENSOR, fd_thunk, cur, 1)) != cudaSuccess) return e;
+    if ((e = timed(c, KIND_FD, fd_thunk, cur, 0)) != cudaSuccess) return e;
+    if (c->cfg.closed_domain && (e = timed(c, KIND_PTH, pth_thunk, cur, 0)) != cudaSuccess) return e;
+  }
+  return timed(c, KIND_LB, lb_thunk, cur, want_out ? 1 : 0);
+}
+
+cudaError_t build_graph(lbm_ctx* c, int cur) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t e1 = enqueue_step(c, cur, false);
+  cudaError_t e2 = e1 == cudaSuccess ? enqueue_step(c, 1 - cur, false) : e1;
+  e = cudaStreamEndCapture(c->st, &graph);
+  if (e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return e2;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(&c->gexec[cur], graph, 0);
+  cudaGraphDestroy(graph);
+  return e;
+}
+
+size_t fields_size(const lbm_ctx* c, unsigned bits) {
+  size_t n = 0;
+  if (bits & LBM_F_T) n += c->N;
+  if (bits & LBM_F_Y) n += (size_t)c->K * c->N;
+  if (bits & LBM_F_U) n += (size_t)c->D * c->N;
+  if (bits & LBM_F_PH) n += c->N;
+  if (bits & LBM_F_RHO) n += c->N;
+  if (bits & LBM_F_LAM) n += c->N;
+  if (bits & LBM_F_G) n += (size_t)c->Q * c->N;
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
+  if (!cfg || !out) return LBM_ERR_ARG;
+  *out = nullptr;
+  std::string msg;
+  lbm_status s = validate(cfg, msg);
+  lbm_ctx* ctx = new (std::nothrow) lbm_ctx();
+  if (!ctx) return LBM_ERR_ALLOC;
+  ctx->cfg = *cfg;
+  *out = ctx;
+  if (s != LBM_OK) return fail(ctx, s, msg);
+  lbm_config& c = ctx->cfg;
+  if (c.dim == 2) c.nz = 1;
+  CK(cudaGetDevice(&ctx->dev), "cudaGetDevice");
+  ctx->st = (cudaStream_t)c.stream;
+  if (!ctx->st) {
+    // graph capture needs a stream other than the legacy default stream; a blocking stream
+    // still orders itself with the legacy default stream
+    CK(cudaStreamCreate(&ctx->st), "cudaStreamCreate");
+    ctx->own_stream = true;
+  }
+  ctx->D = c.dim;
+  ctx->Q = c.dim == 2 ? 9 : 27;
+  ctx->K = c.thermal ? c.n_species : 0;
+  ctx->N = (size_t)c.nx * c.ny * c.nz;
+  ctx->f64 = c.storage == LBM_STORE_F64;
+  ctx->S = c.storage == LBM_STORE_F64 ? 8 : (c.storage == LBM_STORE_F32 ? 4 : 2);
+  ctx->F = ctx->f64 ? 8 : 4;
+  Geo& g = ctx->geo;
+  g.nx = c.nx;
+  g.ny = c.ny;
+  g.nz = c.nz;
+  g.N = (int)ctx->N;
+  for (int a = 0; a < 3; ++a) {
+    g.bc_lo[a] = a < c.dim ? c.bc_lo[a] : BC_PERIODIC;
+    g.bc_hi[a] = a < c.dim ? c.bc_hi[a] : BC_PERIODIC;
+  }
+  // lattice units: nu_lat = nu dt / dx^2, tau = nu_lat / cs2 + 1/2 (Eq. 12)
+  ctx->nu_lat = c.nu_ref * c.dt / (c.dx * c.dx);
+  double sWin = 0.0;
+  for (int k = 0; k < ctx->K; ++k) sWin += c.Y_in[k] / c.sp[k].W;
+  ctx->W_in = sWin > 0 ? 1.0 / sWin : 0.0;
+  // reduction scale: the integrand W / (R T rho_ref) ~ 1e-5 is computed as I_unit * W / T ~ 1
+  const double I_unit = c.T_ref / 0.029;
+  fill_fdconst<float>(ctx->fdc_f, c, ctx->K, ctx->nu_lat, I_unit);
+  fill_fdconst<double>(ctx->fdc_d, c, ctx->K, ctx->nu_lat, I_unit);
+  PthUpdate& pu = ctx->pu;
+  // I = sum(I_unit W/T) / I_s with I_s = I_unit R rho_ref, using the exact scale of the kernels
+  pu.I_s = (ctx->f64 ? (double)ctx->fdc_d.I_scale : (double)ctx->fdc_f.I_scale) * R_GAS * c.rho_ref;
+  pu.M_s = 16.0;
+  pu.R_rho_ref = R_GAS * c.rho_ref;
+  pu.cp_rho_ref = c.cp * c.rho_ref;
+  pu.rin_fac = c.thermal ? ctx->W_in / (R_GAS * c.T_in * c.rho_ref) : 0.0;
+  pu.fixed_point = ctx->f64 ? 0 : 1;
+
+  // device state
+  const size_t N = ctx->N;
+  bool ok = true;
+  for (int b = 0; b < 2; ++b) ok = ok && (ctx->g[b] = dalloc(ctx, (size_t)ctx->Q * N * ctx->S));
+  ok = ok && (ctx->u = dalloc(ctx, (size_t)ctx->D * N * ctx->F));
+  ok = ok && (ctx->rho = dalloc(ctx, N * ctx->F));
+  ok = ok && (ctx->lam = dalloc(ctx, N * ctx->F));
+  ok = ok && (ctx->ph = dalloc(ctx, N * ctx->F));
+  ok = ok && (ctx->links = (uint32_t*)dalloc(ctx, N * 4));
+  ok = ok && (ctx->mask = (uint8_t*)dalloc(ctx, N));
+  ok = ok && (ctx->inlet_u = dalloc(ctx, (size_t)ctx->D * c.ny * c.nz * ctx->F));
+  ok = ok && (ctx->pth = (PthState*)dalloc(ctx, sizeof(PthState)));
+  ok = ok && (ctx->flag = (int*)dalloc(ctx, 16));
+  ctx->nblocks_fd = (int)((N + FD_BLOCK - 1) / FD_BLOCK);
+  ok = ok && (ctx->partials = dalloc(ctx, (size_t)ctx->nblocks_fd * 16));
+  if (c.thermal) {
+    for (int b = 0; b < 2; ++b) {
+      ok = ok && (ctx->T[b] = dalloc(ctx, N * ctx->F));
+      ok = ok && (ctx->Y[b] = dalloc(ctx, (size_t)ctx->K * N * ctx->F));
+    }
+    if (c.flame_sensor) ok = ok && (ctx->Floc = dalloc(ctx, N * ctx->F));
+  }
+  if (!ok) {
+    dfree_all(ctx);
+    return fail(ctx, LBM_ERR_ALLOC, "device allocation failed");
+  }
+  CK(cudaMemsetAsync(ctx->flag, 0, 16, ctx->st), "memset");
+  CK(cudaMemsetAsync(ctx->inlet_u, 0, (size_t)ctx->D * c.ny * c.nz * ctx->F, ctx->st), "memset");
+  if (ctx->Floc) CK(cudaMemsetAsync(ctx->Floc, 0, N * ctx->F, ctx->st), "memset");
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->dev);
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  else cudaDeviceSynchronize();
+  drop_graphs(ctx);
+  for (auto& e : ctx->ev_used) {
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  dfree_all(ctx);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->st);
+  delete ctx;
+}
+
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* mask, const double* inlet_u, int on_device) {
+  if (!ctx || !mask) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (ctx->allocs.empty()) return fail(ctx, LBM_ERR_STATE, "context not initialised");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  const size_t N = ctx->N;
+  const auto kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(ctx->mask, mask, N, kind, ctx->st), "copy mask");
+  const size_t nf = (size_t)ctx->cfg.ny * ctx->cfg.nz;
+  if (inlet_u) {
+    // convert the face velocities to the field type on the device
+    double* tmp = (double*)dalloc(ctx, ctx->D * nf * 8);
+    if (!tmp) return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+    CK(cudaMemcpyAsync(tmp, inlet_u, ctx->D * nf * 8, kind, ctx->st), "copy inlet");
+    if (ctx->f64) {
+      CK(cudaMemcpyAsync(ctx->inlet_u, tmp, ctx->D * nf * 8, cudaMemcpyDeviceToDevice, ctx->st), "copy inlet");
+    } else {
+      std::vector<double> h(ctx->D * nf);
+      std::vector<float> hf(ctx->D * nf);
+      CK(cudaMemcpyAsync(h.data(), tmp, ctx->D * nf * 8, cudaMemcpyDeviceToHost, ctx->st), "copy inlet");
+      CK(cudaStreamSynchronize(ctx->st), "sync");
+      for (size_t i = 0; i < h.size(); ++i) hf[i] = (float)h[i];
+      CK(cudaMemcpyAsync(ctx->inlet_u, hf.data(), ctx->D * nf * 4, cudaMemcpyHostToDevice, ctx->st), "copy inlet");
+      CK(cudaStreamSynchronize(ctx->st), "sync");
+    }
+    CK(cudaStreamSynchronize(ctx->st), "sync");
+    // release the staging buffer
+    ctx->allocs.pop_back();
+    if (ctx->cfg.free) ctx->cfg.free(tmp, ctx->cfg.alloc_user);
+    else cudaFree(tmp);
+  }
+  CK(launch_links(ctx->D, ctx->geo, ctx->mask, ctx->links, ctx->st), "links kernel");
+  std::vector<uint8_t> hm(N);
+  CK(cudaMemcpyAsync(hm.data(), ctx->mask, N, cudaMemcpyDeviceToHost, ctx->st), "copy mask");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  size_t nfl = 0;
+  for (size_t i = 0; i < N; ++i) nfl += hm[i] == 0;
+  ctx->n_fluid = nfl;
+  ctx->have_geo = true;
+  drop_graphs(ctx);
+  return LBM_OK;
+}
+
+lbm_status lbm_set_fields(lbm_ctx* ctx, const double* T, const double* Y, const double* u, const double* P_h,
+                          const double* g_pert, int on_device) {
+  if (!ctx || !u || !P_h) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->have_geo) return fail(ctx, LBM_ERR_STATE, "set_geometry must come first");
+  const lbm_config& c = ctx->cfg;
+  if (c.thermal && (!T || !Y)) return fail(ctx, LBM_ERR_ARG, "thermal run needs T and Y");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  const size_t N = ctx->N, K = ctx->K, D = ctx->D, Q = ctx->Q;
+  // stage all double inputs in one device buffer
+  const size_t nT = c.thermal ? N : 0, nY = c.thermal ? K * N : 0, nG = g_pert ? Q * N : 0;
+  const size_t total = nT + nY + D * N + N + nG + 8;
+  double* buf = (double*)dalloc(ctx, total * 8);
+  if (!buf) return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+  double *dT = buf, *dY = dT + nT, *du = dY + nY, *dP = du + D * N, *dG = dP + N, *dW = dG + nG;
+  const auto kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  lbm_status st = LBM_OK;
+  auto cp = [&](double* dst, const double* src, size_t n) {
+    if (st == LBM_OK && n) {
+      cudaError_t e = cudaMemcpyAsync(dst, src, n * 8, kind, ctx->st);
+      if (e != cudaSuccess) st = cuda_fail(ctx, e, "copy fields");
+    }
+  };
+  cp(dT, T, nT);
+  cp(dY, Y, nY);
+  cp(du, u, D * N);
+  cp(dP, P_h, N);
+  cp(dG, g_pert, nG);
+  double invW[LBM_MAX_SPECIES] = {0};
+  for (size_t k = 0; k < K; ++k) invW[k] = 1.0 / c.sp[k].W;
+  if (st == LBM_OK) {
+    cudaError_t e = cudaMemcpyAsync(dW, invW, 8 * LBM_MAX_SPECIES, cudaMemcpyHostToDevice, ctx->st);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "copy");
+  }
+  const double p_fac = c.thermal ? c.P_th0 / (R_GAS * c.rho_ref) : 0.0;
+  if (st == LBM_OK) {
+    cudaError_t e;
+    const int cur = 0;
+    if (ctx->f64)
+      e = launch_set_fields<double, double>(ctx->D, ctx->geo, dT, dY, (int)K, dW, du, dP, g_pert ? dG : nullptr,
+                                            p_fac, c.P_ref, c.thermal, (double*)ctx->g[cur], (double*)ctx->T[cur],
+                                            (double*)ctx->Y[cur], (double*)ctx->u, (double*)ctx->rho,
+                                            (double*)ctx->lam, (double*)ctx->ph, ctx->st);
+    else if (c.storage == LBM_STORE_F16)
+      e = launch_set_fields<__half, float>(ctx->D, ctx->geo, dT, dY, (int)K, dW, du, dP, g_pert ? dG : nullptr,
+                                           p_fac, c.P_ref, c.thermal, (__half*)ctx->g[cur], (float*)ctx->T[cur],
+                                           (float*)ctx->Y[cur], (float*)ctx->u, (float*)ctx->rho,
+                                           (float*)ctx->lam, (float*)ctx->ph, ctx->st);
+    else
+      e = launch_set_fields<float, float>(ctx->D, ctx->geo, dT, dY, (int)K, dW, du, dP, g_pert ? dG : nullptr,
+                                          p_fac, c.P_ref, c.thermal, (float*)ctx->g[cur], (float*)ctx->T[cur],
+                                          (float*)ctx->Y[cur], (float*)ctx->u, (float*)ctx->rho,
+                                          (float*)ctx->lam, (float*)ctx->ph, ctx->st);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "set_fields kernel");
+  }
+  // thermodynamic-pressure state: P = P_th0, M = P_th0 * I0 (same arithmetic as every step)
+  PthState ps{};
+  ps.P = c.P_th0;
+  ps.fd_rho_d = c.thermal ? c.P_th0 / (R_GAS * c.rho_ref) : 0.0;
+  ps.rho_in_d = c.P_th0 * ctx->pu.rin_fac;
+  ps.fd_rho = (float)ps.fd_rho_d;
+  ps.rho_in = (float)ps.rho_in_d;
+  if (st == LBM_OK) {
+    cudaError_t e = cudaMemcpyAsync(ctx->pth, &ps, sizeof(ps), cudaMemcpyHostToDevice, ctx->st);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "copy");
+  }
+  if (st == LBM_OK && c.thermal && c.closed_domain) {
+    cudaError_t e = ctx->f64
+        ? launch_init_integral<double>(ctx->geo, ctx->mask, (const double*)ctx->T[0], (const double*)ctx->Y[0],
+                                       ctx->fdc_d, ctx->partials, ctx->nblocks_fd, ctx->st)
+        : launch_init_integral<float>(ctx->geo, ctx->mask, (const float*)ctx->T[0], (const float*)ctx->Y[0],
+                                      ctx->fdc_f, ctx->partials, ctx->nblocks_fd, ctx->st);
+    if (e == cudaSuccess) e = launch_pth_update(ctx->pu, ctx->partials, ctx->nblocks_fd, ctx->pth, 1, ctx->st);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "initial integral");
+  }
+  cudaError_t e = cudaStreamSynchronize(ctx->st);
+  if (st == LBM_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "sync");
+  // release the staging buffer
+  for (size_t i = 0; i < ctx->allocs.size(); ++i)
+    if (ctx->allocs[i] == buf) {
+      ctx->allocs.erase(ctx->allocs.begin() + i);
+      break;
+    }
+  if (ctx->cfg.free) ctx->cfg.free(buf, ctx->cfg.alloc_user);
+  else cudaFree(buf);
+  if (st != LBM_OK) return st;
+  ctx->cur = 0;
+  ctx->steps = 0;
+  ctx->have_fields = true;
+  CK(cudaMemsetAsync(ctx->flag, 0, 16, ctx->st), "memset");
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (n_steps < 0) return fail(ctx, LBM_ERR_ARG, "n_steps must be >= 0");
+  if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "set_fields must come first");
+  if (n_steps == 0) return LBM_OK;
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  int left = n_steps - 1;  // the last step also writes the output-only fields
+  if (ctx->use_graphs && !ctx->prof) {
+    while (left >= 2) {
+      if (!ctx->gexec[ctx->cur]) CK(build_graph(ctx, ctx->cur), "graph capture");
+      CK(cudaGraphLaunch(ctx->gexec[ctx->cur], ctx->st), "graph launch");
+      left -= 2;
+      ctx->steps += 2;
+    }
+  }
+  while (left > 0) {
+    CK(enqueue_step(ctx, ctx->cur, false), "step launch");
+    ctx->cur ^= 1;
+    --left;
+    ++ctx->steps;
+  }
+  CK(enqueue_step(ctx, ctx->cur, true), "step launch");
+  ctx->cur ^= 1;
+  ++ctx->steps;
+  return LBM_OK;
+}
+
+size_t lbm_fields_size(const lbm_ctx* ctx, unsigned bits) { return ctx ? fields_size(ctx, bits) : 0; }
+
+lbm_status lbm_get_fields(lbm_ctx* ctx, unsigned bits, double* dst, int dst_on_device) {
+  if (!ctx || !dst) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "no fields");
+  if (!ctx->cfg.thermal && (bits & (LBM_F_T | LBM_F_Y | LBM_F_RHO | LBM_F_LAM)))
+    return fail(ctx, LBM_ERR_ARG, "T, Y, rho, Lambda need a thermal run");
+  if (bits & ~127u) return fail(ctx, LBM_ERR_ARG, "unknown field bits");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  const size_t n = fields_size(ctx, bits);
+  if (n == 0) return LBM_OK;
+  double* out = dst;
+  if (!dst_on_device) {
+    if (ctx->scratch_out_n < n) {
+      double* p = (double*)dalloc(ctx, n * 8);
+      if (!p) return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+      ctx->scratch_out = p;
+      ctx->scratch_out_n = n;
+    }
+    out = ctx->scratch_out;
+  }
+  const int cur = ctx->cur;
+  cudaError_t e;
+  if (ctx->f64)
+    e = launch_get_fields<double, double>(ctx->D, ctx->geo, bits, ctx->K, (const double*)ctx->g[cur],
+                                          (const double*)ctx->T[cur], (const double*)ctx->Y[cur],
+                                          (const double*)ctx->u, (const double*)ctx->ph, (const double*)ctx->rho,
+                                          (const double*)ctx->lam, ctx->pth, ctx->cfg.P_ref, out, ctx->st);
+  else if (ctx->cfg.storage == LBM_STORE_F16)
+    e = launch_get_fields<__half, float>(ctx->D, ctx->geo, bits, ctx->K, (const __half*)ctx->g[cur],
+                                         (const float*)ctx->T[cur], (const float*)ctx->Y[cur], (const float*)ctx->u,
+                                         (const float*)ctx->ph, (const float*)ctx->rho, (const float*)ctx->lam,
+                                         ctx->pth, ctx->cfg.P_ref, out, ctx->st);
+  else
+    e = launch_get_fields<float, float>(ctx->D, ctx->geo, bits, ctx->K, (const float*)ctx->g[cur],
+                                        (const float*)ctx->T[cur], (const float*)ctx->Y[cur], (const float*)ctx->u,
+                                        (const float*)ctx->ph, (const float*)ctx->rho, (const float*)ctx->lam,
+                                        ctx->pth, ctx->cfg.P_ref, out, ctx->st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "get_fields kernel");
+  if (!dst_on_device) CK(cudaMemcpyAsync(dst, out, n * 8, cudaMemcpyDeviceToHost, ctx->st), "copy out");
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, ctx->flag, 4, cudaMemcpyDeviceToHost, ctx->st), "copy flag");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  if (flag) {
+    CK(cudaMemsetAsync(ctx->flag, 0, 4, ctx->st), "memset");
+    return fail(ctx, LBM_ERR_NONFINITE, "a step produced a non-finite velocity");
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_scalars(lbm_ctx* ctx, double out[4]) {
+  if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "no fields");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  PthState ps;
+  CK(cudaMemcpyAsync(&ps, ctx->pth, sizeof(ps), cudaMemcpyDeviceToHost, ctx->st), "copy");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  out[0] = ps.P;
+  out[1] = ps.dP;
+  out[2] = ps.M;
+  out[3] = (double)ctx->steps;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_links(lbm_ctx* ctx, uint32_t* dst, int dst_on_device) {
+  if (!ctx || !dst) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->have_geo) return fail(ctx, LBM_ERR_STATE, "no geometry");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  CK(cudaMemcpyAsync(dst, ctx->links, ctx->N * 4, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     ctx->st), "copy links");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  return LBM_OK;
+}
+
+size_t lbm_state_bytes(const lbm_ctx* ctx) {
+  if (!ctx) return 0;
+  const size_t N = ctx->N;
+  size_t b = (size_t)ctx->Q * N * ctx->S + (size_t)ctx->D * N * ctx->F + sizeof(PthState);
+  if (ctx->cfg.thermal) b += (1 + (size_t)ctx->K) * N * ctx->F;
+  return b;
+}
+
+static lbm_status copy_state(lbm_ctx* ctx, char* dev, bool save) {
+  const size_t N = ctx->N;
+  auto mv = [&](void* state, size_t bytes) -> cudaError_t {
+    cudaError_t e = save ? cudaMemcpyAsync(dev, state, bytes, cudaMemcpyDeviceToDevice, ctx->st)
+                         : cudaMemcpyAsync(state, dev, bytes, cudaMemcpyDeviceToDevice, ctx->st);
+    dev += bytes;
+    return e;
+  };
+  const int cur = ctx->cur;
+  CK(mv(ctx->g[cur], (size_t)ctx->Q * N * ctx->S), "copy state");
+  CK(mv(ctx->u, (size_t)ctx->D * N * ctx->F), "copy state");
+  if (ctx->cfg.thermal) {
+    CK(mv(ctx->T[cur], N * ctx->F), "copy state");
+    CK(mv(ctx->Y[cur], (size_t)ctx->K * N * ctx->F), "copy state");
+  }
+  CK(mv(ctx->pth, sizeof(PthState)), "copy state");
+  return LBM_OK;
+}
+
+lbm_status lbm_save_state(lbm_ctx* ctx, void* dst_device) {
+  if (!ctx || !dst_device) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "no fields");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  return copy_state(ctx, (char*)dst_device, true);
+}
+
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* src_device) {
+  if (!ctx || !src_device) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "set_fields must come first");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  return copy_state(ctx, (char*)src_device, false);
+}
+
+lbm_status lbm_profile(lbm_ctx* ctx, int enable) {
+  if (!ctx) return LBM_ERR_ARG;
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  for (auto& e : ctx->ev_used) {
+    ctx->ev_pool.push_back(e.second.first);
+    ctx->ev_pool.push_back(e.second.second);
+  }
+  ctx->ev_used.clear();
+  for (int k = 0; k < LBM_KERNEL_KINDS; ++k) {
+    ctx->ms[k] = 0;
+    ctx->cnt[k] = 0;
+  }
+  ctx->prof = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_kernel_times(lbm_ctx* ctx, double ms[LBM_KERNEL_KINDS], long long launches[LBM_KERNEL_KINDS]) {
+  if (!ctx || !ms || !launches) return fail(ctx, LBM_ERR_ARG, "null argument");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  for (auto& e : ctx->ev_used) {
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, e.second.first, e.second.second), "event time");
+    ctx->ms[e.first] += t;
+    ctx->cnt[e.first] += 1;
+    ctx->ev_pool.push_back(e.second.first);
+    ctx->ev_pool.push_back(e.second.second);
+  }
+  ctx->ev_used.clear();
+  for (int k = 0; k < LBM_KERNEL_KINDS; ++k) {
+    ms[k] = ctx->ms[k];
+    launches[k] = ctx->cnt[k];
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_kernel_bytes(const lbm_ctx* ctx, double bytes[LBM_KERNEL_KINDS]) {
+  if (!ctx || !bytes) return LBM_ERR_ARG;
+  const double N = (double)ctx->N, Nf = (double)ctx->n_fluid, S = (double)ctx->S, F = (double)ctx->F;
+  const double K = ctx->K, D = ctx->D, Q = ctx->Q;
+  const bool th = ctx->cfg.thermal;
+  // FD: read T, Y, u; write T, Y, rho, Lambda; mask per cell; flame factor when the sensor is on
+  bytes[KIND_FD] = th ? Nf * ((2.0 * (1 + K) + D + 2.0 + (ctx->cfg.flame_sensor ? 1.0 : 0.0)) * F) + N : 0.0;
+  bytes[KIND_SENSOR] = (th && ctx->cfg.flame_sensor) ? Nf * 4.0 * F + N : 0.0;
+  bytes[KIND_PTH] = (th && ctx->cfg.closed_domain) ? 16.0 * ctx->nblocks_fd : 0.0;
+  // LB: populations read + written, link word, and (thermal) rho, Lambda, T read + u written
+  bytes[KIND_LB] = Nf * (2.0 * Q * S + (th ? (3.0 + D) * F : 0.0)) + 4.0 * N;
+  return LBM_OK;
+}
+
+lbm_status lbm_use_graphs(lbm_ctx* ctx, int enable) {
+  if (!ctx) return LBM_ERR_ARG;
+  ctx->use_graphs = enable != 0;
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,276 @@
+// Set-up, output and reduction kernels: boundary link words, initial equilibrium populations
+// (Eq. 6), field output, and the thermodynamic-pressure update.
+#include "launch.h"
+
+namespace hlbm {
+
+namespace {
+
+// Link word of one cell: bit i set when the source r - c_i of direction i is a solid cell, lies
+// beyond a wall face, the low-x inlet or the high-x outlet (any link that is not a plain pull);
+// bit 31 marks a fluid cell; 0 for a solid cell.
+__global__ void links_kernel(int D, Geo g, const uint8_t* __restrict__ mask, uint32_t* __restrict__ out) {
+  const int r = blockIdx.x * AUX_BLOCK + threadIdx.x;
+  if (r >= g.N) return;
+  if (mask[r]) {
+    out[r] = 0u;
+    return;
+  }
+  const int x = r % g.nx, t = r / g.nx, y = t % g.ny, z = t / g.ny;
+  const int pos[3] = {x, y, z};
+  const int dims[3] = {g.nx, g.ny, g.nz};
+  const int Q = D == 2 ? 9 : 27;
+  uint32_t word = 1u << 31;
+  for (int i = 0; i < Q; ++i) {
+    const int c[3] = {cx(i), cy(i), D == 3 ? cz(i) : 0};
+    bool inlet = false, outlet = false, wall = false;
+    int s[3];
+    for (int a = 0; a < 3; ++a) {
+      if (a >= D) {
+        s[a] = 0;
+        continue;
+      }
+      const int n = dims[a];
+      int v = pos[a] - c[a];
+      const bool below = v < 0, above = v >= n;
+      if (g.bc_lo[a] == BC_PERIODIC) { if (below) v += n; }
+      else if (g.bc_lo[a] == BC_WALL) wall |= below;
+      else if (g.bc_lo[a] == BC_INLET) inlet |= below;
+      if (g.bc_hi[a] == BC_PERIODIC) { if (above) v -= n; }
+      else if (g.bc_hi[a] == BC_WALL) wall |= above;
+      else if (g.bc_hi[a] == BC_OUTLET) outlet |= above;
+      s[a] = v < 0 ? 0 : (v > n - 1 ? n - 1 : v);
+    }
+    const int si = s[0] + g.nx * (s[1] + g.ny * s[2]);
+    const bool bb = inlet || outlet || wall || mask[si] != 0;
+    if (bb) word |= 1u << i;
+  }
+  out[r] = word;
+}
+
+template <typename S, typename R>
+__global__ void set_fields_kernel(int D, Geo g, const double* __restrict__ T, const double* __restrict__ Y,
+                                  int K, const double* __restrict__ invW, const double* __restrict__ u,
+                                  const double* __restrict__ P_h, const double* __restrict__ g_pert,
+                                  double p_fac, double P_ref, int thermal, S* g_out, R* T_out, R* Y_out,
+                                  R* u_out, R* rho_out, R* lam_out, R* ph_out) {
+  const int r = blockIdx.x * AUX_BLOCK + threadIdx.x;
+  if (r >= g.N) return;
+  const size_t N = (size_t)g.N;
+  double rho = 1.0;
+  if (thermal) {
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) {
+      s += Y[k * N + r] * invW[k];
+      Y_out[k * N + r] = (R)Y[k * N + r];
+    }
+    rho = p_fac / (s * T[r]);  // P_th W / (R T rho_ref)
+    T_out[r] = (R)T[r];
+  }
+  const double ux = u[r], uy = u[N + r], uz = D == 3 ? u[2 * N + r] : 0.0;
+  u_out[r] = (R)ux;
+  u_out[N + r] = (R)uy;
+  if (D == 3) u_out[2 * N + r] = (R)uz;
+  rho_out[r] = (R)rho;
+  lam_out[r] = (R)0;
+  const double ph = P_h[r];
+  ph_out[r] = (R)ph;
+  const int Q = D == 2 ? 9 : 27;
+  const double usq = ux * ux + uy * uy + uz * uz;
+  for (int i = 0; i < Q; ++i) {
+    const double w = D == 2 ? wgt<2>(i) : wgt<3>(i);
+    const double cu = cx(i) * ux + cy(i) * uy + (D == 3 ? cz(i) * uz : 0.0);
+    const double feq = w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);  // Eq. 4
+    double geq = w * (ph - rho / 3.0) + feq / 3.0;                          // Eq. 6
+    if (g_pert) geq += g_pert[(size_t)i * N + r];
+    g_out[(size_t)i * N + r] = (S)((R)((geq - w * P_ref) / w));
+  }
+}
+
+template <typename S, typename R>
+__global__ void get_fields_kernel(int D, Geo g, unsigned bits, int K, const S* __restrict__ gp,
+                                  const R* __restrict__ T, const R* __restrict__ Y, const R* __restrict__ u,
+                                  const R* __restrict__ ph, const R* __restrict__ rho, const R* __restrict__ lam,
+                                  const PthState* pth, double P_ref, double* __restrict__ dst) {
+  const int r = blockIdx.x * AUX_BLOCK + threadIdx.x;
+  if (r >= g.N) return;
+  const size_t N = (size_t)g.N;
+  size_t off = 0;
+  if (bits & 1u) { dst[off + r] = (double)T[r]; off += N; }
+  if (bits & 2u) {
+    for (int k = 0; k < K; ++k) dst[off + k * N + r] = (double)Y[k * N + r];
+    off += (size_t)K * N;
+  }
+  if (bits & 4u) {
+    for (int a = 0; a < D; ++a) dst[off + a * N + r] = (double)u[a * N + r];
+    off += (size_t)D * N;
+  }
+  if (bits & 8u) { dst[off + r] = (double)ph[r]; off += N; }
+  if (bits & 16u) { dst[off + r] = (double)rho[r]; off += N; }
+  if (bits & 32u) {
+    const double extra = sizeof(R) == 8 ? pth->lb_lam_d : (double)pth->lb_lam;
+    dst[off + r] = (double)lam[r] + extra;
+    off += N;
+  }
+  if (bits & 64u) {
+    const int Q = D == 2 ? 9 : 27;
+    for (int i = 0; i < Q; ++i) {
+      const double w = D == 2 ? wgt<2>(i) : wgt<3>(i);
+      dst[off + (size_t)i * N + r] = w * ((double)(R)gp[(size_t)i * N + r] + P_ref);
+    }
+  }
+}
+
+// Thermodynamic-pressure integrand of the stored initial state, with the same arithmetic and
+// the same partial layout as the per-step reduction of the finite-difference kernel.
+template <typename R>
+__global__ void init_integral_kernel(Geo g, const uint8_t* __restrict__ mask, const R* __restrict__ T,
+                                     const R* __restrict__ Y, FDConst<R> c, void* __restrict__ partials) {
+  const int r = blockIdx.x * AUX_BLOCK + threadIdx.x;
+  R v = R(0);
+  if (r < g.N && mask[r] == 0) {
+    R s = R(0);
+    for (int k = 0; k < c.K; ++k) s += Y[(size_t)k * g.N + r] * (R)c.inv_W[k];
+    v = (R)c.I_scale / (s * T[r]);
+  }
+  if constexpr (sizeof(R) == 4) {
+    __shared__ long long sh[AUX_BLOCK];
+    sh[threadIdx.x] = f32_to_fix32((float)v);
+    __syncthreads();
+    for (int o = AUX_BLOCK / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      ((long long*)partials)[2 * blockIdx.x] = sh[0];
+      ((long long*)partials)[2 * blockIdx.x + 1] = 0;
+    }
+  } else {
+    __shared__ double sh[AUX_BLOCK];
+    sh[threadIdx.x] = (double)v;
+    __syncthreads();
+    for (int o = AUX_BLOCK / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      ((double*)partials)[2 * blockIdx.x] = sh[0];
+      ((double*)partials)[2 * blockIdx.x + 1] = 0.0;
+    }
+  }
+}
+
+// One block: exact sum of the per-block partials, then the thermodynamic-pressure update
+// P^{n+1} = M^{n+1} / I^{n+1} in FP64.
+__global__ void pth_update_kernel(PthUpdate pu, const void* __restrict__ partials, int nblocks, PthState* pth,
+                                  int init) {
+  __shared__ long long sI[1024], sM[1024];
+  __shared__ double dI[1024], dM[1024];
+  const int t = threadIdx.x;
+  if (pu.fixed_point) {
+    const long long* p = (const long long*)partials;
+    long long a = 0, b = 0;
+    for (int i = t; i < nblocks; i += blockDim.x) { a += p[2 * i]; b += p[2 * i + 1]; }
+    sI[t] = a;
+    sM[t] = b;
+  } else {
+    const double* p = (const double*)partials;
+    double a = 0, b = 0;
+    for (int i = t; i < nblocks; i += blockDim.x) { a += p[2 * i]; b += p[2 * i + 1]; }
+    dI[t] = a;
+    dM[t] = b;
+  }
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (t < o) {
+      if (pu.fixed_point) { sI[t] += sI[t + o]; sM[t] += sM[t + o]; }
+      else { dI[t] += dI[t + o]; dM[t] += dM[t + o]; }
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    double I, mflux;
+    if (pu.fixed_point) {
+      I = (double)sI[0] / (FIX_SCALE * pu.I_s);
+      mflux = (double)sM[0] / (FIX_SCALE * pu.M_s);
+    } else {
+      I = dI[0] / pu.I_s;
+      mflux = dM[0] / pu.M_s;
+    }
+    const double P_old = pth->P;
+    // set-up: M = P_th0 I0 and nothing moves; step: P^{n+1} = M^{n+1} / I^{n+1}
+    const double M_new = init ? P_old * I : pth->M + mflux;
+    const double P_new = init ? P_old : M_new / I;
+    const double dP = P_new - P_old;
+    pth->M = M_new;
+    pth->P = P_new;
+    pth->dP = dP;
+    pth->lb_lam_d = -dP / P_old;
+    pth->fd_rho_d = P_new / pu.R_rho_ref;
+    pth->fd_dT_d = dP / pu.cp_rho_ref;
+    pth->rho_in_d = P_new * pu.rin_fac;
+    pth->lb_lam = (float)pth->lb_lam_d;
+    pth->fd_rho = (float)pth->fd_rho_d;
+    pth->fd_dT = (float)pth->fd_dT_d;
+    pth->rho_in = (float)pth->rho_in_d;
+  }
+}
+}  // namespace
+
+cudaError_t launch_links(int D, const Geo& g, const uint8_t* mask, uint32_t* out, cudaStream_t st) {
+  links_kernel<<<(g.N + AUX_BLOCK - 1) / AUX_BLOCK, AUX_BLOCK, 0, st>>>(D, g, mask, out);
+  return cudaGetLastError();
+}
+
+template <typename S, typename R>
+cudaError_t launch_set_fields(int D, const Geo& g, const double* T, const double* Y, int K,
+                              const double* invW, const double* u, const double* P_h,
+                              const double* g_pert, double p_fac, double P_ref, int thermal, S* g_out,
+                              R* T_out, R* Y_out, R* u_out, R* rho_out, R* lam_out, R* ph_out,
+                              cudaStream_t st) {
+  set_fields_kernel<S, R><<<(g.N + AUX_BLOCK - 1) / AUX_BLOCK, AUX_BLOCK, 0, st>>>(
+      D, g, T, Y, K, invW, u, P_h, g_pert, p_fac, P_ref, thermal, g_out, T_out, Y_out, u_out, rho_out,
+      lam_out, ph_out);
+  return cudaGetLastError();
+}
+
+template <typename S, typename R>
+cudaError_t launch_get_fields(int D, const Geo& g, unsigned bits, int K, const S* gp, const R* T,
+                              const R* Y, const R* u, const R* ph, const R* rho, const R* lam,
+                              const PthState* pth, double P_ref, double* dst, cudaStream_t st) {
+  get_fields_kernel<S, R><<<(g.N + AUX_BLOCK - 1) / AUX_BLOCK, AUX_BLOCK, 0, st>>>(
+      D, g, bits, K, gp, T, Y, u, ph, rho, lam, pth, P_ref, dst);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_init_integral(const Geo& g, const uint8_t* mask, const R* T, const R* Y, const FDConst<R>& c,
+                                 void* partials, int nblocks, cudaStream_t st) {
+  init_integral_kernel<R><<<nblocks, AUX_BLOCK, 0, st>>>(g, mask, T, Y, c, partials);
+  return cudaGetLastError();
+}
+template cudaError_t launch_init_integral<float>(const Geo&, const uint8_t*, const float*, const float*,
+                                                 const FDConst<float>&, void*, int, cudaStream_t);
+template cudaError_t launch_init_integral<double>(const Geo&, const uint8_t*, const double*, const double*,
+                                                  const FDConst<double>&, void*, int, cudaStream_t);
+
+cudaError_t launch_pth_update(const PthUpdate& pu, const void* partials, int nblocks, PthState* pth,
+                              int init, cudaStream_t st) {
+  pth_update_kernel<<<1, 1024, 0, st>>>(pu, partials, nblocks, pth, init);
+  return cudaGetLastError();
+}
+
+#define INST(S, R)                                                                                     \
+  template cudaError_t launch_set_fields<S, R>(int, const Geo&, const double*, const double*, int,    \
+                                               const double*, const double*, const double*,           \
+                                               const double*, double, double, int, S*, R*, R*, R*, R*, \
+                                               R*, R*, cudaStream_t);                                  \
+  template cudaError_t launch_get_fields<S, R>(int, const Geo&, unsigned, int, const S*, const R*,    \
+                                               const R*, const R*, const R*, const R*, const R*,       \
+                                               const PthState*, double, double*, cudaStream_t);
+INST(double, double)
+INST(float, float)
+INST(__half, float)
+#undef INST
+
+}  // namespace hlbm

@@ -1,0 +1,156 @@
+// Shared device-side definitions of the GB300 library: lattice tables (compile-time),
+// parameter blocks passed by value to the kernels, and small numeric helpers.
+//
+// Lattice (Section 2.1): D2Q9 / D3Q27 from the tensor product of the three-point rule with
+// weights (1/6, 2/3, 1/6); direction i has c = ((i%3)-1, ((i/3)%3)-1, (i/9)-1); the opposite
+// direction is Q-1-i. All constants below are derived from that rule at compile time.
+#pragma once
+#include <cstdint>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace hlbm {
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET = 2, BC_OUTLET = 3 };
+enum { COLL_BGK = 0, COLL_CUMULANT = 1 };
+constexpr int MAX_SP = 8;
+constexpr int MAX_RX = 4;
+
+template <int D> struct Lat;
+template <> struct Lat<2> { static constexpr int Q = 9; };
+template <> struct Lat<3> { static constexpr int Q = 27; };
+
+__host__ __device__ constexpr int cx(int i) { return i % 3 - 1; }
+__host__ __device__ constexpr int cy(int i) { return (i / 3) % 3 - 1; }
+__host__ __device__ constexpr int cz(int i) { return i / 9 - 1; }
+__host__ __device__ constexpr double w1(int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+template <int D> __host__ __device__ constexpr double wgt(int i) {
+  return D == 2 ? w1(cx(i)) * w1(cy(i)) : w1(cx(i)) * w1(cy(i)) * w1(cz(i));
+}
+
+// ---------------------------------------------------------------------------- geometry
+struct Geo {
+  int nx, ny, nz;
+  int N;
+  int bc_lo[3], bc_hi[3];
+};
+
+// Thermodynamic-pressure scalars, kept on the device and updated by the reduction kernel.
+struct PthState {
+  double P;        // thermodynamic pressure, Pa (level n during the FD update)
+  double M;        // total mass, lattice units
+  double dP;       // last increment of P (Pa per step)
+  double steps;    // number of steps taken
+  float fd_rho;    // P / (R rho_ref): rho_lat = fd_rho * W / T
+  float fd_dT;     // dP_prev / (cp rho_ref): pressure-work increment of T is fd_dT / rho_lat
+  float lb_lam;    // -dP / P_old, added to Lambda by the LB kernel of this step
+  float rho_in;    // inlet density, lattice units
+  double fd_rho_d, fd_dT_d, lb_lam_d, rho_in_d;  // same in FP64 for the FP64 storage path
+};
+
+// Fixed-point scales of the exact integer reduction (sum of per-cell FP32 terms).
+constexpr double FIX_SCALE = 4294967296.0;  // 2^32
+
+// Finite-difference / chemistry constants (lattice units unless noted), in the arithmetic type R.
+template <typename R> struct FDConst {
+  int K, nrx;
+  int sensor, sensor_species, sensor_oxidizer;
+  int closed;
+  R nu_lat, T_ref_inv, mu_exp, inv_Pr;
+  R inv_Le[MAX_SP];       // 1 / Le_k
+  R inv_W[MAX_SP];        // 1 / W_k  (mol/kg)
+  R W[MAX_SP];
+  R hf_W[MAX_SP];         // h_f,k * W_k (J/mol)
+  R dt_phys;              // s
+  R inv_cp;               // 1 / cp
+  R inv_rho_ref;
+  R F, sensor_beta, inv_wref, sensor_Ta;
+  R eps_T, eps_Y;
+  R T_in, Y_in[MAX_SP];
+  // reactions: q = A exp(-E/(R T)) T^beta prod c^n. E/R is split into hi + lo parts for the
+  // float path (float-float argument); the double path uses ER_hi = E/R and ER_lo = 0.
+  R A[MAX_RX], beta[MAX_RX], ER_hi[MAX_RX], ER_lo[MAX_RX];
+  R nu[MAX_RX][MAX_SP], order[MAX_RX][MAX_SP];
+  R I_scale;              // integrand -> O(1) before the reduction
+  R M_scale;              // mass flux -> O(1) before the reduction
+};
+
+// ---------------------------------------------------------------------------- storage
+// Populations are stored shifted: h = (g - w P_ref) / w. Loads return g.
+template <typename S, typename R> __device__ __forceinline__ R ld_pop(const S* p) { return (R)(*p); }
+template <> __device__ __forceinline__ float ld_pop<__half, float>(const __half* p) {
+  return __half2float(__ldg(p));
+}
+template <> __device__ __forceinline__ float ld_pop<float, float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ double ld_pop<double, double>(const double* p) { return __ldg(p); }
+
+template <typename S, typename R> __device__ __forceinline__ void st_pop(S* p, R v) { *p = (S)v; }
+template <> __device__ __forceinline__ void st_pop<__half, float>(__half* p, float v) {
+  *p = __float2half_rn(v);
+}
+
+template <typename R> __device__ __forceinline__ R ldg(const R* p) { return __ldg(p); }
+
+// ---------------------------------------------------------------------------- fixed point
+// x * 2^32 as a 64-bit integer, using integer operations only (the value of a float is
+// mantissa * 2^(exponent - 23), so the product is a shift of the mantissa). Bits below 2^-32
+// are truncated; |x| must stay below 2^30. Summing these integers is exact and independent of
+// the order, which makes the reductions deterministic.
+__device__ __forceinline__ long long f32_to_fix32(float x) {
+  const unsigned b = __float_as_uint(x);
+  const int e = (int)((b >> 23) & 0xffu);
+  if (e == 0) return 0;  // zero or subnormal: below the resolution
+  const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+  const int sh = e - 127 - 23 + 32;
+  long long v = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0);
+  return (b >> 31) ? -v : v;
+}
+
+// Warp-wide sum of a 64-bit integer (exact).
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------- kernel arguments
+constexpr int LB_BLOCK = 128;
+
+template <typename R> struct LBArgs {
+  Geo geo;
+  const void* g_in;
+  void* g_out;
+  const uint32_t* links;
+  const R* rho;      // thermal: density at level n (lattice units)
+  const R* lam;      // thermal: Lambda from the FD update (without the P_th term)
+  const R* T;        // thermal: temperature at level n (viscosity law)
+  const R* inlet_u;  // [D][ny*nz], low-x face
+  R* u;              // [D][N]: read at outlet cells (previous step), written as below
+  int write_u;       // 1: write u of every cell; 0: outlet cells only
+  R* ph_out;         // [N] or nullptr
+  const PthState* pth;
+  int* flag;
+  R nu_lat, T_ref_inv, mu_exp, smag_k, omega_b, om3, om4, om5, om6, P_ref;
+};
+
+constexpr int FD_BLOCK = 256;
+enum { NB_FLUID = 0, NB_SOLID = 1, NB_INLET = 2, NB_OUTLET = 3 };
+
+template <typename R> struct FDArgs {
+  Geo geo;
+  const uint8_t* mask;
+  const R* T;         // [N] level n
+  const R* Y;         // [K][N] level n
+  R* T_out;           // [N] level n+1
+  R* Y_out;           // [K][N]
+  const R* u;         // [D][N]
+  const R* inlet_u;   // [D][ny*nz]
+  R* Floc;            // [N] flame sensor output (nullptr: F_loc = F)
+  R* rho_out;         // [N]
+  R* lam_out;         // [N]
+  void* partials;     // [grid][2] fixed-point int64 (float path) or double (double path)
+  const PthState* pth;
+  FDConst<R> c;
+};
+
+}  // namespace hlbm

@@ -1,0 +1,323 @@
+// Finite-difference update of temperature and species (Section 2.3) with Arrhenius chemistry
+// and the thickened-flame factor, the flame sensor, and the thermodynamic-pressure reduction.
+// One thread per cell, lattice units of length and time (dr = dt = 1).
+//
+//   phi^{n+1} = phi^n - sum_a u_a (phi_hat(r + e_a/2) - phi_hat(r - e_a/2)) + N_phi
+//   N_phi = (1/rho) sum_a [G(r+e/2)(phi(r+e) - phi(r)) - G(r-e/2)(phi(r) - phi(r-e))] + sources
+// WENO3 face values (upwind side from the face velocity), centred diffusion with the arithmetic
+// face mean of G = F_loc mu(T) / (Pr Le), chemistry divided by F_loc, pressure work on T.
+// Lambda (Eq. 3) = N_T / T + sum_k (W / W_k) N_k, rho = P_th W / (R T).
+// Stencil points outside the fluid take ghost values: zero gradient (walls, solids, outlet) or
+// the inlet state (low-x inlet), velocity 0 at walls and solids, inlet velocity at the inlet.
+#pragma once
+#include "common.cuh"
+
+namespace hlbm {
+
+// Kind and index of the neighbour of (p[0], p[1], p[2]) at +sigma along `axis`.
+// On return p holds the (wrapped) neighbour coordinates when the kind is fluid.
+__device__ __forceinline__ int nb_classify(const Geo& g, const uint8_t* __restrict__ mask, int axis,
+                                           int sigma, int* p, int base, int& idx) {
+  const int n = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
+  int v = p[axis] + sigma;
+  int kind = NB_FLUID;
+  if (v < 0) {
+    if (g.bc_lo[axis] == BC_PERIODIC) v += n;
+    else kind = g.bc_lo[axis] == BC_INLET ? NB_INLET : NB_SOLID;
+  } else if (v >= n) {
+    if (g.bc_hi[axis] == BC_PERIODIC) v -= n;
+    else kind = g.bc_hi[axis] == BC_OUTLET ? NB_OUTLET : NB_SOLID;
+  }
+  idx = base;
+  if (kind == NB_FLUID) {
+    int q[3] = {p[0], p[1], p[2]};
+    q[axis] = v;
+    const int j = q[0] + g.nx * (q[1] + g.ny * q[2]);
+    if (__ldg(mask + j)) {
+      kind = NB_SOLID;
+    } else {
+      idx = j;
+      p[axis] = v;
+    }
+  }
+  return kind;
+}
+
+// exp(-E / (R T)) with the exponent argument E/(R T) carried in float-float arithmetic
+// (error ~1e-13 relative before the final float rounding of the exponential).
+__device__ __forceinline__ float arrhenius(float ER_hi, float ER_lo, float T) {
+  const float r = 1.0f / T;
+  const float e = fmaf(-T, r, 1.0f);  // exact residual of the reciprocal
+  const float rlo = r * e;
+  const float hi = ER_hi * r;
+  const float lo = fmaf(ER_hi, r, -hi) + ER_hi * rlo + ER_lo * r;
+  return expf(-hi) * (1.0f - lo);
+}
+
+// x^y for x >= 0: FP32 as exp2(y log2 x) with the hardware log2 / exp2 (relative error a few
+// 1e-7, against ~50 instructions for powf); FP64 with pow.
+template <typename R> __device__ __forceinline__ R powr(R x, R y);
+template <> __device__ __forceinline__ float powr<float>(float x, float y) { return exp2f(y * __log2f(x)); }
+template <> __device__ __forceinline__ double powr<double>(double x, double y) { return pow(x, y); }
+
+template <typename R> __device__ __forceinline__ R fdiv(R a, R b) { return a / b; }
+template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
+
+template <typename R> __device__ __forceinline__ R weno3(R a, R b, R c, R eps) {
+  const R q0 = R(-0.5) * a + R(1.5) * b;
+  const R q1 = R(0.5) * (b + c);
+  const R s0 = (eps + (b - a) * (b - a));
+  const R s1 = (eps + (c - b) * (c - b));
+  const R t0 = s0 * s0, t1 = s1 * s1;  // alpha_k = d_k / t_k
+  // (d0/t0 q0 + d1/t1 q1) / (d0/t0 + d1/t1) with d0 = 1/3, d1 = 2/3
+  // the denominator stays far below 2^126, the range where the fast division is exact enough
+  return fdiv<R>(t1 * q0 + R(2) * t0 * q1, t1 + R(2) * t0);
+}
+
+// Reaction rates q_j (mol/(m^3 s)) of one cell.
+template <typename R>
+__device__ __forceinline__ void reaction_rates(const FDConst<R>& c, R T, const R* Y, R rho_phys, R* q) {
+#pragma unroll
+  for (int j = 0; j < MAX_RX; ++j) {
+    if (j >= c.nrx) break;
+    R v;
+    if constexpr (sizeof(R) == 4) {
+      v = c.A[j] * arrhenius(c.ER_hi[j], c.ER_lo[j], T);
+    } else {
+      v = c.A[j] * exp(-c.ER_hi[j] / T);
+    }
+    if (c.beta[j] != R(0)) v *= powr<R>(T, c.beta[j]);
+#pragma unroll
+    for (int k = 0; k < MAX_SP; ++k) {
+      if (k >= c.K) break;
+      const R n = c.order[j][k];
+      if (n != R(0)) {
+        const R conc = rho_phys * fmax(Y[k], R(0)) * (R)c.inv_W[k];
+        v *= (n == R(1)) ? conc : powr<R>(conc, n);
+      }
+    }
+    q[j] = v;
+  }
+}
+
+template <typename R> __device__ __forceinline__ R nu_of(const FDConst<R>& c, int j, int k) {
+  return c.nu[j][k];
+}
+
+// Flame sensor: F_loc = 1 + (F - 1) tanh(beta Omega / Omega_0) with
+// Omega = max(Y_F, 0) max(Y_O, 0) exp(-T_s / T), stored per fluid cell.
+template <int D, typename R>
+__global__ void __launch_bounds__(FD_BLOCK) flame_sensor_kernel(const FDArgs<R> a) {
+  const int r = blockIdx.x * FD_BLOCK + threadIdx.x;
+  if (r >= a.geo.N) return;
+  if (__ldg(a.mask + r)) return;
+  const FDConst<R>& c = a.c;
+  const size_t N = (size_t)a.geo.N;
+  const R T = ldg(a.T + r);
+  const R yf = fmax(ldg(a.Y + c.sensor_species * N + r), R(0));
+  const R yo = fmax(ldg(a.Y + c.sensor_oxidizer * N + r), R(0));
+  const R om = yf * yo * exp(-c.sensor_Ta / T);
+  a.Floc[r] = R(1) + (c.F - R(1)) * tanh(c.sensor_beta * om * c.inv_wref);
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(FD_BLOCK) fd_step_kernel(const FDArgs<R> a) {
+  const int r = blockIdx.x * FD_BLOCK + threadIdx.x;
+  const FDConst<R>& c = a.c;
+  const Geo& g = a.geo;
+  const size_t N = (size_t)g.N;
+  const bool active = r < g.N && __ldg(a.mask + r) == 0;
+  R termI = R(0), termM = R(0);  // P_th integrand and boundary mass flux of this cell
+
+  if (active) {
+    const int x = r % g.nx;
+    const int t = r / g.nx;
+    const int y = t % g.ny;
+    const int z = t / g.ny;
+    // neighbour classification: [axis][side] for distance 1 and 2
+    int k1[3][2], i1[3][2], k2[3][2], i2[3][2];
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int sigma = sd ? 1 : -1;
+        int p[3] = {x, y, z};
+        int j1;
+        const int kk1 = nb_classify(g, a.mask, ax, sigma, p, r, j1);
+        k1[ax][sd] = kk1;
+        i1[ax][sd] = j1;
+        if (kk1 == NB_FLUID) {
+          int j2;
+          k2[ax][sd] = nb_classify(g, a.mask, ax, sigma, p, j1, j2);
+          i2[ax][sd] = j2;
+        } else {
+          k2[ax][sd] = kk1;
+          i2[ax][sd] = r;
+        }
+      }
+    }
+    // local state
+    const R Tr = ldg(a.T + r);
+    R Yr[MAX_SP];
+    R sW = R(0);
+#pragma unroll
+    for (int k = 0; k < MAX_SP; ++k) {
+      if (k < c.K) {
+        Yr[k] = ldg(a.Y + k * N + r);
+        sW += Yr[k] * (R)c.inv_W[k];
+      } else {
+        Yr[k] = R(0);
+      }
+    }
+    const R W = R(1) / sW;
+    const R fdr = sizeof(R) == 4 ? (R)a.pth->fd_rho : (R)a.pth->fd_rho_d;
+    const R rho = fdr * W / Tr;  // lattice units
+    const R rho_phys = rho / (R)c.inv_rho_ref;
+    const R inv_rho = R(1) / rho;
+    R q[MAX_RX];
+    reaction_rates<R>(c, Tr, Yr, rho_phys, q);
+    const R Fr = a.Floc ? ldg(a.Floc + r) : c.F;
+    const R mur = (R)c.nu_lat * powr<R>(Tr * (R)c.T_ref_inv, (R)c.mu_exp);
+    R ur[3] = {ldg(a.u + r), ldg(a.u + N + r), D == 3 ? ldg(a.u + 2 * N + r) : R(0)};
+    const int f = y + g.ny * z;
+    const int nf = g.ny * g.nz;
+    // face coefficients (F mu) and face velocities
+    R FMf[3][2], uf[3][2];
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int kk = k1[ax][sd];
+        const int j = i1[ax][sd];
+        const R Tn = kk == NB_FLUID ? ldg(a.T + j) : (kk == NB_INLET ? (R)c.T_in : Tr);
+        const R Fn = (a.Floc && kk == NB_FLUID) ? ldg(a.Floc + j) : Fr;
+        const R mun = (R)c.nu_lat * powr<R>(Tn * (R)c.T_ref_inv, (R)c.mu_exp);
+        FMf[ax][sd] = R(0.5) * (Fr * mur + Fn * mun);
+        R un;
+        if (kk == NB_FLUID) un = ldg(a.u + ax * N + j);
+        else if (kk == NB_INLET) un = ldg(a.inlet_u + ax * nf + f);
+        else if (kk == NB_OUTLET) un = ur[ax];
+        else un = R(0);
+        uf[ax][sd] = R(0.5) * (ur[ax] + un);
+      }
+    }
+    // chemistry sources
+    const R dt = (R)c.dt_phys;
+    const R inv_rpF = R(1) / (rho_phys * Fr);
+    R qdot = R(0);
+#pragma unroll
+    for (int j = 0; j < MAX_RX; ++j) {
+      if (j >= c.nrx) break;
+      R hsum = R(0);
+#pragma unroll
+      for (int k = 0; k < MAX_SP; ++k)
+        if (k < c.K) hsum += (R)c.hf_W[k] * nu_of<R>(c, j, k);
+      qdot -= hsum * q[j];
+    }
+    const R fd_dT = sizeof(R) == 4 ? (R)a.pth->fd_dT : (R)a.pth->fd_dT_d;
+    R lam = R(0);
+    R sWn = R(0);
+    R Tnew = Tr;
+    // fields: 0 = T, 1.. = Y_k
+#pragma unroll 1
+    for (int fi = 0; fi <= c.K; ++fi) {
+      const R* phi = fi == 0 ? a.T : a.Y + (size_t)(fi - 1) * N;
+      const R phin = fi == 0 ? (R)c.T_in : (R)c.Y_in[fi - 1];
+      const R eps = fi == 0 ? (R)c.eps_T : (R)c.eps_Y;
+      const R gfac = (R)c.inv_Pr * (fi == 0 ? R(1) : (R)c.inv_Le[fi - 1]);
+      const R pr = ldg(phi + r);
+      R adv = R(0), dif = R(0);
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        R v1[2], v2[2];
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          v1[sd] = k1[ax][sd] == NB_INLET ? phin : ldg(phi + i1[ax][sd]);
+          v2[sd] = k2[ax][sd] == NB_INLET ? phin : ldg(phi + i2[ax][sd]);
+        }
+        // v1[0] = phi(r - e), v2[0] = phi(r - 2e), v1[1] = phi(r + e), v2[1] = phi(r + 2e)
+        const R fp = uf[ax][1] >= R(0) ? weno3<R>(v1[0], pr, v1[1], eps) : weno3<R>(v2[1], v1[1], pr, eps);
+        const R fm = uf[ax][0] >= R(0) ? weno3<R>(v2[0], v1[0], pr, eps) : weno3<R>(v1[1], pr, v1[0], eps);
+        adv += ur[ax] * (fp - fm);
+        dif += FMf[ax][1] * (v1[1] - pr) - FMf[ax][0] * (pr - v1[0]);
+      }
+      dif *= gfac * inv_rho;
+      R src;
+      if (fi == 0) {
+        src = dt * qdot * inv_rpF * (R)c.inv_cp + fd_dT * inv_rho;
+      } else {
+        R om = R(0);
+#pragma unroll
+        for (int j = 0; j < MAX_RX; ++j)
+          if (j < c.nrx) om += nu_of<R>(c, j, fi - 1) * q[j];
+        src = dt * (R)c.W[fi - 1] * om * inv_rpF;
+      }
+      const R NA = dif + src;
+      const R pn = pr - adv + NA;
+      if (fi == 0) {
+        a.T_out[r] = pn;
+        lam += NA / Tr;
+        Tnew = pn;
+      } else {
+        a.Y_out[(size_t)(fi - 1) * N + r] = pn;
+        lam += W * (R)c.inv_W[fi - 1] * NA;
+        sWn += pn * (R)c.inv_W[fi - 1];
+      }
+    }
+    a.rho_out[r] = rho;
+    a.lam_out[r] = lam;
+    if (c.closed) {
+      // W_new / (R T_new rho_ref), pre-scaled; gas constant folded into I_scale
+      termI = (R)c.I_scale / (sWn * Tnew);
+      if (x == 0 && g.bc_lo[0] == BC_INLET) {
+        const R rin = sizeof(R) == 4 ? (R)a.pth->rho_in : (R)a.pth->rho_in_d;
+        termM += (R)c.M_scale * rin * ldg(a.inlet_u + f);
+      }
+      if (x == g.nx - 1 && g.bc_hi[0] == BC_OUTLET) termM -= (R)c.M_scale * rho * ur[0];
+    }
+  }
+  if (!c.closed) return;  // uniform across the grid
+  // block reduction of the two terms
+  __shared__ long long sI[FD_BLOCK / 32], sM[FD_BLOCK / 32];
+  __shared__ double dI[FD_BLOCK / 32], dM[FD_BLOCK / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if constexpr (sizeof(R) == 4) {
+    long long vI = warp_sum_ll(f32_to_fix32((float)termI));
+    long long vM = warp_sum_ll(f32_to_fix32((float)termM));
+    if (lane == 0) { sI[wid] = vI; sM[wid] = vM; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long tI = 0, tM = 0;
+      for (int w = 0; w < FD_BLOCK / 32; ++w) { tI += sI[w]; tM += sM[w]; }
+      long long* out = (long long*)a.partials;
+      out[2 * blockIdx.x] = tI;
+      out[2 * blockIdx.x + 1] = tM;
+    }
+  } else {
+    double vI = (double)termI, vM = (double)termM;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      vI += __shfl_down_sync(0xffffffffu, vI, o);
+      vM += __shfl_down_sync(0xffffffffu, vM, o);
+    }
+    if (lane == 0) { dI[wid] = vI; dM[wid] = vM; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tI = 0, tM = 0;
+      for (int w = 0; w < FD_BLOCK / 32; ++w) { tI += dI[w]; tM += dM[w]; }
+      double* out = (double*)a.partials;
+      out[2 * blockIdx.x] = tI;
+      out[2 * blockIdx.x + 1] = tM;
+    }
+  }
+}
+
+template <int D, typename R>
+cudaError_t launch_fd(const FDArgs<R>& a, cudaStream_t st, bool sensor_pass) {
+  const int grid = (a.geo.N + FD_BLOCK - 1) / FD_BLOCK;
+  if (sensor_pass) flame_sensor_kernel<D, R><<<grid, FD_BLOCK, 0, st>>>(a);
+  else fd_step_kernel<D, R><<<grid, FD_BLOCK, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace hlbm

@@ -1,0 +1,37 @@
+// Host-side declarations of the kernel launchers (one translation unit per lattice/storage,
+// compiled in parallel) used by the C-ABI runtime in api.cu.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace hlbm {
+
+template <int D, typename S, typename R>
+cudaError_t launch_lb(const LBArgs<R>& a, int thermal, int coll, cudaStream_t st);
+template <int D, typename R>
+cudaError_t launch_fd(const FDArgs<R>& a, cudaStream_t st, bool sensor_pass);
+
+// aux_kernels.cu
+cudaError_t launch_links(int D, const Geo& g, const uint8_t* mask, uint32_t* out, cudaStream_t st);
+template <typename S, typename R>
+cudaError_t launch_set_fields(int D, const Geo& g, const double* T, const double* Y, int K,
+                              const double* invW, const double* u, const double* P_h,
+                              const double* g_pert, double P_th0_over_R_rho_ref, double P_ref,
+                              int thermal, S* g_out, R* T_out, R* Y_out, R* u_out, R* rho_out,
+                              R* lam_out, R* ph_out, cudaStream_t st);
+template <typename S, typename R>
+cudaError_t launch_get_fields(int D, const Geo& g, unsigned bits, int K, const S* gp, const R* T,
+                              const R* Y, const R* u, const R* ph, const R* rho, const R* lam,
+                              const PthState* pth, double P_ref, double* dst, cudaStream_t st);
+template <typename R>
+cudaError_t launch_init_integral(const Geo& g, const uint8_t* mask, const R* T, const R* Y, const FDConst<R>& c,
+                                 void* partials, int nblocks, cudaStream_t st);
+struct PthUpdate {
+  double I_s, M_s, R_rho_ref, cp_rho_ref, rin_fac;  // rin_fac = W_in / (R T_in rho_ref)
+  int fixed_point;                                  // partials are int64 fixed point
+};
+cudaError_t launch_pth_update(const PthUpdate& pu, const void* partials, int nblocks, PthState* pth,
+                              int init, cudaStream_t st);
+constexpr int AUX_BLOCK = 256;
+}  // namespace hlbm

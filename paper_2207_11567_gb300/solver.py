@@ -1,0 +1,194 @@
+"""Python face of the C ABI: a ``Solver`` that owns one library context.
+
+PyTorch provides device memory (the caching allocator, through the ABI's allocator hooks) and
+the CUDA stream; every step of the method runs in the library's CUDA kernels.
+"""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _check(ctx, status):
+    if status != L.LBM_OK:
+        msg = L.lib.lbm_last_error(ctx).decode() if ctx else ""
+        raise L.HLBMError(status, msg)
+
+
+class _TorchAllocator:
+    """Device allocations through torch's caching allocator on one stream."""
+
+    def __init__(self, device, stream):
+        self.device, self.stream = device, stream
+        self.alloc = L.ALLOC_FN(self._alloc)
+        self.free = L.FREE_FN(self._free)
+
+    def _alloc(self, nbytes, _user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+        except Exception:  # out of memory: the library reports LBM_ERR_ALLOC
+            return None
+
+    def _free(self, ptr, _user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+
+def _as_c_double(arr):
+    """Host float64 contiguous array and its pointer (the array must be kept alive)."""
+    a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64))
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+class Solver:
+    """One simulation context (``include/hlbm.h``)."""
+
+    def __init__(self, cfg, mask, inlet_u=None, device=None, stream=None, torch_alloc=True):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the hybrid LB/FD library needs a CUDA device")
+        self.cfg = cfg
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            self._c = L.config_from_dict(cfg, C.c_void_p(self.stream.cuda_stream))
+            self._alloc = None
+            if torch_alloc:
+                self._alloc = _TorchAllocator(self.device, self.stream)
+                self._c.alloc, self._c.free = self._alloc.alloc, self._alloc.free
+            self.ctx = C.c_void_p()
+            st = L.lib.lbm_init(C.byref(self._c), C.byref(self.ctx))
+            if st != L.LBM_OK:
+                msg = L.lib.lbm_last_error(self.ctx).decode() if self.ctx else ""
+                L.lib.lbm_destroy(self.ctx)
+                self.ctx = None
+                raise L.HLBMError(st, msg)
+        self.dim = cfg["dim"]
+        self.Q = 3 ** self.dim
+        self.K = len(cfg.get("species", [])) if cfg.get("thermal") else 0
+        nz = cfg.get("nz", 1) if self.dim == 3 else 1
+        self.N = cfg["nx"] * cfg["ny"] * nz
+        self.set_geometry(mask, inlet_u)
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            L.lib.lbm_destroy(self.ctx)
+            self.ctx = None
+
+    # ---------------------------------------------------------------------------- set-up
+    def set_geometry(self, mask, inlet_u=None):
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
+        if m.size != self.N:
+            raise ValueError("mask size")
+        keep = None
+        ptr = None
+        if inlet_u is not None:
+            keep, ptr = _as_c_double(inlet_u)
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_set_geometry(self.ctx, m.ctypes.data_as(C.c_void_p), ptr, 0))
+        del keep
+
+    def set_fields(self, T=None, Y=None, u=None, P_h=None, g_pert=None):
+        keep = []
+
+        def p(a):
+            if a is None:
+                return None
+            arr, ptr = _as_c_double(a)
+            keep.append(arr)
+            return ptr
+
+        if u is None:
+            u = np.zeros((self.dim, self.N))
+        if P_h is None:
+            P_h = np.zeros(self.N)
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_set_fields(self.ctx, p(T), p(Y), p(u), p(P_h), p(g_pert), 0))
+
+    # ------------------------------------------------------------------------------ run
+    def step(self, n=1):
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_step(self.ctx, int(n)))
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    # --------------------------------------------------------------------------- output
+    def fields(self, bits=L.F_T | L.F_Y | L.F_U | L.F_PH | L.F_RHO | L.F_LAM | L.F_G, device=False):
+        """Selected fields as float64 (numpy on the host, or a torch tensor on the device)."""
+        if not self.cfg.get("thermal"):
+            bits &= ~(L.F_T | L.F_Y | L.F_RHO | L.F_LAM)
+        n = L.lib.lbm_fields_size(self.ctx, bits)
+        with torch.cuda.device(self.device):
+            if device:
+                out = torch.empty(n, dtype=torch.float64, device=self.device)
+                self.stream.wait_stream(torch.cuda.current_stream(self.device))
+                _check(self.ctx, L.lib.lbm_get_fields(self.ctx, bits, C.c_void_p(out.data_ptr()), 1))
+                buf = out
+            else:
+                buf = np.empty(n, dtype=np.float64)
+                _check(self.ctx, L.lib.lbm_get_fields(self.ctx, bits, buf.ctypes.data_as(C.c_void_p), 0))
+        res, off, N = {}, 0, self.N
+        for bit, name, count in ((L.F_T, "T", 1), (L.F_Y, "Y", self.K), (L.F_U, "u", self.dim),
+                                 (L.F_PH, "P_h", 1), (L.F_RHO, "rho", 1), (L.F_LAM, "lam", 1),
+                                 (L.F_G, "g", self.Q)):
+            if bits & bit:
+                v = buf[off: off + count * N]
+                res[name] = v.reshape(count, N) if count != 1 or name in ("Y",) else v
+                off += count * N
+        return res
+
+    def scalars(self):
+        out = (C.c_double * 4)()
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_get_scalars(self.ctx, out))
+        return {"P_th": out[0], "dP": out[1], "M": out[2], "steps": int(out[3])}
+
+    def links(self):
+        out = np.empty(self.N, dtype=np.uint32)
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_get_links(self.ctx, out.ctypes.data_as(C.c_void_p), 0))
+        return out
+
+    # ---------------------------------------------------------------------- checkpoints
+    def state_bytes(self):
+        return int(L.lib.lbm_state_bytes(self.ctx))
+
+    def save_state(self, buf=None):
+        if buf is None:
+            buf = torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_save_state(self.ctx, C.c_void_p(buf.data_ptr())))
+        return buf
+
+    def load_state(self, buf):
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_load_state(self.ctx, C.c_void_p(buf.data_ptr())))
+
+    # ------------------------------------------------------------------------- profiling
+    def profile(self, enable=True):
+        _check(self.ctx, L.lib.lbm_profile(self.ctx, int(enable)))
+
+    def kernel_times(self):
+        ms = (C.c_double * L.KERNEL_KINDS)()
+        n = (C.c_longlong * L.KERNEL_KINDS)()
+        _check(self.ctx, L.lib.lbm_kernel_times(self.ctx, ms, n))
+        return {L.KERNEL_NAMES[k]: (ms[k], n[k]) for k in range(L.KERNEL_KINDS)}
+
+    def kernel_bytes(self):
+        b = (C.c_double * L.KERNEL_KINDS)()
+        _check(self.ctx, L.lib.lbm_kernel_bytes(self.ctx, b))
+        return {L.KERNEL_NAMES[k]: b[k] for k in range(L.KERNEL_KINDS)}
+
+    def use_graphs(self, enable=True):
+        _check(self.ctx, L.lib.lbm_use_graphs(self.ctx, int(enable)))
+
+
+def from_workload(wl, **kw):
+    """Solver initialised with a ``workloads.Workload``'s geometry and fields."""
+    s = Solver(wl.cfg, wl.mask, wl.inlet_u, **kw)
+    s.set_fields(T=wl.T, Y=wl.Y, u=wl.u, P_h=wl.P_h, g_pert=wl.g_pert)
+    return s

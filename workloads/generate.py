@@ -47,7 +47,8 @@ def _base_cfg(dim, nx, ny, nz, storage, collision="cumulant"):
             "T_ref": 300.0, "mu_exp": 0.7, "Pr": 0.7, "cp": 1400.0, "rho_ref": 1.17,
             "P_th0": 101325.0, "P_ref": 0.0, "omega_bulk": 1.0, "omega_hi": [1.0, 1.0, 1.0, 1.0],
             "smag_cs": 0.0, "thicken_F": 1.0, "flame_sensor": False, "sensor_beta": 10.0,
-            "sensor_wref": 1.0, "sensor_species": 0, "closed_domain": False, "thermal": False,
+            "sensor_wref": 1e-5, "sensor_species": 0, "sensor_oxidizer": 1, "sensor_Ta": 8400.0,
+            "closed_domain": False, "thermal": False,
             "species": [], "reactions": [], "T_in": 300.0, "Y_in": []}
 
 
@@ -147,7 +148,7 @@ def swirl_k(S, Ri, Ro):
 def swirl_3d(nx=256, ny=128, nz=128, reactive=False, storage="f32", seed=0,
              collision="cumulant", u_axial=0.05, swirl=0.6, noise=0.05, smag=0.17, F=8.0,
              steps=None, dx=None, dt=None, A1=1.0e9, A2=5.0e6, T_in=320.0, T_hot=1970.0,
-             sensor_wref=50.0):
+             sensor_wref=1e-5):
     """Swirl-burner-like domain along x: annular swirling inlet (radii 8 and 16 cells at the
     128-cell scale) through an injector duct, square confined chamber, contracting exhaust to
     an outlet; cold (LB only) or reactive (2-step chemistry, thickened flame with sensor,
@@ -201,6 +202,7 @@ def swirl_3d(nx=256, ny=128, nz=128, reactive=False, storage="f32", seed=0,
         b = _tanh_blend(x + 0.5 - xf, 4.0 * s)
         cfg.update({"thermal": True, "thicken_F": F, "flame_sensor": True,
                     "sensor_beta": 10.0, "sensor_wref": sensor_wref, "sensor_species": 0,
+                    "sensor_oxidizer": 1, "sensor_Ta": 8400.0,
                     "closed_domain": True, "species": species(names),
                     "reactions": chemistry_2step(A1, A2), "T_in": T_in, "T_ref": 300.0,
                     "Y_in": list(Yu)})
