@@ -25,6 +25,11 @@ Finite differences (Section 2.3): a stencil point that is not a fluid cell takes
 Packed link word used to compare with the GPU library bit for bit: for a fluid cell, bit i is
 set when direction i is not a plain pull (code 1, 2 or 3) and bit 31 is set; a solid cell has
 word 0.
+
+Packed stencil word of the finite-difference update: for axis a and side s (0: -, 1: +) the
+four bits at 4 (2a + s) hold the kind of the distance-1 point (bits 0-1: 0 fluid, 1 wall or
+solid, 2 inlet, 3 outlet) and of the distance-2 point (bits 2-3: 0 fluid, 1 zero-gradient copy
+of the distance-1 value, 2 inlet); bit 31 marks a fluid cell, a solid cell has word 0.
 """
 import torch
 
@@ -195,3 +200,17 @@ class FDNeighbours:
 
     def index1(self, axis, sigma):
         return self.lines[(axis, sigma)][1]
+
+
+def pack_stencil_words(grid, nb):
+    """Packed finite-difference stencil words (int64 holding the uint32 bit pattern)."""
+    word = torch.zeros(grid.N, dtype=torch.int64)
+    for axis in range(grid.dim):
+        for side, sigma in enumerate((-1, 1)):
+            k1, _, k2, _ = nb.lines[(axis, sigma)]
+            # distance-2 kind relative to the rule: fluid, zero-gradient copy, or inlet
+            d2 = torch.where(k2 == K_FLUID, 0, torch.where(k2 == K_INLET, 2, 1))
+            word |= (k1 | (d2 << 2)) << (4 * (2 * axis + side))
+    word |= grid.fluid.to(torch.int64) << 31
+    word[~grid.fluid] = 0
+    return word

@@ -56,6 +56,9 @@ class Oracle:
     def links_packed(self):
         return geo.pack_links(self.code, self.grid)
 
+    def stencil_words_packed(self):
+        return geo.pack_stencil_words(self.grid, self.nb)
+
     # ----------------------------------------------------------------- state
     def density(self, T, Y, P_th):
         W = fdm.mean_molar_mass(self.p, Y)

@@ -71,6 +71,7 @@ def _load():
         "lbm_get_fields": (C.c_int, [P, C.c_uint, P, C.c_int]),
         "lbm_get_scalars": (C.c_int, [P, C.POINTER(C.c_double)]),
         "lbm_get_links": (C.c_int, [P, P, C.c_int]),
+        "lbm_get_stencil_words": (C.c_int, [P, P, C.c_int]),
         "lbm_state_bytes": (C.c_size_t, [P]),
         "lbm_save_state": (C.c_int, [P, P]),
         "lbm_load_state": (C.c_int, [P, P]),
@@ -88,7 +89,8 @@ def _load():
 
 lib = _load()
 EXPORTED = ("lbm_init", "lbm_destroy", "lbm_last_error", "lbm_set_geometry", "lbm_set_fields", "lbm_step",
-            "lbm_fields_size", "lbm_get_fields", "lbm_get_scalars", "lbm_get_links", "lbm_state_bytes",
+            "lbm_fields_size", "lbm_get_fields", "lbm_get_scalars", "lbm_get_links", "lbm_get_stencil_words",
+            "lbm_state_bytes",
             "lbm_save_state", "lbm_load_state", "lbm_profile", "lbm_kernel_times", "lbm_kernel_bytes",
             "lbm_use_graphs")
 

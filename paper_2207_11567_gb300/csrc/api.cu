@@ -1,6 +1,7 @@
 // C-ABI runtime of the library (declared in include/hlbm.h): configuration checks, unit
 // conversion, device state, the per-step launch sequence (FD -> thermodynamic pressure -> LB,
 // Section 2), CUDA-graph replay of step pairs, kernel timing and checkpoints.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -39,10 +40,12 @@ struct lbm_ctx {
   void* ph = nullptr;
   void* Floc = nullptr;
   uint32_t* links = nullptr;
+  uint32_t* sword = nullptr;
   uint8_t* mask = nullptr;
   void* inlet_u = nullptr;
   void* partials = nullptr;
-  int nblocks_fd = 0;
+  int nblocks_fd = 0;    // partial slots written by the FD kernel
+  int nblocks_init = 0;  // partial slots written by the initial-integral kernel
   PthState* pth = nullptr;
   int* flag = nullptr;
   double* scratch_out = nullptr;  // staging for get_fields
@@ -233,6 +236,7 @@ template <typename R> FDArgs<R> make_fd_args(lbm_ctx* c, int cur) {
   FDArgs<R> a{};
   a.geo = c->geo;
   a.mask = c->mask;
+  a.sword = c->sword;
   a.T = (const R*)c->T[cur];
   a.Y = (const R*)c->Y[cur];
   a.T_out = (R*)c->T[1 - cur];
@@ -249,7 +253,11 @@ template <typename R> FDArgs<R> make_fd_args(lbm_ctx* c, int cur) {
 }
 
 cudaError_t run_lb(lbm_ctx* c, int cur, bool want_out) {
-  const int th = c->cfg.thermal, co = c->cfg.collision;
+  const int th = c->cfg.thermal;
+  // the cumulant kernel has a variant for the default case where orders 3..6 relax fully
+  const bool hi1 = c->cfg.omega_hi[0] == 1.0 && c->cfg.omega_hi[1] == 1.0 && c->cfg.omega_hi[2] == 1.0 &&
+                   c->cfg.omega_hi[3] == 1.0;
+  const int co = c->cfg.collision == LBM_COLL_CUMULANT ? (hi1 ? COLL_CUMULANT_FULL : COLL_CUMULANT) : COLL_BGK;
   if (c->f64) {
     auto a = make_lb_args<double>(c, cur, want_out);
     return c->D == 2 ? launch_lb<2, double, double>(a, th, co, c->st) : launch_lb<3, double, double>(a, th, co, c->st);
@@ -399,12 +407,14 @@ lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
   ok = ok && (ctx->lam = dalloc(ctx, N * ctx->F));
   ok = ok && (ctx->ph = dalloc(ctx, N * ctx->F));
   ok = ok && (ctx->links = (uint32_t*)dalloc(ctx, N * 4));
+  ok = ok && (ctx->sword = (uint32_t*)dalloc(ctx, N * 4));
   ok = ok && (ctx->mask = (uint8_t*)dalloc(ctx, N));
   ok = ok && (ctx->inlet_u = dalloc(ctx, (size_t)ctx->D * c.ny * c.nz * ctx->F));
   ok = ok && (ctx->pth = (PthState*)dalloc(ctx, sizeof(PthState)));
   ok = ok && (ctx->flag = (int*)dalloc(ctx, 16));
-  ctx->nblocks_fd = (int)((N + FD_BLOCK - 1) / FD_BLOCK);
-  ok = ok && (ctx->partials = dalloc(ctx, (size_t)ctx->nblocks_fd * 16));
+  ctx->nblocks_fd = fd_partial_blocks(ctx->D, ctx->geo);
+  ctx->nblocks_init = (int)((N + AUX_BLOCK - 1) / AUX_BLOCK);
+  ok = ok && (ctx->partials = dalloc(ctx, (size_t)std::max(ctx->nblocks_fd, ctx->nblocks_init) * 16));
   if (c.thermal) {
     for (int b = 0; b < 2; ++b) {
       ok = ok && (ctx->T[b] = dalloc(ctx, N * ctx->F));
@@ -471,6 +481,7 @@ lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* mask, const double* inl
     else cudaFree(tmp);
   }
   CK(launch_links(ctx->D, ctx->geo, ctx->mask, ctx->links, ctx->st), "links kernel");
+  CK(launch_stencil_words(ctx->D, ctx->geo, ctx->mask, ctx->sword, ctx->st), "stencil words kernel");
   std::vector<uint8_t> hm(N);
   CK(cudaMemcpyAsync(hm.data(), ctx->mask, N, cudaMemcpyDeviceToHost, ctx->st), "copy mask");
   CK(cudaStreamSynchronize(ctx->st), "sync");
@@ -550,10 +561,10 @@ lbm_status lbm_set_fields(lbm_ctx* ctx, const double* T, const double* Y, const 
   if (st == LBM_OK && c.thermal && c.closed_domain) {
     cudaError_t e = ctx->f64
         ? launch_init_integral<double>(ctx->geo, ctx->mask, (const double*)ctx->T[0], (const double*)ctx->Y[0],
-                                       ctx->fdc_d, ctx->partials, ctx->nblocks_fd, ctx->st)
+                                       ctx->fdc_d, ctx->partials, ctx->nblocks_init, ctx->st)
         : launch_init_integral<float>(ctx->geo, ctx->mask, (const float*)ctx->T[0], (const float*)ctx->Y[0],
-                                      ctx->fdc_f, ctx->partials, ctx->nblocks_fd, ctx->st);
-    if (e == cudaSuccess) e = launch_pth_update(ctx->pu, ctx->partials, ctx->nblocks_fd, ctx->pth, 1, ctx->st);
+                                      ctx->fdc_f, ctx->partials, ctx->nblocks_init, ctx->st);
+    if (e == cudaSuccess) e = launch_pth_update(ctx->pu, ctx->partials, ctx->nblocks_init, ctx->pth, 1, ctx->st);
     if (e != cudaSuccess) st = cuda_fail(ctx, e, "initial integral");
   }
   cudaError_t e = cudaStreamSynchronize(ctx->st);
@@ -665,6 +676,16 @@ lbm_status lbm_get_scalars(lbm_ctx* ctx, double out[4]) {
   return LBM_OK;
 }
 
+lbm_status lbm_get_stencil_words(lbm_ctx* ctx, uint32_t* dst, int dst_on_device) {
+  if (!ctx || !dst) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->have_geo) return fail(ctx, LBM_ERR_STATE, "no geometry");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  CK(cudaMemcpyAsync(dst, ctx->sword, ctx->N * 4, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     ctx->st), "copy stencil words");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  return LBM_OK;
+}
+
 lbm_status lbm_get_links(lbm_ctx* ctx, uint32_t* dst, int dst_on_device) {
   if (!ctx || !dst) return fail(ctx, LBM_ERR_ARG, "null argument");
   if (!ctx->have_geo) return fail(ctx, LBM_ERR_STATE, "no geometry");
@@ -759,7 +780,7 @@ lbm_status lbm_kernel_bytes(const lbm_ctx* ctx, double bytes[LBM_KERNEL_KINDS]) 
   const double K = ctx->K, D = ctx->D, Q = ctx->Q;
   const bool th = ctx->cfg.thermal;
   // FD: read T, Y, u; write T, Y, rho, Lambda; mask per cell; flame factor when the sensor is on
-  bytes[KIND_FD] = th ? Nf * ((2.0 * (1 + K) + D + 2.0 + (ctx->cfg.flame_sensor ? 1.0 : 0.0)) * F) + N : 0.0;
+  bytes[KIND_FD] = th ? Nf * ((2.0 * (1 + K) + D + 2.0 + (ctx->cfg.flame_sensor ? 1.0 : 0.0)) * F) + 4.0 * N : 0.0;
   bytes[KIND_SENSOR] = (th && ctx->cfg.flame_sensor) ? Nf * 4.0 * F + N : 0.0;
   bytes[KIND_PTH] = (th && ctx->cfg.closed_domain) ? 16.0 * ctx->nblocks_fd : 0.0;
   // LB: populations read + written, link word, and (thermal) rho, Lambda, T read + u written

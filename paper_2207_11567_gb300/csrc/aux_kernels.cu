@@ -48,6 +48,54 @@ __global__ void links_kernel(int D, Geo g, const uint8_t* __restrict__ mask, uin
   out[r] = word;
 }
 
+// Stencil word of the FD update (per axis a and side s, 4 bits at 4 (2a + s)): bits 0-1 the kind
+// of the distance-1 point (0 fluid, 1 wall or solid, 2 inlet, 3 outlet), bits 2-3 that of the
+// distance-2 point (0 fluid, 1 zero-gradient copy of the distance-1 value, 2 inlet); bit 31
+// marks a fluid cell, a solid cell has word 0.
+__device__ int sw_kind(const Geo& g, const uint8_t* mask, int axis, int sigma, int* p) {
+  const int n = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
+  int v = p[axis] + sigma;
+  if (v < 0) {
+    if (g.bc_lo[axis] == BC_PERIODIC) v += n;
+    else return g.bc_lo[axis] == BC_INLET ? 2 : 1;
+  } else if (v >= n) {
+    if (g.bc_hi[axis] == BC_PERIODIC) v -= n;
+    else return g.bc_hi[axis] == BC_OUTLET ? 3 : 1;
+  }
+  int q[3] = {p[0], p[1], p[2]};
+  q[axis] = v;
+  if (mask[q[0] + g.nx * (q[1] + g.ny * q[2])]) return 1;
+  p[axis] = v;
+  return 0;
+}
+
+__global__ void stencil_words_kernel(int D, Geo g, const uint8_t* __restrict__ mask, uint32_t* __restrict__ out) {
+  const int r = blockIdx.x * AUX_BLOCK + threadIdx.x;
+  if (r >= g.N) return;
+  if (mask[r]) {
+    out[r] = 0u;
+    return;
+  }
+  const int x = r % g.nx, t = r / g.nx, y = t % g.ny, z = t / g.ny;
+  uint32_t word = 1u << 31;
+  for (int ax = 0; ax < D; ++ax) {
+    for (int sd = 0; sd < 2; ++sd) {
+      int p[3] = {x, y, z};
+      const int sg = sd ? 1 : -1;
+      const int k1 = sw_kind(g, mask, ax, sg, p);
+      int k2;
+      if (k1 != 0) {
+        k2 = k1 == 2 ? 2 : 1;
+      } else {
+        const int kk = sw_kind(g, mask, ax, sg, p);
+        k2 = kk == 0 ? 0 : (kk == 2 ? 2 : 1);
+      }
+      word |= (uint32_t)(k1 | (k2 << 2)) << (4 * (2 * ax + sd));
+    }
+  }
+  out[r] = word;
+}
+
 template <typename S, typename R>
 __global__ void set_fields_kernel(int D, Geo g, const double* __restrict__ T, const double* __restrict__ Y,
                                   int K, const double* __restrict__ invW, const double* __restrict__ u,
@@ -219,6 +267,11 @@ __global__ void pth_update_kernel(PthUpdate pu, const void* __restrict__ partial
 
 cudaError_t launch_links(int D, const Geo& g, const uint8_t* mask, uint32_t* out, cudaStream_t st) {
   links_kernel<<<(g.N + AUX_BLOCK - 1) / AUX_BLOCK, AUX_BLOCK, 0, st>>>(D, g, mask, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_words(int D, const Geo& g, const uint8_t* mask, uint32_t* out, cudaStream_t st) {
+  stencil_words_kernel<<<(g.N + AUX_BLOCK - 1) / AUX_BLOCK, AUX_BLOCK, 0, st>>>(D, g, mask, out);
   return cudaGetLastError();
 }
 

@@ -12,7 +12,8 @@
 namespace hlbm {
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET = 2, BC_OUTLET = 3 };
-enum { COLL_BGK = 0, COLL_CUMULANT = 1 };
+// COLL_CUMULANT_FULL: cumulant collision whose orders 3..6 relax fully (rate 1), the default
+enum { COLL_BGK = 0, COLL_CUMULANT = 1, COLL_CUMULANT_FULL = 2 };
 constexpr int MAX_SP = 8;
 constexpr int MAX_RX = 4;
 
@@ -139,6 +140,7 @@ enum { NB_FLUID = 0, NB_SOLID = 1, NB_INLET = 2, NB_OUTLET = 3 };
 template <typename R> struct FDArgs {
   Geo geo;
   const uint8_t* mask;
+  const uint32_t* sword;  // [N] stencil words (neighbour kinds of the FD stencil)
   const R* T;         // [N] level n
   const R* Y;         // [K][N] level n
   R* T_out;           // [N] level n+1

@@ -120,40 +120,47 @@ __global__ void __launch_bounds__(FD_BLOCK) flame_sensor_kernel(const FDArgs<R> 
   a.Floc[r] = R(1) + (c.F - R(1)) * tanh(c.sensor_beta * om * c.inv_wref);
 }
 
+// Thread-block shape of the FD update: 32 x 4 x 2 cells in 3-D, 32 x 8 in 2-D (256 threads),
+// so that the y and z neighbours of most stencils are loaded by the same block (L1 reuse).
+template <int D> struct FDShape;
+template <> struct FDShape<2> { static constexpr int X = 32, Y = 8, Z = 1; };
+template <> struct FDShape<3> { static constexpr int X = 32, Y = 4, Z = 2; };
+
 template <int D, typename R>
-__global__ void __launch_bounds__(FD_BLOCK) fd_step_kernel(const FDArgs<R> a) {
-  const int r = blockIdx.x * FD_BLOCK + threadIdx.x;
+__global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? 3 : 1) fd_step_kernel(const FDArgs<R> a) {
   const FDConst<R>& c = a.c;
   const Geo& g = a.geo;
-  const size_t N = (size_t)g.N;
-  const bool active = r < g.N && __ldg(a.mask + r) == 0;
+  const int x = blockIdx.x * FDShape<D>::X + threadIdx.x;
+  const int y = blockIdx.y * FDShape<D>::Y + threadIdx.y;
+  const int z = blockIdx.z * FDShape<D>::Z + threadIdx.z;
+  const bool inside = x < g.nx && y < g.ny && z < g.nz;
+  const int r = x + g.nx * (y + g.ny * z);
+  const int N = g.N;
+  const uint32_t sw = inside ? __ldg(a.sword + r) : 0u;
+  const bool active = (sw >> 31) != 0u;
   R termI = R(0), termM = R(0);  // P_th integrand and boundary mass flux of this cell
 
   if (active) {
-    const int x = r % g.nx;
-    const int t = r / g.nx;
-    const int y = t % g.ny;
-    const int z = t / g.ny;
-    // neighbour classification: [axis][side] for distance 1 and 2
-    int k1[3][2], i1[3][2], k2[3][2], i2[3][2];
+    const int pos[3] = {x, y, z};
+    const int dims[3] = {g.nx, g.ny, g.nz};
+    const int strides[3] = {1, g.nx, g.nx * g.ny};
+    // neighbour kinds from the stencil word, indices with periodic wrap
+    int k1[3][2], k2[3][2], i1[3][2], i2[3][2];
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) {
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
-        const int sigma = sd ? 1 : -1;
-        int p[3] = {x, y, z};
-        int j1;
-        const int kk1 = nb_classify(g, a.mask, ax, sigma, p, r, j1);
-        k1[ax][sd] = kk1;
+        const uint32_t bits = (sw >> (4 * (2 * ax + sd))) & 15u;
+        k1[ax][sd] = (int)(bits & 3u);
+        k2[ax][sd] = (int)(bits >> 2);
+        const int sg = sd ? 1 : -1;
+        int p1 = pos[ax] + sg;
+        p1 = p1 < 0 ? p1 + dims[ax] : (p1 >= dims[ax] ? p1 - dims[ax] : p1);
+        int p2 = p1 + sg;
+        p2 = p2 < 0 ? p2 + dims[ax] : (p2 >= dims[ax] ? p2 - dims[ax] : p2);
+        const int j1 = k1[ax][sd] == NB_FLUID ? r + (p1 - pos[ax]) * strides[ax] : r;
         i1[ax][sd] = j1;
-        if (kk1 == NB_FLUID) {
-          int j2;
-          k2[ax][sd] = nb_classify(g, a.mask, ax, sigma, p, j1, j2);
-          i2[ax][sd] = j2;
-        } else {
-          k2[ax][sd] = kk1;
-          i2[ax][sd] = r;
-        }
+        i2[ax][sd] = k2[ax][sd] == 0 ? r + (p2 - pos[ax]) * strides[ax] : j1;
       }
     }
     // local state
@@ -164,7 +171,7 @@ __global__ void __launch_bounds__(FD_BLOCK) fd_step_kernel(const FDArgs<R> a) {
     for (int k = 0; k < MAX_SP; ++k) {
       if (k < c.K) {
         Yr[k] = ldg(a.Y + k * N + r);
-        sW += Yr[k] * (R)c.inv_W[k];
+        sW += Yr[k] * c.inv_W[k];
       } else {
         Yr[k] = R(0);
       }
@@ -172,12 +179,12 @@ __global__ void __launch_bounds__(FD_BLOCK) fd_step_kernel(const FDArgs<R> a) {
     const R W = R(1) / sW;
     const R fdr = sizeof(R) == 4 ? (R)a.pth->fd_rho : (R)a.pth->fd_rho_d;
     const R rho = fdr * W / Tr;  // lattice units
-    const R rho_phys = rho / (R)c.inv_rho_ref;
+    const R rho_phys = rho / c.inv_rho_ref;
     const R inv_rho = R(1) / rho;
     R q[MAX_RX];
     reaction_rates<R>(c, Tr, Yr, rho_phys, q);
     const R Fr = a.Floc ? ldg(a.Floc + r) : c.F;
-    const R mur = (R)c.nu_lat * powr<R>(Tr * (R)c.T_ref_inv, (R)c.mu_exp);
+    const R mur = c.nu_lat * powr<R>(Tr * c.T_ref_inv, c.mu_exp);
     R ur[3] = {ldg(a.u + r), ldg(a.u + N + r), D == 3 ? ldg(a.u + 2 * N + r) : R(0)};
     const int f = y + g.ny * z;
     const int nf = g.ny * g.nz;
@@ -189,9 +196,9 @@ __global__ void __launch_bounds__(FD_BLOCK) fd_step_kernel(const FDArgs<R> a) {
       for (int sd = 0; sd < 2; ++sd) {
         const int kk = k1[ax][sd];
         const int j = i1[ax][sd];
-        const R Tn = kk == NB_FLUID ? ldg(a.T + j) : (kk == NB_INLET ? (R)c.T_in : Tr);
+        const R Tn = kk == NB_FLUID ? ldg(a.T + j) : (kk == NB_INLET ? c.T_in : Tr);
         const R Fn = (a.Floc && kk == NB_FLUID) ? ldg(a.Floc + j) : Fr;
-        const R mun = (R)c.nu_lat * powr<R>(Tn * (R)c.T_ref_inv, (R)c.mu_exp);
+        const R mun = c.nu_lat * powr<R>(Tn * c.T_ref_inv, c.mu_exp);
         FMf[ax][sd] = R(0.5) * (Fr * mur + Fn * mun);
         R un;
         if (kk == NB_FLUID) un = ldg(a.u + ax * N + j);
@@ -202,7 +209,7 @@ __global__ void __launch_bounds__(FD_BLOCK) fd_step_kernel(const FDArgs<R> a) {
       }
     }
     // chemistry sources
-    const R dt = (R)c.dt_phys;
+    const R dt = c.dt_phys;
     const R inv_rpF = R(1) / (rho_phys * Fr);
     R qdot = R(0);
 #pragma unroll
@@ -211,7 +218,7 @@ __global__ void __launch_bounds__(FD_BLOCK) fd_step_kernel(const FDArgs<R> a) {
       R hsum = R(0);
 #pragma unroll
       for (int k = 0; k < MAX_SP; ++k)
-        if (k < c.K) hsum += (R)c.hf_W[k] * nu_of<R>(c, j, k);
+        if (k < c.K) hsum += c.hf_W[k] * c.nu[j][k];
       qdot -= hsum * q[j];
     }
     const R fd_dT = sizeof(R) == 4 ? (R)a.pth->fd_dT : (R)a.pth->fd_dT_d;
@@ -222,35 +229,35 @@ __global__ void __launch_bounds__(FD_BLOCK) fd_step_kernel(const FDArgs<R> a) {
 #pragma unroll 1
     for (int fi = 0; fi <= c.K; ++fi) {
       const R* phi = fi == 0 ? a.T : a.Y + (size_t)(fi - 1) * N;
-      const R phin = fi == 0 ? (R)c.T_in : (R)c.Y_in[fi - 1];
-      const R eps = fi == 0 ? (R)c.eps_T : (R)c.eps_Y;
-      const R gfac = (R)c.inv_Pr * (fi == 0 ? R(1) : (R)c.inv_Le[fi - 1]);
+      const R phin = fi == 0 ? c.T_in : c.Y_in[fi - 1];
+      const R eps = fi == 0 ? c.eps_T : c.eps_Y;
+      const R gfac = c.inv_Pr * (fi == 0 ? R(1) : c.inv_Le[fi - 1]);
       const R pr = ldg(phi + r);
       R adv = R(0), dif = R(0);
 #pragma unroll
       for (int ax = 0; ax < D; ++ax) {
-        R v1[2], v2[2];
-#pragma unroll
-        for (int sd = 0; sd < 2; ++sd) {
-          v1[sd] = k1[ax][sd] == NB_INLET ? phin : ldg(phi + i1[ax][sd]);
-          v2[sd] = k2[ax][sd] == NB_INLET ? phin : ldg(phi + i2[ax][sd]);
-        }
-        // v1[0] = phi(r - e), v2[0] = phi(r - 2e), v1[1] = phi(r + e), v2[1] = phi(r + 2e)
-        const R fp = uf[ax][1] >= R(0) ? weno3<R>(v1[0], pr, v1[1], eps) : weno3<R>(v2[1], v1[1], pr, eps);
-        const R fm = uf[ax][0] >= R(0) ? weno3<R>(v2[0], v1[0], pr, eps) : weno3<R>(v1[1], pr, v1[0], eps);
+        // m1 = phi(r - e), m2 = phi(r - 2e), p1 = phi(r + e), p2 = phi(r + 2e)
+        const R m1 = k1[ax][0] == NB_INLET ? phin : ldg(phi + i1[ax][0]);
+        const R m2 = k2[ax][0] == 2 ? phin : ldg(phi + i2[ax][0]);
+        const R p1 = k1[ax][1] == NB_INLET ? phin : ldg(phi + i1[ax][1]);
+        const R p2 = k2[ax][1] == 2 ? phin : ldg(phi + i2[ax][1]);
+        // select the upwind stencil first, then one reconstruction per face
+        const bool up = uf[ax][1] >= R(0), um = uf[ax][0] >= R(0);
+        const R fp = weno3<R>(up ? m1 : p2, up ? pr : p1, up ? p1 : pr, eps);
+        const R fm = weno3<R>(um ? m2 : p1, um ? m1 : pr, um ? pr : m1, eps);
         adv += ur[ax] * (fp - fm);
-        dif += FMf[ax][1] * (v1[1] - pr) - FMf[ax][0] * (pr - v1[0]);
+        dif += FMf[ax][1] * (p1 - pr) - FMf[ax][0] * (pr - m1);
       }
       dif *= gfac * inv_rho;
       R src;
       if (fi == 0) {
-        src = dt * qdot * inv_rpF * (R)c.inv_cp + fd_dT * inv_rho;
+        src = dt * qdot * inv_rpF * c.inv_cp + fd_dT * inv_rho;
       } else {
         R om = R(0);
 #pragma unroll
         for (int j = 0; j < MAX_RX; ++j)
-          if (j < c.nrx) om += nu_of<R>(c, j, fi - 1) * q[j];
-        src = dt * (R)c.W[fi - 1] * om * inv_rpF;
+          if (j < c.nrx) om += c.nu[j][fi - 1] * q[j];
+        src = dt * c.W[fi - 1] * om * inv_rpF;
       }
       const R NA = dif + src;
       const R pn = pr - adv + NA;
@@ -260,38 +267,40 @@ __global__ void __launch_bounds__(FD_BLOCK) fd_step_kernel(const FDArgs<R> a) {
         Tnew = pn;
       } else {
         a.Y_out[(size_t)(fi - 1) * N + r] = pn;
-        lam += W * (R)c.inv_W[fi - 1] * NA;
-        sWn += pn * (R)c.inv_W[fi - 1];
+        lam += W * c.inv_W[fi - 1] * NA;
+        sWn += pn * c.inv_W[fi - 1];
       }
     }
     a.rho_out[r] = rho;
     a.lam_out[r] = lam;
     if (c.closed) {
       // W_new / (R T_new rho_ref), pre-scaled; gas constant folded into I_scale
-      termI = (R)c.I_scale / (sWn * Tnew);
+      termI = c.I_scale / (sWn * Tnew);
       if (x == 0 && g.bc_lo[0] == BC_INLET) {
         const R rin = sizeof(R) == 4 ? (R)a.pth->rho_in : (R)a.pth->rho_in_d;
-        termM += (R)c.M_scale * rin * ldg(a.inlet_u + f);
+        termM += c.M_scale * rin * ldg(a.inlet_u + f);
       }
-      if (x == g.nx - 1 && g.bc_hi[0] == BC_OUTLET) termM -= (R)c.M_scale * rho * ur[0];
+      if (x == g.nx - 1 && g.bc_hi[0] == BC_OUTLET) termM -= c.M_scale * rho * ur[0];
     }
   }
   if (!c.closed) return;  // uniform across the grid
-  // block reduction of the two terms
+  // block reduction of the two terms into this block's partial slot
   __shared__ long long sI[FD_BLOCK / 32], sM[FD_BLOCK / 32];
   __shared__ double dI[FD_BLOCK / 32], dM[FD_BLOCK / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int tid = threadIdx.x + FDShape<D>::X * (threadIdx.y + FDShape<D>::Y * threadIdx.z);
+  const int lane = tid & 31, wid = tid >> 5;
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   if constexpr (sizeof(R) == 4) {
     long long vI = warp_sum_ll(f32_to_fix32((float)termI));
     long long vM = warp_sum_ll(f32_to_fix32((float)termM));
     if (lane == 0) { sI[wid] = vI; sM[wid] = vM; }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       long long tI = 0, tM = 0;
       for (int w = 0; w < FD_BLOCK / 32; ++w) { tI += sI[w]; tM += sM[w]; }
       long long* out = (long long*)a.partials;
-      out[2 * blockIdx.x] = tI;
-      out[2 * blockIdx.x + 1] = tM;
+      out[2 * bid] = tI;
+      out[2 * bid + 1] = tM;
     }
   } else {
     double vI = (double)termI, vM = (double)termM;
@@ -302,21 +311,33 @@ __global__ void __launch_bounds__(FD_BLOCK) fd_step_kernel(const FDArgs<R> a) {
     }
     if (lane == 0) { dI[wid] = vI; dM[wid] = vM; }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       double tI = 0, tM = 0;
       for (int w = 0; w < FD_BLOCK / 32; ++w) { tI += dI[w]; tM += dM[w]; }
       double* out = (double*)a.partials;
-      out[2 * blockIdx.x] = tI;
-      out[2 * blockIdx.x + 1] = tM;
+      out[2 * bid] = tI;
+      out[2 * bid + 1] = tM;
     }
   }
 }
 
+template <int D> inline dim3 fd_grid(const Geo& g) {
+  return dim3((g.nx + FDShape<D>::X - 1) / FDShape<D>::X, (g.ny + FDShape<D>::Y - 1) / FDShape<D>::Y,
+              (g.nz + FDShape<D>::Z - 1) / FDShape<D>::Z);
+}
+template <int D> inline int fd_blocks(const Geo& g) {
+  const dim3 b = fd_grid<D>(g);
+  return (int)(b.x * b.y * b.z);
+}
+
 template <int D, typename R>
 cudaError_t launch_fd(const FDArgs<R>& a, cudaStream_t st, bool sensor_pass) {
-  const int grid = (a.geo.N + FD_BLOCK - 1) / FD_BLOCK;
-  if (sensor_pass) flame_sensor_kernel<D, R><<<grid, FD_BLOCK, 0, st>>>(a);
-  else fd_step_kernel<D, R><<<grid, FD_BLOCK, 0, st>>>(a);
+  if (sensor_pass) {
+    const int grid = (a.geo.N + FD_BLOCK - 1) / FD_BLOCK;
+    flame_sensor_kernel<D, R><<<grid, FD_BLOCK, 0, st>>>(a);
+  } else {
+    fd_step_kernel<D, R><<<fd_grid<D>(a.geo), dim3(FDShape<D>::X, FDShape<D>::Y, FDShape<D>::Z), 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

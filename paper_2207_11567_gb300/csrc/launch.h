@@ -14,6 +14,8 @@ cudaError_t launch_fd(const FDArgs<R>& a, cudaStream_t st, bool sensor_pass);
 
 // aux_kernels.cu
 cudaError_t launch_links(int D, const Geo& g, const uint8_t* mask, uint32_t* out, cudaStream_t st);
+cudaError_t launch_stencil_words(int D, const Geo& g, const uint8_t* mask, uint32_t* out, cudaStream_t st);
+int fd_partial_blocks(int D, const Geo& g);
 template <typename S, typename R>
 cudaError_t launch_set_fields(int D, const Geo& g, const double* T, const double* Y, int K,
                               const double* invW, const double* u, const double* P_h,

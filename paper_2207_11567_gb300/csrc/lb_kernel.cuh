@@ -41,8 +41,9 @@ template <typename R> __device__ __forceinline__ void chim_bwd(R& a, R& b, R& c,
   c = R(0.5) * (k2 + k1);
 }
 
+// x^y for x > 0: FP32 via the hardware log2 / exp2 (relative error a few 1e-7), FP64 with pow
 template <typename R> __device__ __forceinline__ R pw(R x, R y);
-template <> __device__ __forceinline__ float pw<float>(float x, float y) { return powf(x, y); }
+template <> __device__ __forceinline__ float pw<float>(float x, float y) { return exp2f(y * __log2f(x)); }
 template <> __device__ __forceinline__ double pw<double>(double x, double y) { return pow(x, y); }
 
 // Cumulant relaxation in deviation form. n[] holds the central moments (slot a + 3b [+ 9c])
@@ -50,23 +51,29 @@ template <> __device__ __forceinline__ double pw<double>(double x, double y) { r
 // moments of h_eq are exactly 0 for any odd index and (1/3)^k for k indices equal to 2, so the
 // full central moments are kappa = kappa_eq + n. All formulas below are the cumulant relations
 // (partition formula, unit density) rewritten in n, so that every FP32 quantity is small.
-template <typename R>
+template <bool FULL, typename R>
 __device__ __forceinline__ void cumulant_relax2(R* n, const R om, const R omb, const R om3, const R om4) {
   const R third = R(1) / R(3);
   const R n20 = n[2], n02 = n[6], n11 = n[4];
-  const R C22 = n[8] - third * (n20 + n02) - n20 * n02 - R(2) * n11 * n11;
+  const R C22 = FULL ? R(0) : n[8] - third * (n20 + n02) - n20 * n02 - R(2) * n11 * n11;
   const R tr = R(0.5) * (n20 + n02);
   const R o1 = R(1) - om, ob = R(1) - omb;
   const R s20 = o1 * (n20 - tr) + ob * tr;
   const R s02 = o1 * (n02 - tr) + ob * tr;
   const R s11 = o1 * n11;
   n[2] = s20; n[6] = s02; n[4] = s11;
-  n[5] *= (R(1) - om3);
-  n[7] *= (R(1) - om3);
-  n[8] = (R(1) - om4) * C22 + third * (s20 + s02) + s20 * s02 + R(2) * s11 * s11;
+  if constexpr (FULL) {
+    n[5] = R(0);
+    n[7] = R(0);
+    n[8] = third * (s20 + s02) + s20 * s02 + R(2) * s11 * s11;
+  } else {
+    n[5] *= (R(1) - om3);
+    n[7] *= (R(1) - om3);
+    n[8] = (R(1) - om4) * C22 + third * (s20 + s02) + s20 * s02 + R(2) * s11 * s11;
+  }
 }
 
-template <typename R>
+template <bool FULL, typename R>
 __device__ __forceinline__ void cumulant_relax3(R* n, const R om, const R omb, const R om3,
                                                 const R om4, const R om5, const R om6) {
 #define K(a, b, c) n[(a) + 3 * (b) + 9 * (c)]
@@ -77,26 +84,30 @@ __device__ __forceinline__ void cumulant_relax3(R* n, const R om, const R omb, c
   const R n021 = K(0, 2, 1), n102 = K(1, 0, 2), n012 = K(0, 1, 2), n111 = K(1, 1, 1);
   const R n211 = K(2, 1, 1), n121 = K(1, 2, 1), n112 = K(1, 1, 2);
   const R n220 = K(2, 2, 0), n202 = K(2, 0, 2), n022 = K(0, 2, 2);
-  // forward cumulants of order 4, 5, 6
-  const R C211 = n211 - third * n011 - a * n011 - R(2) * n110 * n101;
-  const R C121 = n121 - third * n101 - b * n101 - R(2) * n110 * n011;
-  const R C112 = n112 - third * n110 - c * n110 - R(2) * n101 * n011;
-  const R C220 = n220 - third * (a + b) - a * b - R(2) * n110 * n110;
-  const R C202 = n202 - third * (a + c) - a * c - R(2) * n101 * n101;
-  const R C022 = n022 - third * (b + c) - b * c - R(2) * n011 * n011;
-  const R C221 = K(2, 2, 1) - ((third + a) * n021 + (third + b) * n201 + R(4) * n110 * n111 +
-                               R(2) * n101 * n120 + R(2) * n011 * n210);
-  const R C212 = K(2, 1, 2) - ((third + a) * n012 + (third + c) * n210 + R(4) * n101 * n111 +
-                               R(2) * n110 * n102 + R(2) * n011 * n201);
-  const R C122 = K(1, 2, 2) - ((third + c) * n120 + (third + b) * n102 + R(4) * n011 * n111 +
-                               R(2) * n101 * n021 + R(2) * n110 * n012);
-  const R C222 = K(2, 2, 2) + ninth * (a + b + c) - third * (n022 + n202 + n220) -
-                 (a * n022 + b * n202 + c * n220) -
-                 R(4) * (n110 * n112 + n101 * n121 + n011 * n211) -
-                 (R(2) * (n210 * n012 + n201 * n021 + n120 * n102) + R(4) * n111 * n111) +
-                 R(2) * third * (a * b + b * c + c * a) + R(2) * a * b * c +
-                 R(4) * ((third + a) * n011 * n011 + (third + b) * n101 * n101 + (third + c) * n110 * n110) +
-                 R(16) * n110 * n101 * n011;
+  // forward cumulants of order 4, 5, 6 (not needed when those orders relax fully)
+  R C211 = R(0), C121 = R(0), C112 = R(0), C220 = R(0), C202 = R(0), C022 = R(0);
+  R C221 = R(0), C212 = R(0), C122 = R(0), C222 = R(0);
+  if constexpr (!FULL) {
+    C211 = n211 - third * n011 - a * n011 - R(2) * n110 * n101;
+    C121 = n121 - third * n101 - b * n101 - R(2) * n110 * n011;
+    C112 = n112 - third * n110 - c * n110 - R(2) * n101 * n011;
+    C220 = n220 - third * (a + b) - a * b - R(2) * n110 * n110;
+    C202 = n202 - third * (a + c) - a * c - R(2) * n101 * n101;
+    C022 = n022 - third * (b + c) - b * c - R(2) * n011 * n011;
+    C221 = K(2, 2, 1) - ((third + a) * n021 + (third + b) * n201 + R(4) * n110 * n111 +
+                                 R(2) * n101 * n120 + R(2) * n011 * n210);
+    C212 = K(2, 1, 2) - ((third + a) * n012 + (third + c) * n210 + R(4) * n101 * n111 +
+                                 R(2) * n110 * n102 + R(2) * n011 * n201);
+    C122 = K(1, 2, 2) - ((third + c) * n120 + (third + b) * n102 + R(4) * n011 * n111 +
+                                 R(2) * n101 * n021 + R(2) * n110 * n012);
+    C222 = K(2, 2, 2) + ninth * (a + b + c) - third * (n022 + n202 + n220) -
+                   (a * n022 + b * n202 + c * n220) -
+                   R(4) * (n110 * n112 + n101 * n121 + n011 * n211) -
+                   (R(2) * (n210 * n012 + n201 * n021 + n120 * n102) + R(4) * n111 * n111) +
+                   R(2) * third * (a * b + b * c + c * a) + R(2) * a * b * c +
+                   R(4) * ((third + a) * n011 * n011 + (third + b) * n101 * n101 + (third + c) * n110 * n110) +
+                   R(16) * n110 * n101 * n011;
+  }
   // second order: trace deviation (rate omega_b) and deviatoric part (rate omega)
   const R tr = third * (a + b + c);
   const R o1 = R(1) - om, ob = R(1) - omb;
@@ -104,12 +115,13 @@ __device__ __forceinline__ void cumulant_relax3(R* n, const R om, const R omb, c
   const R s020 = o1 * (b - tr) + ob * tr;
   const R s002 = o1 * (c - tr) + ob * tr;
   const R s110 = o1 * n110, s101 = o1 * n101, s011 = o1 * n011;
-  const R o3 = R(1) - om3;
-  const R s210 = o3 * n210, s201 = o3 * n201, s120 = o3 * n120, s021 = o3 * n021;
-  const R s102 = o3 * n102, s012 = o3 * n012, s111 = o3 * n111;
-  const R o4 = R(1) - om4, o5 = R(1) - om5, o6 = R(1) - om6;
-  const R D211 = o4 * C211, D121 = o4 * C121, D112 = o4 * C112;
-  const R D220 = o4 * C220, D202 = o4 * C202, D022 = o4 * C022;
+  const R o3 = FULL ? R(0) : R(1) - om3;
+  const R s210 = FULL ? R(0) : o3 * n210, s201 = FULL ? R(0) : o3 * n201, s120 = FULL ? R(0) : o3 * n120;
+  const R s021 = FULL ? R(0) : o3 * n021, s102 = FULL ? R(0) : o3 * n102, s012 = FULL ? R(0) : o3 * n012;
+  const R s111 = FULL ? R(0) : o3 * n111;
+  const R o4 = FULL ? R(0) : R(1) - om4, o5 = FULL ? R(0) : R(1) - om5, o6 = FULL ? R(0) : R(1) - om6;
+  const R D211 = FULL ? R(0) : o4 * C211, D121 = FULL ? R(0) : o4 * C121, D112 = FULL ? R(0) : o4 * C112;
+  const R D220 = FULL ? R(0) : o4 * C220, D202 = FULL ? R(0) : o4 * C202, D022 = FULL ? R(0) : o4 * C022;
   // back to central moments (deviation form)
   K(2, 0, 0) = s200; K(0, 2, 0) = s020; K(0, 0, 2) = s002;
   K(1, 1, 0) = s110; K(1, 0, 1) = s101; K(0, 1, 1) = s011;
@@ -121,11 +133,11 @@ __device__ __forceinline__ void cumulant_relax3(R* n, const R om, const R omb, c
   K(2, 2, 0) = D220 + third * (s200 + s020) + s200 * s020 + R(2) * s110 * s110;
   K(2, 0, 2) = D202 + third * (s200 + s002) + s200 * s002 + R(2) * s101 * s101;
   K(0, 2, 2) = D022 + third * (s020 + s002) + s020 * s002 + R(2) * s011 * s011;
-  K(2, 2, 1) = o5 * C221 + (third + s200) * s021 + (third + s020) * s201 + R(4) * s110 * s111 +
+  K(2, 2, 1) = (FULL ? R(0) : o5 * C221) + (third + s200) * s021 + (third + s020) * s201 + R(4) * s110 * s111 +
                R(2) * s101 * s120 + R(2) * s011 * s210;
-  K(2, 1, 2) = o5 * C212 + (third + s200) * s012 + (third + s002) * s210 + R(4) * s101 * s111 +
+  K(2, 1, 2) = (FULL ? R(0) : o5 * C212) + (third + s200) * s012 + (third + s002) * s210 + R(4) * s101 * s111 +
                R(2) * s110 * s102 + R(2) * s011 * s201;
-  K(1, 2, 2) = o5 * C122 + (third + s002) * s120 + (third + s020) * s102 + R(4) * s011 * s111 +
+  K(1, 2, 2) = (FULL ? R(0) : o5 * C122) + (third + s002) * s120 + (third + s020) * s102 + R(4) * s011 * s111 +
                R(2) * s101 * s021 + R(2) * s110 * s012;
   const R A = (third + s200) * D022 + (third + s020) * D202 + (third + s002) * D220;
   const R B = R(4) * (s110 * D112 + s101 * D121 + s011 * D211);
@@ -134,7 +146,7 @@ __device__ __forceinline__ void cumulant_relax3(R* n, const R om, const R omb, c
                s200 * s020 * s002 +
                R(2) * ((third + s200) * s011 * s011 + (third + s020) * s101 * s101 + (third + s002) * s110 * s110) +
                R(8) * s110 * s101 * s011;
-  K(2, 2, 2) = o6 * C222 + A + B + C3 + Dd;
+  K(2, 2, 2) = (FULL ? R(0) : o6 * C222) + A + B + C3 + Dd;
 #undef K
 }
 
@@ -163,15 +175,15 @@ __device__ __forceinline__ void add_delta_eq(R* m, const R* dx, const R* dy, con
 template <int D, typename S, typename R, bool THERMAL, int COLL>
 __global__ void __launch_bounds__(LB_BLOCK) lb_step_kernel(const LBArgs<R> a) {
   constexpr int Q = Lat<D>::Q;
-  const int r = blockIdx.x * LB_BLOCK + threadIdx.x;
-  if (r >= a.geo.N) return;
+  const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz;
+  // one block row of LB_BLOCK cells along x; y and z come from the grid (no integer division)
+  const int x = blockIdx.x * LB_BLOCK + threadIdx.x;
+  const int y = blockIdx.y;
+  const int z = blockIdx.z;
+  if (x >= nx) return;
+  const int r = x + nx * (y + ny * z);
   const uint32_t lw = __ldg(a.links + r);
   if (!(lw >> 31)) return;
-  const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz;
-  const int x = r % nx;
-  const int t = r / nx;
-  const int y = t % ny;
-  const int z = t / ny;
   const size_t N = (size_t)a.geo.N;
   const S* __restrict__ gin = (const S*)a.g_in;
   const R third = R(1) / R(3);
@@ -314,7 +326,8 @@ __global__ void __launch_bounds__(LB_BLOCK) lb_step_kernel(const LBArgs<R> a) {
     tau0 = R(3) * a.nu_lat + R(0.5);
   }
 
-  if constexpr (COLL == COLL_CUMULANT) {
+  if constexpr (COLL != COLL_BGK) {
+    constexpr bool FULL = COLL == COLL_CUMULANT_FULL;
     // central moments of w d (d = h/w - 1) about u, minus those of h_eq - w, give the central
     // moments n of h - h_eq (h_eq: product-form equilibrium); see delta_eq
     const R dlx[3] = {R(0), -ux, ux * ux}, dly[3] = {R(0), -uy, uy * uy}, dlz[3] = {R(0), -uz, uz * uz};
@@ -347,8 +360,8 @@ __global__ void __launch_bounds__(LB_BLOCK) lb_step_kernel(const LBArgs<R> a) {
       tau = R(0.5) * (tau0 + sqrt(tau0 * tau0 + a.smag_k * sqrt(n2)));
     }
     const R om = R(1) / tau;
-    if constexpr (D == 2) cumulant_relax2<R>(q, om, a.omega_b, a.om3, a.om4);
-    else cumulant_relax3<R>(q, om, a.omega_b, a.om3, a.om4, a.om5, a.om6);
+    if constexpr (D == 2) cumulant_relax2<FULL, R>(q, om, a.omega_b, a.om3, a.om4);
+    else cumulant_relax3<FULL, R>(q, om, a.omega_b, a.om3, a.om4, a.om5, a.om6);
     add_delta_eq<D, R, 0>(q, dlx, dly, dlz, R(1));
     if constexpr (D == 3) {
 #pragma unroll
@@ -422,14 +435,18 @@ __global__ void __launch_bounds__(LB_BLOCK) lb_step_kernel(const LBArgs<R> a) {
 
 template <int D, typename S, typename R>
 cudaError_t launch_lb(const LBArgs<R>& a, int thermal, int coll, cudaStream_t st) {
-  const int grid = (a.geo.N + LB_BLOCK - 1) / LB_BLOCK;
+  const dim3 grid((a.geo.nx + LB_BLOCK - 1) / LB_BLOCK, a.geo.ny, a.geo.nz);
+#define LB_LAUNCH(TH, CO) lb_step_kernel<D, S, R, TH, CO><<<grid, LB_BLOCK, 0, st>>>(a)
   if (thermal) {
-    if (coll == COLL_CUMULANT) lb_step_kernel<D, S, R, true, COLL_CUMULANT><<<grid, LB_BLOCK, 0, st>>>(a);
-    else lb_step_kernel<D, S, R, true, COLL_BGK><<<grid, LB_BLOCK, 0, st>>>(a);
+    if (coll == COLL_CUMULANT_FULL) LB_LAUNCH(true, COLL_CUMULANT_FULL);
+    else if (coll == COLL_CUMULANT) LB_LAUNCH(true, COLL_CUMULANT);
+    else LB_LAUNCH(true, COLL_BGK);
   } else {
-    if (coll == COLL_CUMULANT) lb_step_kernel<D, S, R, false, COLL_CUMULANT><<<grid, LB_BLOCK, 0, st>>>(a);
-    else lb_step_kernel<D, S, R, false, COLL_BGK><<<grid, LB_BLOCK, 0, st>>>(a);
+    if (coll == COLL_CUMULANT_FULL) LB_LAUNCH(false, COLL_CUMULANT_FULL);
+    else if (coll == COLL_CUMULANT) LB_LAUNCH(false, COLL_CUMULANT);
+    else LB_LAUNCH(false, COLL_BGK);
   }
+#undef LB_LAUNCH
   return cudaGetLastError();
 }
 

@@ -153,6 +153,12 @@ class Solver:
             _check(self.ctx, L.lib.lbm_get_links(self.ctx, out.ctypes.data_as(C.c_void_p), 0))
         return out
 
+    def stencil_words(self):
+        out = np.empty(self.N, dtype=np.uint32)
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_get_stencil_words(self.ctx, out.ctypes.data_as(C.c_void_p), 0))
+        return out
+
     # ---------------------------------------------------------------------- checkpoints
     def state_bytes(self):
         return int(L.lib.lbm_state_bytes(self.ctx))

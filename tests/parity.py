@@ -41,6 +41,7 @@ def gpu_run(wl, steps, **kw):
     s.step(steps)
     out = s.fields()
     out["links"] = s.links()
+    out["stencil_words"] = s.stencil_words()
     out["scalars"] = s.scalars()
     s.close()
     return out

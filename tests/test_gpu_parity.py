@@ -51,6 +51,7 @@ def test_chamber2d_f32_thermal():
     o, st = oracle_run(wl, 200)
     gpu = gpu_run(wl, 200)
     assert np.array_equal(gpu["links"].astype(np.int64), o.links_packed().numpy())
+    assert np.array_equal(gpu["stencil_words"].astype(np.int64), o.stencil_words_packed().numpy())
     _check32(wl, 200, gpu, st)
 
 
@@ -59,6 +60,7 @@ def test_swirl3d_f32_reactive_closed():
     o, st = oracle_run(wl, 30)
     gpu = gpu_run(wl, 30)
     assert np.array_equal(gpu["links"].astype(np.int64), o.links_packed().numpy())
+    assert np.array_equal(gpu["stencil_words"].astype(np.int64), o.stencil_words_packed().numpy())
     _check32(wl, 30, gpu, st)
     assert abs(gpu["scalars"]["P_th"] - st["P_th"]) / st["P_th"] < 1e-6
 
