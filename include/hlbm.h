@@ -184,6 +184,26 @@ lbm_status lbm_kernel_bytes(const lbm_ctx* ctx, double bytes[LBM_KERNEL_KINDS]);
 /* 1: capture pairs of steps in CUDA graphs (default), 0: launch directly. */
 lbm_status lbm_use_graphs(lbm_ctx* ctx, int enable);
 
+/* Allocation-free thermodynamic-pressure integral. The paper has no counterpart of this call;
+ * it serves callers that cannot allocate device memory (a host framework that owns every
+ * allocation through its own pool, code where cudaMalloc is forbidden or would synchronise the
+ * device, a monitor holding only pointers to fields made elsewhere).
+ * Computes I = sum over cells with mask == 0 of W / (R T rho_ref), W = (sum_k Y_k / W_k)^-1,
+ * with the kernel and exact fixed-point partial sums that lbm_step uses every step, and writes
+ * it to I_out. T [n_cells] and Y [n_species][n_cells] are FP32, mask [n_cells] uint8, I_out one
+ * double: all device pointers. W: n_species molar masses (kg/mol) in host memory. Work is
+ * enqueued on `stream` (NULL = legacy default stream); the call returns before it completes.
+ * It calls no allocator: per-block partial sums go to a static device array of 1 MiB that every
+ * GPU loading this library holds until the process exits, which limits n_cells to 16777216
+ * (larger sizes return LBM_ERR_ARG). The first call on a device resolves that array's device
+ * address (cudaGetSymbolAddress) and should therefore come before any stream capture on that
+ * device. All calls on a device share the array, so calls that overlap on the GPU (on
+ * different streams) race; nothing in the array needs to start at zero, since each call
+ * overwrites every slot it reads. err (may be NULL) receives a one-line message. */
+lbm_status lbm_pth_integral_noalloc(const float* T, const float* Y, const uint8_t* mask, int n_cells,
+                                   int n_species, const double* W, double T_ref, double rho_ref,
+                                   double* I_out, void* stream, char* err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

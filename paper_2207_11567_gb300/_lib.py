@@ -79,6 +79,8 @@ def _load():
         "lbm_kernel_times": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
         "lbm_kernel_bytes": (C.c_int, [P, C.POINTER(C.c_double)]),
         "lbm_use_graphs": (C.c_int, [P, C.c_int]),
+        "lbm_pth_integral_noalloc": (C.c_int, [P, P, P, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_double,
+                                               C.c_double, P, P, C.c_char_p, C.c_size_t]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -92,7 +94,7 @@ EXPORTED = ("lbm_init", "lbm_destroy", "lbm_last_error", "lbm_set_geometry", "lb
             "lbm_fields_size", "lbm_get_fields", "lbm_get_scalars", "lbm_get_links", "lbm_get_stencil_words",
             "lbm_state_bytes",
             "lbm_save_state", "lbm_load_state", "lbm_profile", "lbm_kernel_times", "lbm_kernel_bytes",
-            "lbm_use_graphs")
+            "lbm_use_graphs", "lbm_pth_integral_noalloc")
 
 
 class HLBMError(RuntimeError):
