@@ -49,7 +49,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -159,10 +159,15 @@ def oracle_sample(max_seconds=20.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="full", choices=["full", "mid"],
+                    help="mid: 192x96x96 cut of the same workload family, for small profiler captures")
+    ap.add_argument("--only", default=None, choices=["f32", "f16"],
+                    help="time one storage variant only (profiler captures)")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -191,9 +196,19 @@ def main():
         torch.cuda.set_device(0)
     dev_index = torch.cuda.current_device()
 
-    wl = W.make(WORKLOAD)
+    def make():
+        if args.case == "mid":
+            return W.generate.swirl_3d(192, 96, 96, reactive=True, seed=0)
+        return W.make(WORKLOAD)
+
+    if args.only:
+        r = run_variant(make(), args.only, args.steps, args.warmup, torch, profile_steps=2)
+        print(json.dumps({"case": args.case, "storage": args.only, "ms_per_step": r["ms"] / args.steps,
+                          "kernels": r["kernels"]}))
+        return
+    wl = make()
     # FP16-storage variant first (its own solver), then the FP32 headline
-    f16 = run_variant(W.make(WORKLOAD), "f16", args.steps, args.warmup, torch, profile_steps=10)
+    f16 = run_variant(make(), "f16", args.steps, args.warmup, torch, profile_steps=10)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -205,7 +220,7 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
         torch.distributed.barrier()
-    e2e_s, h2d, d2h = e2e_run(W.make(WORKLOAD), args.steps, torch)
+    e2e_s, h2d, d2h = (1.0, 0, 0) if args.no_e2e else e2e_run(make(), args.steps, torch)
     if rank != 0:
         torch.distributed.destroy_process_group()
         return

@@ -96,6 +96,8 @@ __global__ void stencil_words_kernel(int D, Geo g, const uint8_t* __restrict__ m
   out[r] = word;
 }
 
+// Equilibrium populations of Eq. 6 (with Eq. 4) for the given fields, in the arithmetic type R of
+// the storage (FP64 for FP64 storage, FP32 otherwise; FP64 is slow on this part).
 template <typename S, typename R>
 __global__ void set_fields_kernel(int D, Geo g, const double* __restrict__ T, const double* __restrict__ Y,
                                   int K, const double* __restrict__ invW, const double* __restrict__ u,
@@ -105,33 +107,38 @@ __global__ void set_fields_kernel(int D, Geo g, const double* __restrict__ T, co
   const int r = blockIdx.x * AUX_BLOCK + threadIdx.x;
   if (r >= g.N) return;
   const size_t N = (size_t)g.N;
-  double rho = 1.0;
+  R rho = R(1);
   if (thermal) {
-    double s = 0.0;
+    R s = R(0);
     for (int k = 0; k < K; ++k) {
-      s += Y[k * N + r] * invW[k];
-      Y_out[k * N + r] = (R)Y[k * N + r];
+      const R yk = (R)Y[k * N + r];
+      s += yk * (R)invW[k];
+      Y_out[k * N + r] = yk;
     }
-    rho = p_fac / (s * T[r]);  // P_th W / (R T rho_ref)
-    T_out[r] = (R)T[r];
+    const R Tr = (R)T[r];
+    rho = (R)p_fac / (s * Tr);  // P_th W / (R T rho_ref)
+    T_out[r] = Tr;
   }
-  const double ux = u[r], uy = u[N + r], uz = D == 3 ? u[2 * N + r] : 0.0;
-  u_out[r] = (R)ux;
-  u_out[N + r] = (R)uy;
-  if (D == 3) u_out[2 * N + r] = (R)uz;
-  rho_out[r] = (R)rho;
-  lam_out[r] = (R)0;
-  const double ph = P_h[r];
-  ph_out[r] = (R)ph;
+  const R ux = (R)u[r], uy = (R)u[N + r], uz = D == 3 ? (R)u[2 * N + r] : R(0);
+  u_out[r] = ux;
+  u_out[N + r] = uy;
+  if (D == 3) u_out[2 * N + r] = uz;
+  rho_out[r] = rho;
+  lam_out[r] = R(0);
+  const R ph = (R)P_h[r];
+  ph_out[r] = ph;
   const int Q = D == 2 ? 9 : 27;
-  const double usq = ux * ux + uy * uy + uz * uz;
+  const R usq = ux * ux + uy * uy + uz * uz;
+  const R third = R(1) / R(3);
   for (int i = 0; i < Q; ++i) {
-    const double w = D == 2 ? wgt<2>(i) : wgt<3>(i);
-    const double cu = cx(i) * ux + cy(i) * uy + (D == 3 ? cz(i) * uz : 0.0);
-    const double feq = w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);  // Eq. 4
-    double geq = w * (ph - rho / 3.0) + feq / 3.0;                          // Eq. 6
-    if (g_pert) geq += g_pert[(size_t)i * N + r];
-    g_out[(size_t)i * N + r] = (S)((R)((geq - w * P_ref) / w));
+    // q_i = g_eq,i / w_i - P_ref = (P_h - P_ref) + rho/3 (3 cu + 4.5 cu^2 - 1.5 u^2)
+    const R cu = (R)cx(i) * ux + (R)cy(i) * uy + (D == 3 ? (R)cz(i) * uz : R(0));
+    R q = (ph - (R)P_ref) + rho * third * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
+    if (g_pert) {
+      const R w = (R)(D == 2 ? wgt<2>(i) : wgt<3>(i));
+      q += (R)g_pert[(size_t)i * N + r] / w;
+    }
+    g_out[(size_t)i * N + r] = (S)q;
   }
 }
 

@@ -79,15 +79,25 @@ template <typename R> struct FDConst {
 // ---------------------------------------------------------------------------- storage
 // Populations are stored shifted: h = (g - w P_ref) / w. Loads return g.
 template <typename S, typename R> __device__ __forceinline__ R ld_pop(const S* p) { return (R)(*p); }
+// FP16: read the raw 16-bit word through the read-only path and reinterpret it, so that the
+// compiler can issue all loads of a cell back to back
 template <> __device__ __forceinline__ float ld_pop<__half, float>(const __half* p) {
-  return __half2float(__ldg(p));
+  return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
 }
 template <> __device__ __forceinline__ float ld_pop<float, float>(const float* p) { return __ldg(p); }
 template <> __device__ __forceinline__ double ld_pop<double, double>(const double* p) { return __ldg(p); }
 
+// raw load of the stored value (no conversion) and its conversion, for two-phase streaming
+template <typename S> __device__ __forceinline__ S ld_raw(const S* p) { return __ldg(p); }
+template <> __device__ __forceinline__ __half ld_raw<__half>(const __half* p) {
+  return __ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p)));
+}
+template <typename S, typename R> __device__ __forceinline__ R cvt_pop(S v) { return (R)v; }
+template <> __device__ __forceinline__ float cvt_pop<__half, float>(__half v) { return __half2float(v); }
+
 template <typename S, typename R> __device__ __forceinline__ void st_pop(S* p, R v) { *p = (S)v; }
 template <> __device__ __forceinline__ void st_pop<__half, float>(__half* p, float v) {
-  *p = __float2half_rn(v);
+  *reinterpret_cast<unsigned short*>(p) = __half_as_ushort(__float2half_rn(v));
 }
 
 template <typename R> __device__ __forceinline__ R ldg(const R* p) { return __ldg(p); }

@@ -127,7 +127,7 @@ template <> struct FDShape<2> { static constexpr int X = 32, Y = 8, Z = 1; };
 template <> struct FDShape<3> { static constexpr int X = 32, Y = 4, Z = 2; };
 
 template <int D, typename R>
-__global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? 3 : 1) fd_step_kernel(const FDArgs<R> a) {
+__global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? 4 : 1) fd_step_kernel(const FDArgs<R> a) {
   const FDConst<R>& c = a.c;
   const Geo& g = a.geo;
   const int x = blockIdx.x * FDShape<D>::X + threadIdx.x;
@@ -241,12 +241,23 @@ __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? 3 : 1) fd_step_kern
         const R m2 = k2[ax][0] == 2 ? phin : ldg(phi + i2[ax][0]);
         const R p1 = k1[ax][1] == NB_INLET ? phin : ldg(phi + i1[ax][1]);
         const R p2 = k2[ax][1] == 2 ? phin : ldg(phi + i2[ax][1]);
-        // select the upwind stencil first, then one reconstruction per face
+        // WENO3 written with the one-sided differences around r, shared by both faces and the
+        // diffusion flux: face = b + (t(d_bc) d_ab + 2 t(d_ab) d_bc) / (2 (t(d_bc) + 2 t(d_ab)))
+        // with t(d) = (eps + d^2)^2 (b the upwind value, d_ab, d_bc its upwind-side differences)
+        const R dm2 = m1 - m2, dm1 = pr - m1, dp1 = p1 - pr, dp2 = p2 - p1;
+        const R sm2 = fma(dm2, dm2, eps), sm1 = fma(dm1, dm1, eps), sp1 = fma(dp1, dp1, eps), sp2 = fma(dp2, dp2, eps);
+        const R tm2 = sm2 * sm2, tm1 = sm1 * sm1, tp1 = sp1 * sp1, tp2 = sp2 * sp2;
         const bool up = uf[ax][1] >= R(0), um = uf[ax][0] >= R(0);
-        const R fp = weno3<R>(up ? m1 : p2, up ? pr : p1, up ? p1 : pr, eps);
-        const R fm = weno3<R>(um ? m2 : p1, um ? m1 : pr, um ? pr : m1, eps);
+        // face r + 1/2: upwind (m1, r, p1) or (p2, p1, r)
+        const R bP = up ? pr : p1, dabP = up ? dm1 : -dp2, dbcP = up ? dp1 : -dp1;
+        const R tabP = up ? tm1 : tp2, tbcP = up ? tp1 : tp1;
+        // face r - 1/2: upwind (m2, m1, r) or (p1, r, m1)
+        const R bM = um ? m1 : pr, dabM = um ? dm2 : -dp1, dbcM = um ? dm1 : -dm1;
+        const R tabM = um ? tm2 : tp1, tbcM = um ? tm1 : tm1;
+        const R fp = bP + R(0.5) * fdiv<R>(tbcP * dabP + R(2) * tabP * dbcP, tbcP + R(2) * tabP);
+        const R fm = bM + R(0.5) * fdiv<R>(tbcM * dabM + R(2) * tabM * dbcM, tbcM + R(2) * tabM);
         adv += ur[ax] * (fp - fm);
-        dif += FMf[ax][1] * (p1 - pr) - FMf[ax][0] * (pr - m1);
+        dif += FMf[ax][1] * dp1 - FMf[ax][0] * dm1;
       }
       dif *= gfac * inv_rho;
       R src;

@@ -199,34 +199,27 @@ __global__ void __launch_bounds__(LB_BLOCK) lb_step_kernel(const LBArgs<R> a) {
 
   // ---------------------------------------------------------------- pull streaming
   // q_i = g_i / w_i - P_ref (the stored shifted form). Offsets fit in 32 bits (checked at init).
-  R q[Q];
+  // Per-axis offsets to the minus / plus neighbour, wrapped on periodic faces (a plain pull across
+  // a non-periodic face never happens: those links are bounce-back, inlet or outlet links).
+  // phase 1 issues every load into raw[] (storage type), phase 2 converts: all loads of a cell
+  // are in flight together whatever the storage type
+  S raw[Q];
   const int sy_ = nx, sz_ = nx * ny;
-  const bool interior = x > 0 && x < nx - 1 && y > 0 && y < ny - 1 && (D == 2 || (z > 0 && z < nz - 1));
   const int Ni = a.geo.N;
+  const int oxm = x > 0 ? -1 : nx - 1, oxp = x < nx - 1 ? 1 : 1 - nx;
+  const int oym = y > 0 ? -sy_ : (ny - 1) * sy_, oyp = y < ny - 1 ? sy_ : (1 - ny) * sy_;
+  const int ozm = z > 0 ? -sz_ : (nz - 1) * sz_, ozp = z < nz - 1 ? sz_ : (1 - nz) * sz_;
   const bool outlet_cell = x == nx - 1 && a.geo.bc_hi[0] == BC_OUTLET;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int ci = cx(i), cj = cy(i), ck = (D == 3) ? cz(i) : 0;
     if ((lw >> i) & 1u) {
-      q[i] = ld_pop<S, R>(gin + (Q - 1 - i) * Ni + r);
+      raw[i] = ld_raw<S>(gin + (Q - 1 - i) * Ni + r);
     } else {
-      int s;
-      if (interior) {
-        s = r - (ci + cj * sy_ + ck * sz_);
-      } else {
-        // only periodic faces remain for a plain pull
-        int sx = x - ci;
-        sx = sx < 0 ? nx - 1 : (sx >= nx ? 0 : sx);
-        int sy = y - cj;
-        sy = sy < 0 ? ny - 1 : (sy >= ny ? 0 : sy);
-        int sz = 0;
-        if (D == 3) {
-          sz = z - ck;
-          sz = sz < 0 ? nz - 1 : (sz >= nz ? 0 : sz);
-        }
-        s = sx + sy * sy_ + sz * sz_;
-      }
-      q[i] = ld_pop<S, R>(gin + i * Ni + s);
+      // source r - c_i
+      const int s = r + (ci == 1 ? oxm : (ci == -1 ? oxp : 0)) + (cj == 1 ? oym : (cj == -1 ? oyp : 0)) +
+                    (ck == 1 ? ozm : (ck == -1 ? ozp : 0));
+      raw[i] = ld_raw<S>(gin + i * Ni + s);
       if constexpr (THERMAL) {
         if (ci * ci + cj * cj + ck * ck == 1) {
           // direction -e_a pulls from r + e_a; +e_a pulls from r - e_a
@@ -241,6 +234,9 @@ __global__ void __launch_bounds__(LB_BLOCK) lb_step_kernel(const LBArgs<R> a) {
       }
     }
   }
+  R q[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) q[i] = cvt_pop<S, R>(raw[i]);
   // moving-wall term of the low-x inlet: g_i += 2 w_i rho (c_i . u_w)
   if (x == 0 && a.geo.bc_lo[0] == BC_INLET) {
     const int f = y + ny * z;
