@@ -87,6 +87,24 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_time_ms(ms, world):
+    """Max over ranks of a rank's timed-region duration (ms): the whole-job time of the
+    replicas. Uses the initialised process group (NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(cells, steps, world, ms):
+    """Whole-job throughput in MLUPS: every rank advances its own copy of the workload."""
+    return cells * steps * world / (ms * 1e-3) / 1e6
+
+
 def _timed_steps(solver, steps, torch):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     solver.synchronize()
@@ -214,11 +232,8 @@ def main():
     torch.cuda.synchronize()
     with Clocks(dev_index) as clk:
         f32 = run_variant(wl, "f32", args.steps, args.warmup, torch, profile_steps=10)
-    ms = f32["ms"]
+    ms = job_time_ms(f32["ms"], world)
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
         torch.distributed.barrier()
     e2e_s, h2d, d2h = (1.0, 0, 0) if args.no_e2e else e2e_run(make(), args.steps, torch)
     if rank != 0:
@@ -226,7 +241,7 @@ def main():
         return
 
     N = wl.N
-    value = N * args.steps * world / (ms * 1e-3) / 1e6
+    value = job_value(N, args.steps, world, ms)
     peak, peak_kind = _peaks()
     kern = f32["kernels"]
     dominant = max(kern, key=lambda k: kern[k]["ms_avg"] * kern[k]["launches"])

@@ -1,0 +1,43 @@
+"""Replica timing of bench.py across ranks: max over ranks and whole-job throughput, checked
+with two gloo ranks on the CPU."""
+import os
+import socket
+
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms = bench.job_time_ms(10.0 + 5.0 * rank, world)
+    q.put((rank, ms, bench.job_value(1000, 4, world, ms)))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_max():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [o[1] for o in out] == [15.0, 15.0]
+    # 1000 cells x 4 steps x 2 replicas in 15 ms
+    assert abs(out[0][2] - 1000 * 4 * 2 / 15e-3 / 1e6) < 1e-12
+
+
+def test_single_rank_is_unchanged():
+    import bench
+    assert bench.job_time_ms(7.5, 1) == 7.5
