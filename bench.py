@@ -186,6 +186,9 @@ def main():
     ap.add_argument("--only", default=None, choices=["f32", "f16"],
                     help="time one storage variant only (profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["c4_swirl_reactive_3d", "c3_swirl_cold_3d",
+                                                             "c2_chamber_2d"],
+                    help="benchmark configuration (default: the reactive swirl burner)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -198,7 +201,7 @@ def main():
         cb = oracle_sample(max_seconds=max(5.0, min(60.0, 2.0 * args.steps)))
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-                "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+                "dtype": "f64", "data": "synthetic", "config": {"workload": args.workload, "sample": cb["sample"]},
                 "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                                             "d2h_bytes_per_step": 0}, "vs_baseline": None}
         print(json.dumps(line))
@@ -216,8 +219,8 @@ def main():
 
     def make():
         if args.case == "mid":
-            return W.generate.swirl_3d(192, 96, 96, reactive=True, seed=0)
-        return W.make(WORKLOAD)
+            return W.generate.swirl_3d(192, 96, 96, reactive=args.workload != "c3_swirl_cold_3d", seed=0)
+        return W.make(args.workload)
 
     if args.only:
         r = run_variant(make(), args.only, args.steps, args.warmup, torch, profile_steps=2)
@@ -250,7 +253,7 @@ def main():
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
-            tr = json.load(f).get(f"{dominant}:{WORKLOAD}:f32")
+            tr = json.load(f).get(f"{dominant}:{args.workload}:f32")
             traffic = tr if tr else None
     except Exception:
         traffic = None
@@ -259,9 +262,12 @@ def main():
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [wl.cfg["nx"], wl.cfg["ny"], wl.cfg["nz"]], "cells": N,
-                   "lattice": "D3Q27", "collision": "cumulant+smagorinsky", "species": 6, "reactions": 2,
-                   "thicken_F": 8, "flame_sensor": True, "closed_domain": True, "storage": "f32",
+        "config": {"workload": args.workload, "grid": [wl.cfg["nx"], wl.cfg["ny"], wl.cfg["nz"]], "cells": N,
+                   "lattice": "D3Q27" if wl.cfg["dim"] == 3 else "D2Q9", "collision": "cumulant+smagorinsky",
+                   "species": len(wl.cfg.get("species", [])) if wl.cfg.get("thermal") else 0,
+                   "reactions": len(wl.cfg.get("reactions", [])) if wl.cfg.get("thermal") else 0,
+                   "thicken_F": wl.cfg.get("thicken_F"), "flame_sensor": wl.cfg.get("flame_sensor"),
+                   "closed_domain": wl.cfg.get("closed_domain"), "storage": "f32",
                    "parallelism": f"replicas{world}", "l2": "state 4.3 GB > L2, no flush needed"},
         "e2e": {"value": N * args.steps / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps,

@@ -149,6 +149,11 @@ lbm_status validate(const lbm_config* cfg, std::string& msg) {
                               !(cfg->sensor_wref > 0) || !(cfg->sensor_Ta >= 0)))
       return bad("invalid flame sensor parameters");
     if (!(cfg->thicken_F >= 1.0)) return bad("thicken_F must be >= 1");
+    for (int j = 0; j < cfg->n_reactions; ++j) {
+      int nz = 0;
+      for (int k = 0; k < cfg->n_species; ++k) nz += cfg->rx[j].order[k] != 0.0;
+      if (nz > 4) return bad("at most 4 species with a nonzero order per reaction");
+    }
   } else if (cfg->closed_domain || cfg->flame_sensor) {
     return bad("closed_domain and flame_sensor need thermal");
   }
@@ -223,10 +228,19 @@ template <typename R> void fill_fdconst(FDConst<R>& f, const lbm_config& c, int 
     const double ER = rx.E / R_GAS;
     f.ER_hi[j] = (R)ER;
     f.ER_lo[j] = (R)(ER - (double)f.ER_hi[j]);
+    double heat = 0.0;
+    f.nord[j] = 0;
     for (int k = 0; k < K; ++k) {
       f.nu[j][k] = (R)rx.nu[k];
       f.order[j][k] = (R)rx.order[k];
+      heat -= c.sp[k].hf * c.sp[k].W * rx.nu[k];
+      if (rx.order[k] != 0.0 && f.nord[j] < MAX_ORD) {
+        f.ord_k[j][f.nord[j]] = k;
+        f.ord_n[j][f.nord[j]] = (R)rx.order[k];
+        ++f.nord[j];
+      }
     }
+    f.heat[j] = (R)heat;
   }
   f.I_scale = (R)I_unit;
   f.M_scale = (R)16.0;

@@ -16,6 +16,7 @@ enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET = 2, BC_OUTLET = 3 };
 enum { COLL_BGK = 0, COLL_CUMULANT = 1, COLL_CUMULANT_FULL = 2 };
 constexpr int MAX_SP = 8;
 constexpr int MAX_RX = 4;
+constexpr int MAX_ORD = 4;  // species with a nonzero order in one reaction
 
 template <int D> struct Lat;
 template <> struct Lat<2> { static constexpr int Q = 9; };
@@ -72,6 +73,11 @@ template <typename R> struct FDConst {
   // float path (float-float argument); the double path uses ER_hi = E/R and ER_lo = 0.
   R A[MAX_RX], beta[MAX_RX], ER_hi[MAX_RX], ER_lo[MAX_RX];
   R nu[MAX_RX][MAX_SP], order[MAX_RX][MAX_SP];
+  // compact form: the species with a nonzero order in each reaction, and the heat released per
+  // mole of each reaction, -sum_k h_f,k W_k nu_jk (J/mol)
+  int nord[MAX_RX], ord_k[MAX_RX][MAX_ORD];
+  R ord_n[MAX_RX][MAX_ORD];
+  R heat[MAX_RX];
   R I_scale;              // integrand -> O(1) before the reduction
   R M_scale;              // mass flux -> O(1) before the reduction
 };
@@ -126,6 +132,10 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
 
 // ---------------------------------------------------------------------------- kernel arguments
 constexpr int LB_BLOCK = 128;
+// resident blocks per SM the register allocation aims for (6: 80 registers, no spill)
+#ifndef LB_MIN_BLOCKS
+#define LB_MIN_BLOCKS 6
+#endif
 
 template <typename R> struct LBArgs {
   Geo geo;

@@ -74,12 +74,13 @@ template <typename R> __device__ __forceinline__ R weno3(R a, R b, R c, R eps) {
   return fdiv<R>(t1 * q0 + R(2) * t0 * q1, t1 + R(2) * t0);
 }
 
-// Reaction rates q_j (mol/(m^3 s)) of one cell.
-template <typename R>
+// Reaction rates q_j (mol/(m^3 s)) of one cell. NR > 0: reaction count known at compile time.
+template <int NR, typename R>
 __device__ __forceinline__ void reaction_rates(const FDConst<R>& c, R T, const R* Y, R rho_phys, R* q) {
+  const int nr = NR > 0 ? NR : c.nrx;
 #pragma unroll
-  for (int j = 0; j < MAX_RX; ++j) {
-    if (j >= c.nrx) break;
+  for (int j = 0; j < (NR > 0 ? NR : MAX_RX); ++j) {
+    if (NR == 0 && j >= nr) break;
     R v;
     if constexpr (sizeof(R) == 4) {
       v = c.A[j] * arrhenius(c.ER_hi[j], c.ER_lo[j], T);
@@ -88,13 +89,12 @@ __device__ __forceinline__ void reaction_rates(const FDConst<R>& c, R T, const R
     }
     if (c.beta[j] != R(0)) v *= powr<R>(T, c.beta[j]);
 #pragma unroll
-    for (int k = 0; k < MAX_SP; ++k) {
-      if (k >= c.K) break;
-      const R n = c.order[j][k];
-      if (n != R(0)) {
-        const R conc = rho_phys * fmax(Y[k], R(0)) * (R)c.inv_W[k];
-        v *= (n == R(1)) ? conc : powr<R>(conc, n);
-      }
+    for (int m = 0; m < MAX_ORD; ++m) {
+      if (m >= c.nord[j]) break;
+      const int k = c.ord_k[j][m];
+      const R n = c.ord_n[j][m];
+      const R conc = rho_phys * fmax(Y[k], R(0)) * c.inv_W[k];
+      v *= (n == R(1)) ? conc : powr<R>(conc, n);
     }
     q[j] = v;
   }
@@ -126,7 +126,9 @@ template <int D> struct FDShape;
 template <> struct FDShape<2> { static constexpr int X = 32, Y = 8, Z = 1; };
 template <> struct FDShape<3> { static constexpr int X = 32, Y = 4, Z = 2; };
 
-template <int D, typename R>
+// NK, NR > 0: species and reaction counts known at compile time (loops unroll exactly);
+// NK = NR = 0: counts read from the constants at run time.
+template <int D, typename R, int NK, int NR>
 __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? 4 : 1) fd_step_kernel(const FDArgs<R> a) {
   const FDConst<R>& c = a.c;
   const Geo& g = a.geo;
@@ -164,12 +166,16 @@ __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? 4 : 1) fd_step_kern
       }
     }
     // local state
+    constexpr int KMAX = NK > 0 ? NK : MAX_SP;
+    constexpr int RMAX = NR > 0 ? NR : MAX_RX;
+    const int K = NK > 0 ? NK : c.K;
+    const int nrx = NR > 0 ? NR : c.nrx;
     const R Tr = ldg(a.T + r);
-    R Yr[MAX_SP];
+    R Yr[KMAX];
     R sW = R(0);
 #pragma unroll
-    for (int k = 0; k < MAX_SP; ++k) {
-      if (k < c.K) {
+    for (int k = 0; k < KMAX; ++k) {
+      if (NK > 0 || k < K) {
         Yr[k] = ldg(a.Y + k * N + r);
         sW += Yr[k] * c.inv_W[k];
       } else {
@@ -181,8 +187,8 @@ __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? 4 : 1) fd_step_kern
     const R rho = fdr * W / Tr;  // lattice units
     const R rho_phys = rho / c.inv_rho_ref;
     const R inv_rho = R(1) / rho;
-    R q[MAX_RX];
-    reaction_rates<R>(c, Tr, Yr, rho_phys, q);
+    R q[RMAX];
+    reaction_rates<NR, R>(c, Tr, Yr, rho_phys, q);
     const R Fr = a.Floc ? ldg(a.Floc + r) : c.F;
     const R mur = c.nu_lat * powr<R>(Tr * c.T_ref_inv, c.mu_exp);
     R ur[3] = {ldg(a.u + r), ldg(a.u + N + r), D == 3 ? ldg(a.u + 2 * N + r) : R(0)};
@@ -213,21 +219,15 @@ __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? 4 : 1) fd_step_kern
     const R inv_rpF = R(1) / (rho_phys * Fr);
     R qdot = R(0);
 #pragma unroll
-    for (int j = 0; j < MAX_RX; ++j) {
-      if (j >= c.nrx) break;
-      R hsum = R(0);
-#pragma unroll
-      for (int k = 0; k < MAX_SP; ++k)
-        if (k < c.K) hsum += c.hf_W[k] * c.nu[j][k];
-      qdot -= hsum * q[j];
-    }
+    for (int j = 0; j < RMAX; ++j)
+      if (NR > 0 || j < nrx) qdot += c.heat[j] * q[j];
     const R fd_dT = sizeof(R) == 4 ? (R)a.pth->fd_dT : (R)a.pth->fd_dT_d;
     R lam = R(0);
     R sWn = R(0);
     R Tnew = Tr;
     // fields: 0 = T, 1.. = Y_k
 #pragma unroll 1
-    for (int fi = 0; fi <= c.K; ++fi) {
+    for (int fi = 0; fi <= K; ++fi) {
       const R* phi = fi == 0 ? a.T : a.Y + (size_t)(fi - 1) * N;
       const R phin = fi == 0 ? c.T_in : c.Y_in[fi - 1];
       const R eps = fi == 0 ? c.eps_T : c.eps_Y;
@@ -266,8 +266,8 @@ __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? 4 : 1) fd_step_kern
       } else {
         R om = R(0);
 #pragma unroll
-        for (int j = 0; j < MAX_RX; ++j)
-          if (j < c.nrx) om += c.nu[j][fi - 1] * q[j];
+        for (int j = 0; j < RMAX; ++j)
+          if (NR > 0 || j < nrx) om += c.nu[j][fi - 1] * q[j];
         src = dt * c.W[fi - 1] * om * inv_rpF;
       }
       const R NA = dif + src;
@@ -347,7 +347,10 @@ cudaError_t launch_fd(const FDArgs<R>& a, cudaStream_t st, bool sensor_pass) {
     const int grid = (a.geo.N + FD_BLOCK - 1) / FD_BLOCK;
     flame_sensor_kernel<D, R><<<grid, FD_BLOCK, 0, st>>>(a);
   } else {
-    fd_step_kernel<D, R><<<fd_grid<D>(a.geo), dim3(FDShape<D>::X, FDShape<D>::Y, FDShape<D>::Z), 0, st>>>(a);
+    const dim3 grid = fd_grid<D>(a.geo), block(FDShape<D>::X, FDShape<D>::Y, FDShape<D>::Z);
+    if (a.c.K == 6 && a.c.nrx == 2) fd_step_kernel<D, R, 6, 2><<<grid, block, 0, st>>>(a);
+    else if (a.c.K == 4 && a.c.nrx == 1) fd_step_kernel<D, R, 4, 1><<<grid, block, 0, st>>>(a);
+    else fd_step_kernel<D, R, 0, 0><<<grid, block, 0, st>>>(a);
   }
   return cudaGetLastError();
 }

@@ -173,7 +173,7 @@ __device__ __forceinline__ void add_delta_eq(R* m, const R* dx, const R* dy, con
 }
 
 template <int D, typename S, typename R, bool THERMAL, int COLL>
-__global__ void __launch_bounds__(LB_BLOCK) lb_step_kernel(const LBArgs<R> a) {
+__global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const LBArgs<R> a) {
   constexpr int Q = Lat<D>::Q;
   const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz;
   // one block row of LB_BLOCK cells along x; y and z come from the grid (no integer division)
