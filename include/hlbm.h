@@ -181,6 +181,32 @@ lbm_status lbm_kernel_times(lbm_ctx* ctx, double ms[LBM_KERNEL_KINDS], long long
 /* Algorithmic bytes of one launch of each kernel kind (each array touched once). */
 lbm_status lbm_kernel_bytes(const lbm_ctx* ctx, double bytes[LBM_KERNEL_KINDS]);
 
+/* Adjoint of one step (discrete reverse mode; the paper has no adjoint, this is the exact
+ * transpose of lbm_step's update: LB stream-collide, bounce-back, inlet and outlet rules,
+ * FD transport and chemistry). Supported: 2-D, FP32 or FP64 storage, cumulant collision with the
+ * default higher-order rates, open domain, constant thickening factor (LBM_ERR_UNSUPPORTED
+ * otherwise). state_n: device copy of state n in the lbm_save_state layout. adj: device buffer
+ * in the same layout and types holding the adjoint of state n+1 (populations in the stored
+ * shifted form); overwritten with the adjoint of state n. grad_inlet: device array [dim][ny] of
+ * the field type to which the adjoint of the inlet-face velocity is added. The context's own
+ * state is replaced by state_n (used to recompute the forward step). Upwind choices and the
+ * max(Y, 0) of the rate law are held fixed (derivative 0 across their switches). */
+lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* state_n, void* adj, void* grad_inlet);
+
+/* Objective J = sum over fluid cells of the fuel consumption rate -omega_F (kg/(m^3 s), lattice
+ * cell volume 1) of the context's current state, written to *J (host), and its gradient with
+ * respect to the state written to adj_out (device, lbm_save_state layout: T and Y parts filled,
+ * populations and velocity zero). Same support as lbm_adjoint_step. Synchronises the stream. */
+lbm_status lbm_fuel_objective(lbm_ctx* ctx, int fuel_species, double* J, void* adj_out);
+
+/* Gradient with respect to the initial temperature field: reverse of lbm_set_fields, whose
+ * populations are the equilibrium of Eq. 6 with rho = P_th W / (R T) (Eq. 13), so that T enters
+ * both T itself and the populations. state0: device copy of the state lbm_set_fields produced
+ * (lbm_save_state layout; it becomes the context's state); adj0: device adjoint of that state;
+ * grad_T0: device array [N] of the field type, overwritten with dJ/dT0. Same support as
+ * lbm_adjoint_step, thermal runs only. */
+lbm_status lbm_initial_T_adjoint(lbm_ctx* ctx, const void* state0, const void* adj0, void* grad_T0);
+
 /* 1: capture pairs of steps in CUDA graphs (default), 0: launch directly. */
 lbm_status lbm_use_graphs(lbm_ctx* ctx, int enable);
 

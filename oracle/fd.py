@@ -48,13 +48,17 @@ def mean_molar_mass(p, Y):
 
 
 def reaction_rates(p, T, Y, rho_phys):
-    """q_j [mol/(m^3 s)] for every reaction, list of [N] tensors."""
+    """q_j [mol/(m^3 s)] for every reaction, list of [N] tensors.
+
+    [X]^n is taken as 0 where Y <= 0, with derivative 0 there (the base is replaced by 1
+    before the power so that reverse-mode differentiation stays finite)."""
     out = []
     for rx in p.reactions:
         q = rx["A"] * T ** rx["beta"] * torch.exp(-rx["E"] / (R_GAS * T))
         for k, n in rx["order"].items():
-            conc = rho_phys * torch.clamp(Y[k], min=0.0) / p.W[k]
-            q = q * conc ** n
+            pos = Y[k] > 0
+            conc = rho_phys * torch.where(pos, Y[k], torch.ones_like(Y[k])) / p.W[k]
+            q = q * torch.where(pos, conc ** n, torch.zeros_like(conc))
         out.append(q)
     return out
 
@@ -140,3 +144,12 @@ def fd_update(p, grid, nb, T, Y, u, uin_r, P_th, dP_lag):
 def pth_integrand(p, T, Y):
     """W / (R T rho_ref): thermodynamic-pressure integrand per fluid cell (cell volume 1)."""
     return mean_molar_mass(p, Y) / (R_GAS * T * p.rho_ref)
+
+
+def fuel_consumption(p, T, Y, P_th, fluid, fuel):
+    """Objective of the adjoint tests (not in the paper): J = sum over fluid cells of the fuel
+    consumption rate -omega_F [kg/(m^3 s)] of the rate law above, cell volume 1."""
+    W = mean_molar_mass(p, Y)
+    rho_phys = P_th * W / (R_GAS * T)
+    om = species_rates(p, reaction_rates(p, T, Y, rho_phys))[fuel]
+    return -(om.expand_as(T)[fluid]).sum()

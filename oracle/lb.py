@@ -93,7 +93,9 @@ def tau_smagorinsky(lat, h, u, tau0, cs_smag):
     tr = sum(Pi[a, a] for a in range(d)) / d
     for a in range(d):
         Pi[a, a] = Pi[a, a] - tr
-    norm = torch.sqrt((Pi * Pi).sum((0, 1)))
+    n2 = (Pi * Pi).sum((0, 1))
+    # |Pi|, with derivative 0 where Pi = 0 (square root of a positive placeholder there)
+    norm = torch.where(n2 > 0, torch.sqrt(torch.where(n2 > 0, n2, torch.ones_like(n2))), torch.zeros_like(n2))
     return 0.5 * (tau0 + torch.sqrt(tau0 * tau0 + 18.0 * math.sqrt(2.0) * cs_smag ** 2 * norm))
 
 

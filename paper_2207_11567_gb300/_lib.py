@@ -79,6 +79,9 @@ def _load():
         "lbm_kernel_times": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
         "lbm_kernel_bytes": (C.c_int, [P, C.POINTER(C.c_double)]),
         "lbm_use_graphs": (C.c_int, [P, C.c_int]),
+        "lbm_adjoint_step": (C.c_int, [P, P, P, P]),
+        "lbm_fuel_objective": (C.c_int, [P, C.c_int, C.POINTER(C.c_double), P]),
+        "lbm_initial_T_adjoint": (C.c_int, [P, P, P, P]),
         "lbm_pth_integral_noalloc": (C.c_int, [P, P, P, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_double,
                                                C.c_double, P, P, C.c_char_p, C.c_size_t]),
     }
@@ -94,7 +97,8 @@ EXPORTED = ("lbm_init", "lbm_destroy", "lbm_last_error", "lbm_set_geometry", "lb
             "lbm_fields_size", "lbm_get_fields", "lbm_get_scalars", "lbm_get_links", "lbm_get_stencil_words",
             "lbm_state_bytes",
             "lbm_save_state", "lbm_load_state", "lbm_profile", "lbm_kernel_times", "lbm_kernel_bytes",
-            "lbm_use_graphs", "lbm_pth_integral_noalloc")
+            "lbm_use_graphs", "lbm_pth_integral_noalloc", "lbm_adjoint_step", "lbm_fuel_objective",
+            "lbm_initial_T_adjoint")
 
 
 class HLBMError(RuntimeError):

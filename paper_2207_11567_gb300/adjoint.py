@@ -1,0 +1,102 @@
+"""Gradient of a combustion functional through K steps of the hybrid solver: discrete adjoint
+(reverse mode) with checkpointing, behind ``torch.autograd.Function``.
+
+The paper computes no gradients; this is the exact transpose of the discrete step the library
+runs (lbm_adjoint_step), chained over the steps. The functional is the fuel consumption at the
+last step, J = sum over fluid cells of -omega_F(T^K, Y^K) (lbm_fuel_objective); its parameters
+are the inlet-face velocity (the boundary data of the inlet rule) and the initial temperature
+field T0 (which sets T^0 and, through rho = P_th W / (R T) of Eq. 13, the initial equilibrium
+populations of Eq. 6).
+
+Forward: set the inlet and the initial fields, run K steps, saving the state every C steps.
+Backward: for each segment, last first, reload its checkpoint, recompute and keep the segment's
+states, then apply lbm_adjoint_step from the segment's last step down to its first, which also
+adds the inlet-velocity adjoint; lbm_initial_T_adjoint turns the adjoint of state 0 into dJ/dT0.
+Memory: K/C checkpoints plus C states, each ``Solver.state_bytes()`` of device memory.
+Every arithmetic step runs in the library's CUDA kernels; this module only orders the calls.
+"""
+import numpy as np
+import torch
+
+from .solver import Solver
+
+
+class AdjointProblem:
+    """A fixed geometry, initial composition, velocity and pressure, step count and checkpoint
+    interval; J and its gradient are functions of the inlet velocity and of T0."""
+
+    def __init__(self, cfg, mask, Y0, u0=None, P_h0=None, g_pert=None, n_steps=100, checkpoint_every=100,
+                 fuel=0, device=None):
+        if not cfg.get("thermal"):
+            raise ValueError("the fuel-consumption functional needs a thermal configuration")
+        self.cfg = cfg
+        self.mask = np.asarray(mask)
+        self.Y0, self.u0, self.P_h0, self.g_pert = Y0, u0, P_h0, g_pert
+        self.n_steps = int(n_steps)
+        self.C = max(1, int(checkpoint_every))
+        self.fuel = int(fuel)
+        self.solver = Solver(cfg, self.mask, None, device=device)
+        self.dtype = torch.float64 if cfg.get("storage", "f32") == "f64" else torch.float32
+        esize = 8 if self.dtype == torch.float64 else 4
+        self.n_words = (self.solver.state_bytes() + esize - 1) // esize
+        self.dim, self.ny = cfg["dim"], cfg["ny"]
+        self._ckpt = []
+
+    def close(self):
+        self.solver.close()
+
+    def _zeros(self, n):
+        return torch.zeros(n, dtype=self.dtype, device=self.solver.device)
+
+    def forward(self, inlet_u, T0):
+        """Run the K steps from (inlet_u [dim][ny], T0 [N]); returns J and keeps checkpoints."""
+        s = self.solver
+        s.set_geometry(self.mask, np.asarray(inlet_u, dtype=np.float64).reshape(self.dim, self.ny))
+        s.set_fields(T=np.asarray(T0, dtype=np.float64), Y=self.Y0, u=self.u0, P_h=self.P_h0, g_pert=self.g_pert)
+        self._ckpt = []
+        for n in range(self.n_steps):
+            if n % self.C == 0:
+                self._ckpt.append(s.save_state())
+            s.step(1)
+        self._adjK = self._zeros(self.n_words)
+        return s.fuel_objective(self.fuel, self._adjK)
+
+    def backward(self, scale=1.0):
+        """dJ/d(inlet_u) [dim][ny] and dJ/dT0 [N] for the last forward call (storage type)."""
+        if not self._ckpt:
+            raise RuntimeError("backward needs a forward call first")
+        s = self.solver
+        adj = self._adjK * scale
+        gin = self._zeros(self.dim * self.ny)
+        for seg in reversed(range(len(self._ckpt))):
+            n0 = seg * self.C
+            n1 = min(n0 + self.C, self.n_steps)
+            states = [self._ckpt[seg]]
+            if n1 - n0 > 1:
+                s.load_state(self._ckpt[seg])
+                for _ in range(n0 + 1, n1):
+                    s.step(1)
+                    states.append(s.save_state())
+            for n in reversed(range(n0, n1)):
+                s.adjoint_step(states[n - n0], adj, gin)
+        gT = self._zeros(s.N)
+        s.initial_T_adjoint(self._ckpt[0], adj, gT)
+        return gin.reshape(self.dim, self.ny), gT
+
+
+class HybridStepFn(torch.autograd.Function):
+    """J = HybridStepFn.apply(inlet_u, T0, problem): the fuel consumption after the problem's K
+    steps, differentiable with respect to the inlet-face velocity and the initial temperature."""
+
+    @staticmethod
+    def forward(ctx, inlet_u, T0, problem):
+        ctx.problem = problem
+        ctx.meta = (inlet_u.dtype, inlet_u.device, T0.dtype, T0.device)
+        J = problem.forward(inlet_u.detach().cpu().numpy(), T0.detach().cpu().numpy())
+        return torch.tensor(J, dtype=torch.float64, device=inlet_u.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        gin, gT = ctx.problem.backward(float(gJ))
+        idt, idev, tdt, tdev = ctx.meta
+        return gin.to(dtype=idt, device=idev), gT.to(dtype=tdt, device=tdev), None

@@ -1,0 +1,181 @@
+// Adjoint step and objective of the 2-D hybrid step (not in the paper): the exact discrete
+// reverse of one lbm_step (FD update -> LB stream-collide), and the fuel-consumption objective
+// J = sum over fluid cells of the fuel consumption rate -omega_F with its gradient.
+#include "adjoint_fd.cuh"
+#include "adjoint_lb.cuh"
+#include "fd_kernel.cuh"
+#include "launch.h"
+
+namespace hlbm {
+
+namespace {
+
+// J = sum_fluid -omega_F(T, Y) (kg/(m^3 s) per unit lattice volume) and dJ/dT, dJ/dY.
+template <typename R>
+__global__ void fuel_objective_kernel(FDArgs<R> a, int fuel, R* __restrict__ Tbar, R* __restrict__ Ybar,
+                                      double* __restrict__ partials) {
+  const FDConst<R>& c = a.c;
+  const int r = blockIdx.x * FD_BLOCK + threadIdx.x;
+  const int N = a.geo.N;
+  double v = 0.0;
+  if (r < N) {
+    const uint32_t sw = __ldg(a.sword + r);
+    R Tb = R(0);
+    R Yb[MAX_SP];
+    for (int k = 0; k < MAX_SP; ++k) Yb[k] = R(0);
+    if (sw >> 31) {
+      const R Tr = a.T[r];
+      R Yr[MAX_SP];
+      R sW = R(0);
+      for (int k = 0; k < c.K; ++k) {
+        Yr[k] = a.Y[k * N + r];
+        sW += Yr[k] * c.inv_W[k];
+      }
+      const R W = R(1) / sW;
+      const R fdr = sizeof(R) == 4 ? (R)a.pth->fd_rho : (R)a.pth->fd_rho_d;
+      const R rho = fdr * W / Tr;
+      const R rho_phys = rho / c.inv_rho_ref;
+      R rpb = R(0), Wb = R(0);
+      for (int j = 0; j < c.nrx; ++j) {
+        R q = c.A[j] * exp(-(c.ER_hi[j] + c.ER_lo[j]) / Tr);
+        if (c.beta[j] != R(0)) q *= pow(Tr, c.beta[j]);
+        for (int m = 0; m < c.nord[j]; ++m) {
+          const int k = c.ord_k[j][m];
+          q *= Yr[k] > R(0) ? pow(rho_phys * Yr[k] * c.inv_W[k], c.ord_n[j][m]) : R(0);
+        }
+        const R wj = -c.W[fuel] * c.nu[j][fuel];  // J = sum_j wj q_j
+        v += (double)(wj * q);
+        const R qq = wj * q;
+        Tb += qq * ((c.ER_hi[j] + c.ER_lo[j]) / (Tr * Tr) + c.beta[j] / Tr);
+        for (int m = 0; m < c.nord[j]; ++m) {
+          const int k = c.ord_k[j][m];
+          if (Yr[k] > R(0)) {
+            rpb += qq * c.ord_n[j][m] / rho_phys;
+            Yb[k] += qq * c.ord_n[j][m] / Yr[k];
+          }
+        }
+      }
+      const R rhob = rpb / c.inv_rho_ref;
+      Wb += rhob * fdr / Tr;
+      Tb -= rhob * rho / Tr;
+      const R sWb = -Wb * W * W;
+      for (int k = 0; k < c.K; ++k) Yb[k] += sWb * c.inv_W[k];
+    }
+    Tbar[r] = Tb;
+    for (int k = 0; k < c.K; ++k) Ybar[(size_t)k * N + r] = Yb[k];
+  }
+  __shared__ double sh[FD_BLOCK];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = FD_BLOCK / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+// Reverse of lbm_set_fields with respect to T: the initial populations are the equilibrium
+// q_i = (P_h - P_ref) + rho (c_i.u + 1.5 (c_i.u)^2 - 0.5 u^2) (shifted form) with
+// rho = P_th W / (R T rho_ref), so dJ/dT = Tbar + sum_i qbar_i (c_i.u + 1.5 (c_i.u)^2 - 0.5 u^2) (-rho / T).
+template <typename R>
+__global__ void initial_T_adjoint_kernel(FDArgs<R> a, const R* __restrict__ adj0, R* __restrict__ gradT) {
+  const int r = blockIdx.x * FD_BLOCK + threadIdx.x;
+  const int N = a.geo.N;
+  if (r >= N) return;
+  const R Tb = adj0[(size_t)11 * N + r];
+  if (!(__ldg(a.sword + r) >> 31)) {
+    gradT[r] = Tb;
+    return;
+  }
+  const FDConst<R>& c = a.c;
+  const R Tr = a.T[r];
+  R sW = R(0);
+  for (int k = 0; k < c.K; ++k) sW += a.Y[(size_t)k * N + r] * c.inv_W[k];
+  const R fdr = sizeof(R) == 4 ? (R)a.pth->fd_rho : (R)a.pth->fd_rho_d;
+  const R rho = fdr / (sW * Tr);
+  const R ux = a.u[r], uy = a.u[N + r];
+  const R usq = ux * ux + uy * uy;
+  R rb = R(0);
+  for (int i = 0; i < 9; ++i) {
+    const R cu = (R)cx(i) * ux + (R)cy(i) * uy;
+    rb += adj0[(size_t)i * N + r] * (cu + R(1.5) * cu * cu - R(0.5) * usq);
+  }
+  gradT[r] = Tb - rb * rho / Tr;
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_initial_T_adjoint(const FDArgs<R>& fdf, const R* adj0, R* gradT, cudaStream_t st) {
+  initial_T_adjoint_kernel<R><<<(fdf.geo.N + FD_BLOCK - 1) / FD_BLOCK, FD_BLOCK, 0, st>>>(fdf, adj0, gradT);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_adjoint_step2d(const AdjBuffers<R>& b, const LBArgs<R>& lbf, const FDArgs<R>& fdf, bool thermal,
+                                  cudaStream_t st) {
+  const Geo& g = lbf.geo;
+  const int N = g.N, K = thermal ? fdf.c.K : 0;
+  cudaError_t e;
+  const size_t Rs = sizeof(R);
+  if ((e = cudaMemsetAsync(b.gbar_in, 0, 9 * (size_t)N * Rs, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(b.rho_own, 0, (size_t)N * Rs, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(b.lam_bar, 0, (size_t)N * Rs, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(b.T_lb, 0, (size_t)N * Rs, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(b.u_lb, 0, 2 * (size_t)N * Rs, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(b.rho_nb, 0, 4 * (size_t)N * Rs, st)) != cudaSuccess) return e;
+  LBAdjArgs<R> la{};
+  la.f = lbf;
+  la.u_prev = (const R*)lbf.u;
+  la.gbar_out = b.g_adj;
+  la.ubar_out = b.u_adj;
+  la.gbar_in = b.gbar_in;
+  la.rho_bar = b.rho_own;
+  la.lam_bar = b.lam_bar;
+  la.T_bar = b.T_lb;
+  la.u_bar = b.u_lb;
+  la.rho_nb = b.rho_nb;
+  la.inlet_bar = b.inlet_bar;
+  const dim3 lgrid((g.nx + LB_BLOCK - 1) / LB_BLOCK, g.ny, 1);
+  if (thermal) lb_adjoint_kernel<R, true><<<lgrid, LB_BLOCK, 0, st>>>(la);
+  else lb_adjoint_kernel<R, false><<<lgrid, LB_BLOCK, 0, st>>>(la);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int fb = (N + FD_BLOCK - 1) / FD_BLOCK;
+  if (thermal) {
+    rho_adjoint_gather<R><<<fb, FD_BLOCK, 0, st>>>(g, lbf.links, b.rho_own, b.rho_nb, b.rho_tot);
+    FDAdjArgs<R> fa{};
+    fa.f = fdf;
+    fa.Tbar_out = b.T_adj;
+    fa.Ybar_out = b.Y_adj;
+    fa.rho_bar = b.rho_tot;
+    fa.lam_bar = b.lam_bar;
+    fa.slots = b.slots;
+    fa.u_bar = b.u_fd;
+    fd_adjoint_kernel<R><<<fb, FD_BLOCK, 0, st>>>(fa);
+    fd_adjoint_gather<R><<<fb, FD_BLOCK, 0, st>>>(g, fdf.sword, K, b.slots, b.T_lb, b.u_fd, b.u_lb, b.T_new, b.Y_new,
+                                                   b.u_new);
+  } else {
+    if ((e = cudaMemcpyAsync(b.u_new, b.u_lb, 2 * (size_t)N * Rs, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+      return e;
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_fuel_objective(const FDArgs<R>& fdf, int fuel, R* Tbar, R* Ybar, double* partials, int nblocks,
+                                  cudaStream_t st) {
+  fuel_objective_kernel<R><<<nblocks, FD_BLOCK, 0, st>>>(fdf, fuel, Tbar, Ybar, partials);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_adjoint_step2d<float>(const AdjBuffers<float>&, const LBArgs<float>&, const FDArgs<float>&,
+                                                  bool, cudaStream_t);
+template cudaError_t launch_adjoint_step2d<double>(const AdjBuffers<double>&, const LBArgs<double>&,
+                                                   const FDArgs<double>&, bool, cudaStream_t);
+template cudaError_t launch_initial_T_adjoint<float>(const FDArgs<float>&, const float*, float*, cudaStream_t);
+template cudaError_t launch_initial_T_adjoint<double>(const FDArgs<double>&, const double*, double*, cudaStream_t);
+template cudaError_t launch_fuel_objective<float>(const FDArgs<float>&, int, float*, float*, double*, int, cudaStream_t);
+template cudaError_t launch_fuel_objective<double>(const FDArgs<double>&, int, double*, double*, double*, int,
+                                                   cudaStream_t);
+
+}  // namespace hlbm

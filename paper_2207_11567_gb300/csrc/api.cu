@@ -63,6 +63,9 @@ struct lbm_ctx {
   // graphs
   bool use_graphs = true;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // adjoint workspace (allocated on the first adjoint call)
+  void* adj_ws = nullptr;
+  double* obj_partials = nullptr;
   // profiling
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -561,6 +564,16 @@ lbm_status lbm_set_fields(lbm_ctx* ctx, const double* T, const double* Y, const 
                                           (float*)ctx->lam, (float*)ctx->ph, ctx->st);
     if (e != cudaSuccess) st = cuda_fail(ctx, e, "set_fields kernel");
   }
+  // the second buffer of each double-buffered field starts as a copy, so that cells a step
+  // never writes (solid cells) hold defined values in both (saved states are then defined)
+  if (st == LBM_OK) {
+    cudaError_t e = cudaMemcpyAsync(ctx->g[1], ctx->g[0], Q * N * ctx->S, cudaMemcpyDeviceToDevice, ctx->st);
+    if (e == cudaSuccess && c.thermal)
+      e = cudaMemcpyAsync(ctx->T[1], ctx->T[0], N * ctx->F, cudaMemcpyDeviceToDevice, ctx->st);
+    if (e == cudaSuccess && c.thermal)
+      e = cudaMemcpyAsync(ctx->Y[1], ctx->Y[0], K * N * ctx->F, cudaMemcpyDeviceToDevice, ctx->st);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "copy fields");
+  }
   // thermodynamic-pressure state: P = P_th0, M = P_th0 * I0 (same arithmetic as every step)
   PthState ps{};
   ps.P = c.P_th0;
@@ -800,6 +813,129 @@ lbm_status lbm_kernel_bytes(const lbm_ctx* ctx, double bytes[LBM_KERNEL_KINDS]) 
   // LB: populations read + written, link word, and (thermal) rho, Lambda, T read + u written
   bytes[KIND_LB] = Nf * (2.0 * Q * S + (th ? (3.0 + D) * F : 0.0)) + 4.0 * N;
   return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename R> lbm_status adjoint_step_impl(lbm_ctx* ctx, const void* state_n, void* adj, void* grad_inlet) {
+  const size_t N = ctx->N;
+  const int K = ctx->K;
+  const bool th = ctx->cfg.thermal != 0;
+  // workspace: gbar_in 9N, rho_own N, lam N, T_lb N, u_lb 2N, rho_nb 4N, rho_tot N, slots 9(K+1)N,
+  // u_fd 2N, T_new N, Y_new K N, u_new 2N
+  const size_t words = (9 + 1 + 1 + 1 + 2 + 4 + 1 + 9 * (size_t)(K + 1) + 2 + 1 + (size_t)K + 2) * N;
+  if (!ctx->adj_ws && !(ctx->adj_ws = dalloc(ctx, words * sizeof(R))))
+    return fail(ctx, LBM_ERR_ALLOC, "adjoint workspace allocation failed");
+  lbm_status st = lbm_load_state(ctx, state_n);
+  if (st != LBM_OK) return st;
+  const int cur = ctx->cur;
+  if (th) CK(run_fd(ctx, cur, false), "forward FD for the adjoint");
+  R* w = (R*)ctx->adj_ws;
+  AdjBuffers<R> b{};
+  const R* a = (const R*)adj;
+  b.g_adj = a;
+  b.u_adj = a + 9 * N;
+  b.T_adj = a + 11 * N;
+  b.Y_adj = a + 12 * N;
+  b.gbar_in = w; w += 9 * N;
+  b.rho_own = w; w += N;
+  b.lam_bar = w; w += N;
+  b.T_lb = w; w += N;
+  b.u_lb = w; w += 2 * N;
+  b.rho_nb = w; w += 4 * N;
+  b.rho_tot = w; w += N;
+  b.slots = w; w += 9 * (size_t)(K + 1) * N;
+  b.u_fd = w; w += 2 * N;
+  b.T_new = w; w += N;
+  b.Y_new = w; w += (size_t)K * N;
+  b.u_new = w; w += 2 * N;
+  b.inlet_bar = (R*)grad_inlet;
+  const LBArgs<R> lbf = make_lb_args<R>(ctx, cur, false);
+  const FDArgs<R> fdf = make_fd_args<R>(ctx, cur);
+  CK(launch_adjoint_step2d<R>(b, lbf, fdf, th, ctx->st), "adjoint kernels");
+  R* out = (R*)adj;
+  CK(cudaMemcpyAsync(out, b.gbar_in, 9 * N * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
+  CK(cudaMemcpyAsync(out + 9 * N, b.u_new, 2 * N * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
+  if (th) {
+    CK(cudaMemcpyAsync(out + 11 * N, b.T_new, N * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
+    CK(cudaMemcpyAsync(out + 12 * N, b.Y_new, (size_t)K * N * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st),
+       "copy adjoint");
+  }
+  return LBM_OK;
+}
+
+template <typename R> lbm_status fuel_objective_impl(lbm_ctx* ctx, int fuel, double* J, void* adj_out) {
+  const size_t N = ctx->N;
+  const int nb = (int)((N + FD_BLOCK - 1) / FD_BLOCK);
+  if (!ctx->obj_partials && !(ctx->obj_partials = (double*)dalloc(ctx, (size_t)nb * sizeof(double))))
+    return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+  R* o = (R*)adj_out;
+  CK(cudaMemsetAsync(o, 0, 11 * N * sizeof(R), ctx->st), "memset");
+  const FDArgs<R> fdf = make_fd_args<R>(ctx, ctx->cur);
+  CK(launch_fuel_objective<R>(fdf, fuel, o + 11 * N, o + 12 * N, ctx->obj_partials, nb, ctx->st), "objective");
+  std::vector<double> h(nb);
+  CK(cudaMemcpyAsync(h.data(), ctx->obj_partials, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "copy");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  double s = 0.0;
+  for (double v : h) s += v;
+  *J = s;
+  return LBM_OK;
+}
+
+template <typename R> lbm_status initial_T_adjoint_impl(lbm_ctx* ctx, const void* state0, const void* adj0, void* gT) {
+  lbm_status st = lbm_load_state(ctx, state0);
+  if (st != LBM_OK) return st;
+  const FDArgs<R> fdf = make_fd_args<R>(ctx, ctx->cur);
+  CK(launch_initial_T_adjoint<R>(fdf, (const R*)adj0, (R*)gT, ctx->st), "initial-temperature adjoint");
+  return LBM_OK;
+}
+
+lbm_status adjoint_supported(lbm_ctx* ctx) {
+  const lbm_config& c = ctx->cfg;
+  const bool hi1 = c.omega_hi[0] == 1.0 && c.omega_hi[1] == 1.0;
+  if (c.dim != 2 || c.storage == LBM_STORE_F16 || c.collision != LBM_COLL_CUMULANT || !hi1 || c.closed_domain ||
+      c.flame_sensor)
+    return fail(ctx, LBM_ERR_UNSUPPORTED,
+                "adjoint: 2-D, FP32/FP64 storage, cumulant collision with default higher-order rates, open domain, "
+                "no flame sensor");
+  return LBM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* state_n, void* adj, void* grad_inlet) {
+  if (!ctx || !state_n || !adj || !grad_inlet) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "set_fields must come first");
+  lbm_status s = adjoint_supported(ctx);
+  if (s != LBM_OK) return s;
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  return ctx->f64 ? adjoint_step_impl<double>(ctx, state_n, adj, grad_inlet)
+                  : adjoint_step_impl<float>(ctx, state_n, adj, grad_inlet);
+}
+
+lbm_status lbm_fuel_objective(lbm_ctx* ctx, int fuel_species, double* J, void* adj_out) {
+  if (!ctx || !J || !adj_out) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "set_fields must come first");
+  if (!ctx->cfg.thermal || fuel_species < 0 || fuel_species >= ctx->K)
+    return fail(ctx, LBM_ERR_ARG, "objective needs a thermal run and a valid fuel index");
+  lbm_status s = adjoint_supported(ctx);
+  if (s != LBM_OK) return s;
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  return ctx->f64 ? fuel_objective_impl<double>(ctx, fuel_species, J, adj_out)
+                  : fuel_objective_impl<float>(ctx, fuel_species, J, adj_out);
+}
+
+lbm_status lbm_initial_T_adjoint(lbm_ctx* ctx, const void* state0, const void* adj0, void* grad_T0) {
+  if (!ctx || !state0 || !adj0 || !grad_T0) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "set_fields must come first");
+  if (!ctx->cfg.thermal) return fail(ctx, LBM_ERR_ARG, "initial-temperature adjoint needs a thermal run");
+  lbm_status s = adjoint_supported(ctx);
+  if (s != LBM_OK) return s;
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  return ctx->f64 ? initial_T_adjoint_impl<double>(ctx, state0, adj0, grad_T0)
+                  : initial_T_adjoint_impl<float>(ctx, state0, adj0, grad_T0);
 }
 
 lbm_status lbm_use_graphs(lbm_ctx* ctx, int enable) {

@@ -36,4 +36,19 @@ struct PthUpdate {
 cudaError_t launch_pth_update(const PthUpdate& pu, const void* partials, int nblocks, PthState* pth,
                               int init, cudaStream_t st);
 constexpr int AUX_BLOCK = 256;
+
+// adjoint.cu: buffers of one adjoint step (inputs: adjoint of state n+1; outputs: state n)
+template <typename R> struct AdjBuffers {
+  const R* g_adj; const R* u_adj; const R* T_adj; const R* Y_adj;
+  R* gbar_in; R* rho_own; R* lam_bar; R* T_lb; R* u_lb; R* rho_nb; R* rho_tot; R* slots; R* u_fd;
+  R* T_new; R* Y_new; R* u_new; R* inlet_bar;
+};
+template <typename R>
+cudaError_t launch_adjoint_step2d(const AdjBuffers<R>& b, const LBArgs<R>& lbf, const FDArgs<R>& fdf, bool thermal,
+                                  cudaStream_t st);
+template <typename R>
+cudaError_t launch_initial_T_adjoint(const FDArgs<R>& fdf, const R* adj0, R* gradT, cudaStream_t st);
+template <typename R>
+cudaError_t launch_fuel_objective(const FDArgs<R>& fdf, int fuel, R* Tbar, R* Ybar, double* partials, int nblocks,
+                                  cudaStream_t st);
 }  // namespace hlbm

@@ -116,6 +116,14 @@ class Solver:
     def synchronize(self):
         self.stream.synchronize()
 
+    def _after_torch(self):
+        """Order the context's stream after work already queued on torch's current stream."""
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def _before_torch(self):
+        """Order torch's current stream after the work queued on the context's stream."""
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
     # --------------------------------------------------------------------------- output
     def fields(self, bits=L.F_T | L.F_Y | L.F_U | L.F_PH | L.F_RHO | L.F_LAM | L.F_G, device=False):
         """Selected fields as float64 (numpy on the host, or a torch tensor on the device)."""
@@ -125,8 +133,9 @@ class Solver:
         with torch.cuda.device(self.device):
             if device:
                 out = torch.empty(n, dtype=torch.float64, device=self.device)
-                self.stream.wait_stream(torch.cuda.current_stream(self.device))
+                self._after_torch()
                 _check(self.ctx, L.lib.lbm_get_fields(self.ctx, bits, C.c_void_p(out.data_ptr()), 1))
+                self._before_torch()
                 buf = out
             else:
                 buf = np.empty(n, dtype=np.float64)
@@ -167,12 +176,47 @@ class Solver:
         if buf is None:
             buf = torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.device)
         with torch.cuda.device(self.device):
+            self._after_torch()
             _check(self.ctx, L.lib.lbm_save_state(self.ctx, C.c_void_p(buf.data_ptr())))
+            self._before_torch()
         return buf
 
     def load_state(self, buf):
         with torch.cuda.device(self.device):
+            self._after_torch()
             _check(self.ctx, L.lib.lbm_load_state(self.ctx, C.c_void_p(buf.data_ptr())))
+            self._before_torch()
+
+    # --------------------------------------------------------------------------- adjoint
+    def adjoint_step(self, state_n, adj, grad_inlet):
+        """Reverse of one step from the saved state ``state_n`` (lbm_adjoint_step): ``adj``
+        (device tensor in the lbm_save_state layout and storage type) holds the adjoint of the
+        state after the step and is overwritten with the adjoint of ``state_n``; the adjoint of
+        the inlet-face velocity is added into ``grad_inlet`` ([dim][ny], storage type)."""
+        with torch.cuda.device(self.device):
+            self._after_torch()
+            _check(self.ctx, L.lib.lbm_adjoint_step(self.ctx, C.c_void_p(state_n.data_ptr()),
+                                                    C.c_void_p(adj.data_ptr()), C.c_void_p(grad_inlet.data_ptr())))
+            self._before_torch()
+
+    def initial_T_adjoint(self, state0, adj0, grad_T0):
+        """dJ/dT0 into ``grad_T0`` ([N], storage type) from the adjoint ``adj0`` of the state
+        ``state0`` that set_fields produced (lbm_initial_T_adjoint)."""
+        with torch.cuda.device(self.device):
+            self._after_torch()
+            _check(self.ctx, L.lib.lbm_initial_T_adjoint(self.ctx, C.c_void_p(state0.data_ptr()),
+                                                         C.c_void_p(adj0.data_ptr()), C.c_void_p(grad_T0.data_ptr())))
+            self._before_torch()
+
+    def fuel_objective(self, fuel, adj_out):
+        """J = sum over fluid cells of -omega_fuel for the current state; its gradient with
+        respect to the state is written to ``adj_out`` (lbm_save_state layout). Returns J."""
+        J = C.c_double()
+        with torch.cuda.device(self.device):
+            self._after_torch()
+            _check(self.ctx, L.lib.lbm_fuel_objective(self.ctx, int(fuel), C.byref(J), C.c_void_p(adj_out.data_ptr())))
+            self._before_torch()
+        return J.value
 
     # ------------------------------------------------------------------------- profiling
     def profile(self, enable=True):

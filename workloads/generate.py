@@ -97,10 +97,18 @@ def flame_2d(nx=256, ny=8, storage="f64", seed=0, collision="cumulant", u_in=0.0
 # ------------------------------------------------------------------------ 2-D chamber
 def chamber_2d(nx=1024, ny=256, storage="f32", seed=0, collision="cumulant", F=5.0, smag=0.17,
                obstacle=(16, 48), n_rows=3, per_row=3, inlet=False, u_in=0.02, steps=20000,
-               dx=1e-4, dt=5e-8, A1=1.0e9, A2=5.0e6, hot_radius=10.0, T_u=300.0, T_hot=1950.0):
+               dx=1e-4, dt=5e-8, A1=1.0e9, A2=5.0e6, hot_radius=10.0, T_u=300.0, T_hot=1950.0,
+               inlet_jitter=0.0, u_init=0.0, y_trace=0.0):
     """Confined 2-D chamber: closed left end (or an inlet when ``inlet``), open right end, walls
     top and bottom, ``n_rows`` rows of ``per_row`` rectangular obstacles at seeded positions,
-    hot burnt-gas semicircle at the left end; 2-step chemistry, 6 species, phi = 0.83."""
+    hot burnt-gas semicircle at the left end; 2-step chemistry, 6 species, phi = 0.83.
+    The inlet profile is parabolic, times (1 + inlet_jitter N(0, 1)) per row when inlet_jitter
+    is set (a seeded profile without the mirror symmetry of the parabola). With u_init the gas
+    starts moving: u_x = u_init (1 + 0.2 N(0, 1)), u_y = 0.2 u_init N(0, 1) per cell (a state
+    whose face velocities are nowhere zero, so that no upwind choice sits on its switch).
+    y_trace adds that mass fraction of each product (CO, CO2, H2O), taken from N2, to the fresh
+    and burnt gas and to the inlet mixture (no species then starts at the max(Y, 0) switch of
+    the rate law)."""
     rng = np.random.default_rng(seed)
     names = SPECIES["6sp"]
     cfg = _base_cfg(2, nx, ny, 1, storage, collision)
@@ -127,6 +135,12 @@ def chamber_2d(nx=1024, ny=256, storage="f32", seed=0, collision="cumulant", F=5
     dist = np.sqrt((x + 0.5) ** 2 + (y + 0.5 - ny / 2.0) ** 2)
     b = _tanh_blend(rad - dist, 1.0)
     Yu, Yb = np.array(mixture_phi(names, 0.83)), np.array(burnt_mixture(names, 0.83))
+    if y_trace:
+        for Ym in (Yu, Yb):
+            for nm in ("CO", "CO2", "H2O"):
+                Ym[names.index(nm)] += y_trace
+            Ym[names.index("N2")] -= 3.0 * y_trace
+        cfg["Y_in"] = [float(v) for v in Yu]
     T = T_u + (T_hot - T_u) * b
     Y = Yu[:, None] * (1 - b)[None, :] + Yb[:, None] * b[None, :]
     u = np.zeros((2, nx * ny))
@@ -134,6 +148,12 @@ def chamber_2d(nx=1024, ny=256, storage="f32", seed=0, collision="cumulant", F=5
     if inlet:
         yy = np.arange(ny) + 0.5
         inlet_u[0] = u_in * 4.0 * yy * (ny - yy) / ny ** 2
+        if inlet_jitter:
+            inlet_u[0] *= 1.0 + inlet_jitter * rng.standard_normal(ny)
+    if u_init:
+        u[0] = u_init * (1.0 + 0.2 * rng.standard_normal(nx * ny))
+        u[1] = 0.2 * u_init * rng.standard_normal(nx * ny)
+        u[:, mask == 1] = 0.0
     return Workload("chamber_2d", cfg, mask, inlet_u, u, np.zeros(nx * ny), T=T, Y=Y,
                     steps=steps, info={"obstacles": rows})
 
@@ -237,7 +257,11 @@ _NAMED = {
     "c2_chamber_2d": lambda seed=0: chamber_2d(seed=seed),
     "c3_swirl_cold_3d": lambda seed=0: swirl_3d(seed=seed),
     "c4_swirl_reactive_3d": lambda seed=0: swirl_3d(384, 192, 192, reactive=True, seed=seed),
-    "c5_adjoint_2d": lambda seed=0: chamber_2d(512, 128, inlet=True, steps=2000, seed=seed),
+    # C2 family at 512 x 128 with an inlet; a hot kernel of 24 cells (smaller ones quench under
+    # the thickening within the 2000 steps); a seeded initial flow, jittered inlet profile and a
+    # trace of products keep J differentiable at the point (no upwind tie, no species at 0)
+    "c5_adjoint_2d": lambda seed=0: chamber_2d(512, 128, inlet=True, steps=2000, seed=seed, hot_radius=48.0,
+                                               inlet_jitter=0.1, u_init=0.005, y_trace=1e-4),
 }
 
 
