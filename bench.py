@@ -174,6 +174,91 @@ def oracle_sample(max_seconds=20.0):
                       f"({wl.N} cells) cut from the same workload family, {n} steps in {dt:.1f} s"}
 
 
+def adjoint_bench(args):
+    """Gradient of the fuel consumption after K = 2000 steps of the 512 x 128 chamber (inlet
+    profile of 128 values and initial temperature field), checkpoints every 100 steps: forward
+    and backward wall time with device synchronisation (FP32), their ratio, and an FP64 check of
+    the gradient against central differences along 16 seeded directions (numpy Philox)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2207_11567_gb300 import AdjointProblem
+    torch.cuda.set_device(0)
+    wl = W.make("c5_adjoint_2d")
+    K, C = wl.steps, 100
+    inlet0 = np.asarray(wl.inlet_u, dtype=np.float64).reshape(2, -1)
+    T0 = np.asarray(wl.T, dtype=np.float64).reshape(-1)
+
+    def problem(storage):
+        cfg = dict(wl.cfg)
+        cfg["storage"] = storage
+        return AdjointProblem(cfg, wl.mask, wl.Y, u0=wl.u, P_h0=wl.P_h, g_pert=wl.g_pert, n_steps=K,
+                              checkpoint_every=C, fuel=0)
+
+    pb = problem("f32")
+    for _ in range(max(1, args.warmup)):
+        pb.forward(inlet0, T0)
+        pb.backward()
+    fwd, bwd = [], []
+    with Clocks(torch.cuda.current_device()) as clk:
+        for _ in range(max(1, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            J32 = pb.forward(inlet0, T0)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            gin32, gT32 = pb.backward()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            fwd.append(t1 - t0)
+            bwd.append(t2 - t1)
+    pb.close()
+    tf, tb = statistics.median(fwd), statistics.median(bwd)
+    fd = {}
+    if not args.no_fd_check:
+        rng_seed = 2207
+        fluid = (np.asarray(wl.mask).reshape(-1) == 0).astype(np.float64)
+
+        def check(n_steps, h):
+            """FP64 gradient and |AD - FD| / sum |grad_i d_i| along args.fd_dirs Philox directions."""
+            cfg = dict(wl.cfg)
+            cfg["storage"] = "f64"
+            p = AdjointProblem(cfg, wl.mask, wl.Y, u0=wl.u, P_h0=wl.P_h, g_pert=wl.g_pert, n_steps=n_steps,
+                               checkpoint_every=C, fuel=0)
+            J = p.forward(inlet0, T0)
+            gi, gt = p.backward()
+            gi, gt = gi.cpu().numpy(), gt.cpu().numpy()
+            rng = np.random.Generator(np.random.Philox(rng_seed))
+            errs = []
+            for _ in range(args.fd_dirs):
+                di = rng.standard_normal(inlet0.shape) * (inlet0 != 0) * 0.1 * np.abs(inlet0).max()
+                dT = rng.standard_normal(T0.shape) * fluid * 10.0
+                fdv = (p.forward(inlet0 + h * di, T0 + h * dT) - p.forward(inlet0 - h * di, T0 - h * dT)) / (2 * h)
+                ad = float((gi * di).sum() + (gt * dT).sum())
+                errs.append(abs(ad - fdv) / float(np.abs(gi * di).sum() + np.abs(gt * dT).sum()))
+            p.close()
+            return J, gi, gt, {"K": n_steps, "h": h, "max_err": max(errs), "median_err": statistics.median(errs),
+                               "max_abs_grad": float(max(np.abs(gi).max(), np.abs(gt).max()))}
+
+        J64, gin, gT, full = check(K, 1e-4)
+        _, _, _, short = check(20, 1e-6)
+        g32 = np.concatenate([gin32.double().cpu().numpy().ravel(), gT32.double().cpu().numpy().ravel()])
+        g64 = np.concatenate([gin.ravel(), gT.ravel()])
+        fin = bool(np.isfinite(g32).all())
+        fd = {"directions": args.fd_dirs, "err_measure": "|AD - FD| / sum |grad_i d_i|, FP64",
+              "full_horizon": full, "short_horizon": short, "J_f64": J64, "J_f32": J32, "f32_grad_finite": fin,
+              "f32_vs_f64_grad_rel_l2": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64)) if fin else None}
+    N = wl.N
+    line = {"metric": "adjoint / forward time ratio, gradient of fuel consumption w.r.t. inlet profile and T0",
+            "value": tb / tf, "unit": "x", "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "dtype": "f32", "data": "synthetic", "scaling": "weak", "vs_baseline": None,
+            "config": {"workload": "c5_adjoint_2d", "grid": [wl.cfg["nx"], wl.cfg["ny"]], "cells": N, "K": K,
+                       "checkpoint_every": C, "lattice": "D2Q9", "species": len(wl.cfg["species"])},
+            "forward_s": tf, "backward_s": tb, "forward_mlups": N * K / tf / 1e6, "backward_mlups": N * K / tb / 1e6,
+            "gradient_check": fd, "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -187,9 +272,14 @@ def main():
                     help="time one storage variant only (profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=["c4_swirl_reactive_3d", "c3_swirl_cold_3d",
-                                                             "c2_chamber_2d"],
+                                                             "c2_chamber_2d", "c5_adjoint_2d"],
                     help="benchmark configuration (default: the reactive swirl burner)")
+    ap.add_argument("--no-fd-check", action="store_true", help="c5: skip the FP64 finite-difference check")
+    ap.add_argument("--fd-dirs", type=int, default=16, help="c5: directions of the finite-difference check")
     args = ap.parse_args()
+    if args.workload == "c5_adjoint_2d" and args.impl == "ours":
+        adjoint_bench(args)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -193,6 +193,17 @@ lbm_status lbm_kernel_bytes(const lbm_ctx* ctx, double bytes[LBM_KERNEL_KINDS]);
  * max(Y, 0) of the rate law are held fixed (derivative 0 across their switches). */
 lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* state_n, void* adj, void* grad_inlet);
 
+/* Reverse sweep over one checkpoint segment (same support as lbm_adjoint_step): from the state
+ * `checkpoint` (device, lbm_save_state layout, state n0) the library recomputes n_steps steps,
+ * keeping every state of the segment and its rho, Lambda in device workspace it owns
+ * (n_steps x (state + 2 N) values of the field type), then applies the adjoint step from
+ * n0 + n_steps - 1 down to n0. adj: device buffer in the lbm_save_state layout, holding the
+ * adjoint of state n0 + n_steps on entry and that of state n0 on return (populations of solid
+ * cells are set to zero); grad_inlet: as in lbm_adjoint_step (accumulated). Equivalent to
+ * n_steps calls of lbm_adjoint_step with the saved states, without host round trips. The
+ * context's state ends as state n0 + n_steps. */
+lbm_status lbm_adjoint_segment(lbm_ctx* ctx, const void* checkpoint, int n_steps, void* adj, void* grad_inlet);
+
 /* Objective J = sum over fluid cells of the fuel consumption rate -omega_F (kg/(m^3 s), lattice
  * cell volume 1) of the context's current state, written to *J (host), and its gradient with
  * respect to the state written to adj_out (device, lbm_save_state layout: T and Y parts filled,

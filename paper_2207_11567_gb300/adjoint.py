@@ -9,10 +9,11 @@ field T0 (which sets T^0 and, through rho = P_th W / (R T) of Eq. 13, the initia
 populations of Eq. 6).
 
 Forward: set the inlet and the initial fields, run K steps, saving the state every C steps.
-Backward: for each segment, last first, reload its checkpoint, recompute and keep the segment's
-states, then apply lbm_adjoint_step from the segment's last step down to its first, which also
-adds the inlet-velocity adjoint; lbm_initial_T_adjoint turns the adjoint of state 0 into dJ/dT0.
-Memory: K/C checkpoints plus C states, each ``Solver.state_bytes()`` of device memory.
+Backward: for each segment, last first, lbm_adjoint_segment reloads its checkpoint, recomputes
+and keeps the segment's states, then applies the adjoint step from the segment's last step down
+to its first, adding the inlet-velocity adjoint; lbm_initial_T_adjoint turns the adjoint of
+state 0 into dJ/dT0. Memory: K/C checkpoints of ``Solver.state_bytes()`` plus the library's
+segment workspace (C states with their rho and Lambda).
 Every arithmetic step runs in the library's CUDA kernels; this module only orders the calls.
 """
 import numpy as np
@@ -71,14 +72,7 @@ class AdjointProblem:
         for seg in reversed(range(len(self._ckpt))):
             n0 = seg * self.C
             n1 = min(n0 + self.C, self.n_steps)
-            states = [self._ckpt[seg]]
-            if n1 - n0 > 1:
-                s.load_state(self._ckpt[seg])
-                for _ in range(n0 + 1, n1):
-                    s.step(1)
-                    states.append(s.save_state())
-            for n in reversed(range(n0, n1)):
-                s.adjoint_step(states[n - n0], adj, gin)
+            s.adjoint_segment(self._ckpt[seg], n1 - n0, adj, gin)
         gT = self._zeros(s.N)
         s.initial_T_adjoint(self._ckpt[0], adj, gT)
         return gin.reshape(self.dim, self.ny), gT

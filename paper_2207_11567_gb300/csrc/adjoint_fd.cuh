@@ -17,7 +17,8 @@ template <typename R> struct FDAdjArgs {
   FDArgs<R> f;           // forward arguments of state n (T, Y, u, stencil words, constants)
   const R* Tbar_out;     // [N] adjoint of T^{n+1}
   const R* Ybar_out;     // [K][N] adjoint of Y^{n+1}
-  const R* rho_bar;      // [N] adjoint of rho^n (gathered from the LB adjoint)
+  const R* rho_own;      // [N] adjoint of rho^n used by the cell's own LB update
+  const R* rho_nb;       // [4][N] adjoint of the +x, -x, +y, -y neighbour rho in a cell's LB update
   const R* lam_bar;      // [N] adjoint of Lambda^n (from the LB adjoint)
   R* slots;              // [9][1+K][N] stencil-value adjoints
   R* u_bar;              // [2][N] adjoint of u^n through the advection (center only)
@@ -165,7 +166,19 @@ __global__ void __launch_bounds__(FD_BLOCK) fd_adjoint_kernel(const FDAdjArgs<R>
 
   // ------------------------------------------------------------------------- reverse
   const R lamb = A.lam_bar[r];
-  R rhob = A.rho_bar[r];
+  // adjoint of rho^n: the cell's own part plus the density-gradient parts of the cells that
+  // hold it as their -x / +x / -y / +y neighbour (zero where that cell is solid or mirrored it)
+  R rhob = A.rho_own[r];
+  {
+    const int xm = x > 0 ? r - 1 : (g.bc_lo[0] == BC_PERIODIC ? r + g.nx - 1 : -1);
+    const int xp = x < g.nx - 1 ? r + 1 : (g.bc_hi[0] == BC_PERIODIC ? r - g.nx + 1 : -1);
+    const int ym = y > 0 ? r - g.nx : (g.bc_lo[1] == BC_PERIODIC ? r + (g.ny - 1) * g.nx : -1);
+    const int yp = y < g.ny - 1 ? r + g.nx : (g.bc_hi[1] == BC_PERIODIC ? r - (g.ny - 1) * g.nx : -1);
+    if (xm >= 0) rhob += A.rho_nb[xm];
+    if (xp >= 0) rhob += A.rho_nb[N + xp];
+    if (ym >= 0) rhob += A.rho_nb[2 * N + ym];
+    if (yp >= 0) rhob += A.rho_nb[3 * N + yp];
+  }
   R Trb = R(0), Wb = R(0), inv_rhob = R(0), inv_rpFb = R(0), qdotb = R(0);
   R qb[MAX_RX];
   for (int j = 0; j < MAX_RX; ++j) qb[j] = R(0);
@@ -348,32 +361,6 @@ __global__ void fd_adjoint_gather(Geo g, const uint32_t* __restrict__ sword, int
   }
   ubar[s] = u_fd[s] + u_lb[s];
   ubar[N + s] = u_fd[N + s] + u_lb[N + s];
-}
-
-// Adjoint of rho: the cell's own part plus the density-gradient parts of its four neighbours
-// (buffer layout [+x, -x, +y, -y] of the LB adjoint).
-template <typename R>
-__global__ void rho_adjoint_gather(Geo g, const uint32_t* __restrict__ links, const R* __restrict__ own,
-                                   const R* __restrict__ nb, R* __restrict__ out) {
-  const int s = blockIdx.x * FD_BLOCK + threadIdx.x;
-  if (s >= g.N) return;
-  const int N = g.N;
-  if (!(__ldg(links + s) >> 31)) {
-    out[s] = R(0);
-    return;
-  }
-  const int x = s % g.nx, y = s / g.nx;
-  R v = own[s];
-  // cell s - e_x has s as its +x neighbour (slot 0); s + e_x has it as its -x neighbour (slot 1)
-  const int xm = x > 0 ? s - 1 : (g.bc_lo[0] == BC_PERIODIC ? s + g.nx - 1 : -1);
-  const int xp = x < g.nx - 1 ? s + 1 : (g.bc_hi[0] == BC_PERIODIC ? s - g.nx + 1 : -1);
-  const int ym = y > 0 ? s - g.nx : (g.bc_lo[1] == BC_PERIODIC ? s + (g.ny - 1) * g.nx : -1);
-  const int yp = y < g.ny - 1 ? s + g.nx : (g.bc_hi[1] == BC_PERIODIC ? s - (g.ny - 1) * g.nx : -1);
-  if (xm >= 0) v += nb[0 * N + xm];
-  if (xp >= 0) v += nb[1 * N + xp];
-  if (ym >= 0) v += nb[2 * N + ym];
-  if (yp >= 0) v += nb[3 * N + yp];
-  out[s] = v;
 }
 
 }  // namespace hlbm

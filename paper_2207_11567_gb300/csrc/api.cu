@@ -63,8 +63,11 @@ struct lbm_ctx {
   // graphs
   bool use_graphs = true;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  // adjoint workspace (allocated on the first adjoint call)
+  // adjoint workspace (allocated zero-filled on the first adjoint call): scratch arrays and one
+  // adjoint buffer; segment states (n slots of state + rho + Lambda) for lbm_adjoint_segment
   void* adj_ws = nullptr;
+  void* seg_ws = nullptr;
+  int seg_cap = 0;
   double* obj_partials = nullptr;
   // profiling
   bool prof = false;
@@ -818,50 +821,131 @@ lbm_status lbm_kernel_bytes(const lbm_ctx* ctx, double bytes[LBM_KERNEL_KINDS]) 
 }  // extern "C"
 
 namespace {
-template <typename R> lbm_status adjoint_step_impl(lbm_ctx* ctx, const void* state_n, void* adj, void* grad_inlet) {
+size_t state_words(const lbm_ctx* c) {
+  return ((size_t)c->Q + c->D + (c->cfg.thermal ? 1 + (size_t)c->K : 0)) * c->N;
+}
+
+// Scratch of the adjoint kernels plus one adjoint buffer, zero-filled once: the kernels never
+// write solid-cell entries, which therefore stay zero.
+template <typename R> lbm_status ensure_adj_ws(lbm_ctx* ctx, R** scratch, R** buf) {
   const size_t N = ctx->N;
-  const int K = ctx->K;
-  const bool th = ctx->cfg.thermal != 0;
-  // workspace: gbar_in 9N, rho_own N, lam N, T_lb N, u_lb 2N, rho_nb 4N, rho_tot N, slots 9(K+1)N,
-  // u_fd 2N, T_new N, Y_new K N, u_new 2N
-  const size_t words = (9 + 1 + 1 + 1 + 2 + 4 + 1 + 9 * (size_t)(K + 1) + 2 + 1 + (size_t)K + 2) * N;
-  if (!ctx->adj_ws && !(ctx->adj_ws = dalloc(ctx, words * sizeof(R))))
-    return fail(ctx, LBM_ERR_ALLOC, "adjoint workspace allocation failed");
-  lbm_status st = lbm_load_state(ctx, state_n);
-  if (st != LBM_OK) return st;
-  const int cur = ctx->cur;
-  if (th) CK(run_fd(ctx, cur, false), "forward FD for the adjoint");
-  R* w = (R*)ctx->adj_ws;
+  const size_t sw = adj_scratch_words<R>(N, ctx->K), bw = state_words(ctx);
+  if (!ctx->adj_ws) {
+    if (!(ctx->adj_ws = dalloc(ctx, (sw + bw) * sizeof(R))))
+      return fail(ctx, LBM_ERR_ALLOC, "adjoint workspace allocation failed");
+    CK(cudaMemsetAsync(ctx->adj_ws, 0, (sw + bw) * sizeof(R), ctx->st), "memset");
+  }
+  *scratch = (R*)ctx->adj_ws;
+  *buf = *scratch + sw;
+  return LBM_OK;
+}
+
+template <typename R> AdjBuffers<R> adj_buffers(lbm_ctx* ctx, R* w, const R* in, R* out, void* grad_inlet) {
+  const size_t N = ctx->N;
   AdjBuffers<R> b{};
-  const R* a = (const R*)adj;
-  b.g_adj = a;
-  b.u_adj = a + 9 * N;
-  b.T_adj = a + 11 * N;
-  b.Y_adj = a + 12 * N;
-  b.gbar_in = w; w += 9 * N;
+  b.in = in;
+  b.out = out;
   b.rho_own = w; w += N;
   b.lam_bar = w; w += N;
   b.T_lb = w; w += N;
   b.u_lb = w; w += 2 * N;
   b.rho_nb = w; w += 4 * N;
-  b.rho_tot = w; w += N;
-  b.slots = w; w += 9 * (size_t)(K + 1) * N;
-  b.u_fd = w; w += 2 * N;
-  b.T_new = w; w += N;
-  b.Y_new = w; w += (size_t)K * N;
-  b.u_new = w; w += 2 * N;
+  b.slots = w; w += 9 * (size_t)(ctx->K + 1) * N;
+  b.u_fd = w;
   b.inlet_bar = (R*)grad_inlet;
-  const LBArgs<R> lbf = make_lb_args<R>(ctx, cur, false);
-  const FDArgs<R> fdf = make_fd_args<R>(ctx, cur);
-  CK(launch_adjoint_step2d<R>(b, lbf, fdf, th, ctx->st), "adjoint kernels");
-  R* out = (R*)adj;
-  CK(cudaMemcpyAsync(out, b.gbar_in, 9 * N * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
-  CK(cudaMemcpyAsync(out + 9 * N, b.u_new, 2 * N * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
-  if (th) {
-    CK(cudaMemcpyAsync(out + 11 * N, b.T_new, N * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
-    CK(cudaMemcpyAsync(out + 12 * N, b.Y_new, (size_t)K * N * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st),
-       "copy adjoint");
+  return b;
+}
+
+template <typename R> lbm_status adjoint_step_impl(lbm_ctx* ctx, const void* state_n, void* adj, void* grad_inlet) {
+  const bool th = ctx->cfg.thermal != 0;
+  R *scratch, *buf;
+  lbm_status st = ensure_adj_ws<R>(ctx, &scratch, &buf);
+  if (st != LBM_OK) return st;
+  if ((st = lbm_load_state(ctx, state_n)) != LBM_OK) return st;
+  const int cur = ctx->cur;
+  if (th) CK(run_fd(ctx, cur, false), "forward FD for the adjoint");  // rho^n, Lambda^n
+  const AdjBuffers<R> b = adj_buffers<R>(ctx, scratch, (const R*)adj, buf, grad_inlet);
+  CK(launch_adjoint_step2d<R>(b, make_lb_args<R>(ctx, cur, false), make_fd_args<R>(ctx, cur), th, ctx->st),
+     "adjoint kernels");
+  CK(cudaMemcpyAsync(adj, buf, state_words(ctx) * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
+  return LBM_OK;
+}
+
+// Reverse sweep over one checkpoint segment. Recompute: from the checkpoint, n steps, keeping
+// state k and the rho^k, Lambda^k its step computed in slot k. Reverse: the adjoint step over
+// slots n-1 .. 0, reading each slot in place, alternating between adj and the internal buffer.
+template <typename R>
+lbm_status adjoint_segment_impl(lbm_ctx* ctx, const void* checkpoint, int n, void* adj, void* grad_inlet) {
+  const size_t N = ctx->N;
+  const int K = ctx->K;
+  const bool th = ctx->cfg.thermal != 0;
+  R *scratch, *buf;
+  lbm_status st = ensure_adj_ws<R>(ctx, &scratch, &buf);
+  if (st != LBM_OK) return st;
+  const size_t sw = state_words(ctx), slot_w = sw + (th ? 2 * N : 0);
+  if (n > ctx->seg_cap) {
+    // grow: the old block stays with the context's allocations until lbm_destroy
+    if (!(ctx->seg_ws = dalloc(ctx, (size_t)n * slot_w * sizeof(R))))
+      return fail(ctx, LBM_ERR_ALLOC, "adjoint segment workspace allocation failed");
+    ctx->seg_cap = n;
   }
+  R* seg = (R*)ctx->seg_ws;
+  if ((st = lbm_load_state(ctx, checkpoint)) != LBM_OK) return st;
+  auto state_copy = [&](CopyList<R>& l, R* slot) {
+    const int cur = ctx->cur;
+    int j = l.count;
+    l.src[j] = (const R*)ctx->g[cur]; l.dst[j] = slot; l.n[j++] = 9 * N;
+    l.src[j] = (const R*)ctx->u; l.dst[j] = slot + 9 * N; l.n[j++] = 2 * N;
+    if (th) {
+      l.src[j] = (const R*)ctx->T[cur]; l.dst[j] = slot + 11 * N; l.n[j++] = N;
+      l.src[j] = (const R*)ctx->Y[cur]; l.dst[j] = slot + 12 * N; l.n[j++] = (size_t)K * N;
+    }
+    l.count = j;
+  };
+  {
+    CopyList<R> l{};
+    state_copy(l, seg);
+    CK(launch_copy_list<R>(l, ctx->st), "segment snapshot");
+  }
+  for (int k = 0; k < n; ++k) {
+    CK(enqueue_step(ctx, ctx->cur, false), "segment recompute");
+    ctx->cur ^= 1;
+    ++ctx->steps;
+    CopyList<R> l{};
+    if (th) {
+      R* slot = seg + (size_t)k * slot_w;
+      l.src[0] = (const R*)ctx->rho; l.dst[0] = slot + sw; l.n[0] = N;
+      l.src[1] = (const R*)ctx->lam; l.dst[1] = slot + sw + N; l.n[1] = N;
+      l.count = 2;
+    }
+    if (k + 1 < n) state_copy(l, seg + (size_t)(k + 1) * slot_w);
+    CK(launch_copy_list<R>(l, ctx->st), "segment snapshot");
+  }
+  CK(launch_zero_solid_pops<R>(ctx->geo, ctx->links, (R*)adj, ctx->st), "zero solid adjoint");
+  const R* in = (const R*)adj;
+  R* out = buf;
+  for (int k = n - 1; k >= 0; --k) {
+    R* slot = seg + (size_t)k * slot_w;
+    LBArgs<R> lbf = make_lb_args<R>(ctx, 0, false);
+    lbf.g_in = slot;
+    lbf.u = slot + 9 * N;
+    FDArgs<R> fdf = make_fd_args<R>(ctx, 0);
+    fdf.u = slot + 9 * N;
+    if (th) {
+      lbf.T = slot + 11 * N;
+      lbf.rho = slot + sw;
+      lbf.lam = slot + sw + N;
+      fdf.T = slot + 11 * N;
+      fdf.Y = slot + 12 * N;
+    }
+    const AdjBuffers<R> b = adj_buffers<R>(ctx, scratch, in, out, grad_inlet);
+    CK(launch_adjoint_step2d<R>(b, lbf, fdf, th, ctx->st), "adjoint kernels");
+    R* done = out;
+    out = (R*)in;
+    in = done;
+  }
+  if (in != (const R*)adj)
+    CK(cudaMemcpyAsync(adj, in, sw * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
   return LBM_OK;
 }
 
@@ -925,6 +1009,17 @@ lbm_status lbm_fuel_objective(lbm_ctx* ctx, int fuel_species, double* J, void* a
   CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
   return ctx->f64 ? fuel_objective_impl<double>(ctx, fuel_species, J, adj_out)
                   : fuel_objective_impl<float>(ctx, fuel_species, J, adj_out);
+}
+
+lbm_status lbm_adjoint_segment(lbm_ctx* ctx, const void* checkpoint, int n_steps, void* adj, void* grad_inlet) {
+  if (!ctx || !checkpoint || !adj || !grad_inlet) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (n_steps < 1) return fail(ctx, LBM_ERR_ARG, "n_steps must be >= 1");
+  if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "set_fields must come first");
+  lbm_status s = adjoint_supported(ctx);
+  if (s != LBM_OK) return s;
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  return ctx->f64 ? adjoint_segment_impl<double>(ctx, checkpoint, n_steps, adj, grad_inlet)
+                  : adjoint_segment_impl<float>(ctx, checkpoint, n_steps, adj, grad_inlet);
 }
 
 lbm_status lbm_initial_T_adjoint(lbm_ctx* ctx, const void* state0, const void* adj0, void* grad_T0) {

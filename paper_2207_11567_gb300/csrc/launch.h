@@ -37,15 +37,26 @@ cudaError_t launch_pth_update(const PthUpdate& pu, const void* partials, int nbl
                               int init, cudaStream_t st);
 constexpr int AUX_BLOCK = 256;
 
-// adjoint.cu: buffers of one adjoint step (inputs: adjoint of state n+1; outputs: state n)
+// adjoint.cu: one adjoint step. in: adjoint of state n+1, out: adjoint of state n, both in the
+// lbm_save_state layout (g 9N, u 2N, T N, Y KN). Scratch arrays and the population part of out
+// must hold zeros on solid cells (they are never written there): zero them once at allocation.
 template <typename R> struct AdjBuffers {
-  const R* g_adj; const R* u_adj; const R* T_adj; const R* Y_adj;
-  R* gbar_in; R* rho_own; R* lam_bar; R* T_lb; R* u_lb; R* rho_nb; R* rho_tot; R* slots; R* u_fd;
-  R* T_new; R* Y_new; R* u_new; R* inlet_bar;
+  const R* in; R* out;
+  R* rho_own; R* lam_bar; R* T_lb; R* u_lb; R* rho_nb; R* slots; R* u_fd;
+  R* inlet_bar;
 };
+template <typename R> constexpr size_t adj_scratch_words(size_t N, int K) {
+  return (1 + 1 + 1 + 2 + 4 + 9 * (size_t)(K + 1) + 2) * N;
+}
 template <typename R>
 cudaError_t launch_adjoint_step2d(const AdjBuffers<R>& b, const LBArgs<R>& lbf, const FDArgs<R>& fdf, bool thermal,
                                   cudaStream_t st);
+// copy up to 6 arrays of R in one launch (state snapshots of the reverse sweep)
+template <typename R> struct CopyList {
+  const R* src[6]; R* dst[6]; size_t n[6]; int count;
+};
+template <typename R> cudaError_t launch_copy_list(const CopyList<R>& l, cudaStream_t st);
+template <typename R> cudaError_t launch_zero_solid_pops(const Geo& g, const uint32_t* links, R* pops, cudaStream_t st);
 template <typename R>
 cudaError_t launch_initial_T_adjoint(const FDArgs<R>& fdf, const R* adj0, R* gradT, cudaStream_t st);
 template <typename R>

@@ -199,6 +199,16 @@ class Solver:
                                                     C.c_void_p(adj.data_ptr()), C.c_void_p(grad_inlet.data_ptr())))
             self._before_torch()
 
+    def adjoint_segment(self, checkpoint, n_steps, adj, grad_inlet):
+        """Reverse sweep over n_steps steps from the saved state ``checkpoint``
+        (lbm_adjoint_segment): ``adj`` holds the adjoint of the state n_steps later and is
+        overwritten with that of ``checkpoint``; the inlet adjoint is added into ``grad_inlet``."""
+        with torch.cuda.device(self.device):
+            self._after_torch()
+            _check(self.ctx, L.lib.lbm_adjoint_segment(self.ctx, C.c_void_p(checkpoint.data_ptr()), int(n_steps),
+                                                       C.c_void_p(adj.data_ptr()), C.c_void_p(grad_inlet.data_ptr())))
+            self._before_torch()
+
     def initial_T_adjoint(self, state0, adj0, grad_T0):
         """dJ/dT0 into ``grad_T0`` ([N], storage type) from the adjoint ``adj0`` of the state
         ``state0`` that set_fields produced (lbm_initial_T_adjoint)."""

@@ -220,3 +220,28 @@ def test_adjoint_rejects_unsupported_configs():
     with pytest.raises(L.HLBMError):
         s.adjoint_step(state, adj, gin)
     s.close()
+
+
+@pytest.mark.parametrize("n", [3, 4])
+def test_adjoint_segment_equals_single_steps(n):
+    """lbm_adjoint_segment (recompute in the library, reverse over stored states, alternating
+    buffers) gives the same bits as n lbm_adjoint_step calls on saved states."""
+    from paper_2207_11567_gb300 import from_workload
+    wl = _case("f32")
+    s = from_workload(wl)
+    s.step(2)
+    states = [s.save_state()]
+    for _ in range(n):
+        s.step(1)
+        states.append(s.save_state())
+    adj0 = torch.zeros(s.state_bytes() // 4, dtype=torch.float32, device="cuda")
+    s.fuel_objective(FUEL, adj0)
+    a1, g1 = adj0.clone(), torch.zeros(2 * wl.cfg["ny"], dtype=torch.float32, device="cuda")
+    for k in reversed(range(n)):
+        s.adjoint_step(states[k], a1, g1)
+    a2, g2 = adj0.clone(), torch.zeros_like(g1)
+    s.adjoint_segment(states[0], n, a2, g2)
+    s.close()
+    nw = (wl.Q + 2 + 1 + len(wl.cfg["species"])) * wl.N
+    assert torch.equal(a1[:nw], a2[:nw])
+    assert torch.equal(g1, g2)

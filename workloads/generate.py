@@ -98,7 +98,7 @@ def flame_2d(nx=256, ny=8, storage="f64", seed=0, collision="cumulant", u_in=0.0
 def chamber_2d(nx=1024, ny=256, storage="f32", seed=0, collision="cumulant", F=5.0, smag=0.17,
                obstacle=(16, 48), n_rows=3, per_row=3, inlet=False, u_in=0.02, steps=20000,
                dx=1e-4, dt=5e-8, A1=1.0e9, A2=5.0e6, hot_radius=10.0, T_u=300.0, T_hot=1950.0,
-               inlet_jitter=0.0, u_init=0.0, y_trace=0.0):
+               inlet_jitter=0.0, u_init=0.0, y_trace=0.0, y_floor=0.0):
     """Confined 2-D chamber: closed left end (or an inlet when ``inlet``), open right end, walls
     top and bottom, ``n_rows`` rows of ``per_row`` rectangular obstacles at seeded positions,
     hot burnt-gas semicircle at the left end; 2-step chemistry, 6 species, phi = 0.83.
@@ -108,7 +108,9 @@ def chamber_2d(nx=1024, ny=256, storage="f32", seed=0, collision="cumulant", F=5
     whose face velocities are nowhere zero, so that no upwind choice sits on its switch).
     y_trace adds that mass fraction of each product (CO, CO2, H2O), taken from N2, to the fresh
     and burnt gas and to the inlet mixture (no species then starts at the max(Y, 0) switch of
-    the rate law)."""
+    the rate law). Mass fractions below y_floor are set to 0 (the tanh blend otherwise leaves
+    tails down to 1e-22 of the fresh fuel inside the burnt kernel, where the fractional-order
+    rate law has slopes of order Y^-1/2)."""
     rng = np.random.default_rng(seed)
     names = SPECIES["6sp"]
     cfg = _base_cfg(2, nx, ny, 1, storage, collision)
@@ -143,6 +145,8 @@ def chamber_2d(nx=1024, ny=256, storage="f32", seed=0, collision="cumulant", F=5
         cfg["Y_in"] = [float(v) for v in Yu]
     T = T_u + (T_hot - T_u) * b
     Y = Yu[:, None] * (1 - b)[None, :] + Yb[:, None] * b[None, :]
+    if y_floor:
+        Y[Y < y_floor] = 0.0
     u = np.zeros((2, nx * ny))
     inlet_u = np.zeros((2, ny))
     if inlet:
