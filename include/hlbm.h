@@ -201,7 +201,7 @@ lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* state_n, void* adj, void* 
  * adjoint of state n0 + n_steps on entry and that of state n0 on return (populations of solid
  * cells are set to zero); grad_inlet: as in lbm_adjoint_step (accumulated). Equivalent to
  * n_steps calls of lbm_adjoint_step with the saved states, without host round trips. The
- * context's state ends as state n0 + n_steps. */
+ * context's current state is left as it was. */
 lbm_status lbm_adjoint_segment(lbm_ctx* ctx, const void* checkpoint, int n_steps, void* adj, void* grad_inlet);
 
 /* Objective J = sum over fluid cells of the fuel consumption rate -omega_F (kg/(m^3 s), lattice

@@ -135,7 +135,8 @@ cudaError_t launch_adjoint_step2d(const AdjBuffers<R>& b, const LBArgs<R>& lbf, 
   if (e != cudaSuccess) return e;
   R* out_u = b.out + 9 * (size_t)N;
   if (!thermal) return cudaMemcpyAsync(out_u, b.u_lb, 2 * (size_t)N * sizeof(R), cudaMemcpyDeviceToDevice, st);
-  const int fb = (N + FD_BLOCK - 1) / FD_BLOCK;
+  const int fb = (N + FDA_CELLS - 1) / FDA_CELLS;
+  const dim3 fblock(FDA_CELLS, K + 1);
   FDAdjArgs<R> fa{};
   fa.f = fdf;
   fa.Tbar_out = b.in + 11 * (size_t)N;
@@ -145,21 +146,13 @@ cudaError_t launch_adjoint_step2d(const AdjBuffers<R>& b, const LBArgs<R>& lbf, 
   fa.lam_bar = b.lam_bar;
   fa.slots = b.slots;
   fa.u_bar = b.u_fd;
-  fd_adjoint_kernel<R><<<fb, FD_BLOCK, 0, st>>>(fa);
-  fd_adjoint_gather<R><<<fb, FD_BLOCK, 0, st>>>(g, fdf.sword, K, b.slots, b.T_lb, b.u_fd, b.u_lb,
+  fd_adjoint_kernel<R><<<fb, fblock, 0, st>>>(fa);
+  fd_adjoint_gather<R><<<fb, fblock, 0, st>>>(g, fdf.sword, K, b.slots, b.T_lb, b.u_fd, b.u_lb,
                                                  b.out + 11 * (size_t)N, b.out + 12 * (size_t)N, out_u);
   return cudaGetLastError();
 }
 
 namespace {
-template <typename R> __global__ void copy_list_kernel(CopyList<R> l) {
-  const int j = blockIdx.y;
-  const size_t n = l.n[j];
-  const R* __restrict__ s = l.src[j];
-  R* __restrict__ d = l.dst[j];
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    d[i] = s[i];
-}
 template <typename R> __global__ void zero_solid_pops_kernel(Geo g, const uint32_t* __restrict__ links, R* pops) {
   const int r = blockIdx.x * FD_BLOCK + threadIdx.x;
   if (r >= g.N || (__ldg(links + r) >> 31)) return;
@@ -169,16 +162,6 @@ template <typename R> __global__ void zero_solid_pops_kernel(Geo g, const uint32
 
 template <typename R> cudaError_t launch_zero_solid_pops(const Geo& g, const uint32_t* links, R* pops, cudaStream_t st) {
   zero_solid_pops_kernel<R><<<(g.N + FD_BLOCK - 1) / FD_BLOCK, FD_BLOCK, 0, st>>>(g, links, pops);
-  return cudaGetLastError();
-}
-
-template <typename R> cudaError_t launch_copy_list(const CopyList<R>& l, cudaStream_t st) {
-  if (l.count <= 0) return cudaSuccess;
-  size_t mx = 0;
-  for (int j = 0; j < l.count; ++j) mx = l.n[j] > mx ? l.n[j] : mx;
-  int bx = (int)((mx + 255) / 256);
-  bx = bx < 1 ? 1 : (bx > 4 * 152 ? 4 * 152 : bx);
-  copy_list_kernel<R><<<dim3(bx, l.count), 256, 0, st>>>(l);
   return cudaGetLastError();
 }
 
@@ -193,10 +176,8 @@ template cudaError_t launch_adjoint_step2d<float>(const AdjBuffers<float>&, cons
                                                   bool, cudaStream_t);
 template cudaError_t launch_adjoint_step2d<double>(const AdjBuffers<double>&, const LBArgs<double>&,
                                                    const FDArgs<double>&, bool, cudaStream_t);
-template cudaError_t launch_copy_list<float>(const CopyList<float>&, cudaStream_t);
 template cudaError_t launch_zero_solid_pops<float>(const Geo&, const uint32_t*, float*, cudaStream_t);
 template cudaError_t launch_zero_solid_pops<double>(const Geo&, const uint32_t*, double*, cudaStream_t);
-template cudaError_t launch_copy_list<double>(const CopyList<double>&, cudaStream_t);
 template cudaError_t launch_initial_T_adjoint<float>(const FDArgs<float>&, const float*, float*, cudaStream_t);
 template cudaError_t launch_initial_T_adjoint<double>(const FDArgs<double>&, const double*, double*, cudaStream_t);
 template cudaError_t launch_fuel_objective<float>(const FDArgs<float>&, int, float*, float*, double*, int, cudaStream_t);

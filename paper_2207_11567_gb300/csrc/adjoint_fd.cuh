@@ -10,6 +10,7 @@
 // whose stencils contain it.
 #pragma once
 #include "common.cuh"
+#include "fd_kernel.cuh"
 
 namespace hlbm {
 
@@ -30,8 +31,9 @@ __device__ __forceinline__ void weno_face_rev(R dab, R dbc, R eps, R fb, R& bb, 
   const R sab = dab * dab + eps, sbc = dbc * dbc + eps;
   const R tab = sab * sab, tbc = sbc * sbc;
   const R Nn = tbc * dab + R(2) * tab * dbc, Dn = tbc + R(2) * tab;
-  const R Nb = fb * R(0.5) / Dn;
-  const R Db = -fb * R(0.5) * Nn / (Dn * Dn);
+  const R iD = fdiv<R>(R(1), Dn);
+  const R Nb = fb * R(0.5) * iD;
+  const R Db = -Nb * Nn * iD;
   const R tabb = Nb * R(2) * dbc + Db * R(2);
   const R tbcb = Nb * dab + Db;
   bb = fb;
@@ -41,189 +43,209 @@ __device__ __forceinline__ void weno_face_rev(R dab, R dbc, R eps, R fb, R& bb, 
 template <typename R> __device__ __forceinline__ R weno_face(R b, R dab, R dbc, R eps) {
   const R sab = dab * dab + eps, sbc = dbc * dbc + eps;
   const R tab = sab * sab, tbc = sbc * sbc;
-  return b + R(0.5) * (tbc * dab + R(2) * tab * dbc) / (tbc + R(2) * tab);
+  return b + R(0.5) * fdiv<R>(tbc * dab + R(2) * tab * dbc, tbc + R(2) * tab);
 }
 
 // slot numbering: 0 center, 1 + 2*(2a+s) distance-1 point, 2 + 2*(2a+s) distance-2 point
 __device__ __forceinline__ int slot1(int ax, int sd) { return 1 + 2 * (2 * ax + sd); }
 __device__ __forceinline__ int slot2(int ax, int sd) { return 2 + 2 * (2 * ax + sd); }
 
-template <typename R>
-__global__ void __launch_bounds__(FD_BLOCK) fd_adjoint_kernel(const FDAdjArgs<R> A) {
-  const FDArgs<R>& a = A.f;
-  const FDConst<R>& c = a.c;
-  const Geo& g = a.geo;
-  const int r = blockIdx.x * FD_BLOCK + threadIdx.x;
-  if (r >= g.N) return;
-  const uint32_t sw = __ldg(a.sword + r);
-  if (!(sw >> 31)) return;
-  const int N = g.N;
-  const int K = c.K;
-  const int x = r % g.nx, y = r / g.nx;
-  const int pos[2] = {x, y}, dims[2] = {g.nx, g.ny}, strides[2] = {1, g.nx};
+// Thread layout of the adjoint kernels: blockDim = (FDA_CELLS, K + 1), x the cell within the
+// block, y the field (0: T, k + 1: Y_k), so that a cell's fields are reversed in parallel.
+constexpr int FDA_CELLS = 32;
+constexpr int FDA_THREADS = FDA_CELLS * (MAX_SP + 1);
+// per-field partial adjoints of the quantities the fields share, summed over the fields
+enum { PA_INVRHO = 0, PA_INVRPF, PA_QDOT, PA_TR, PA_W, PA_FM, PA_UR = PA_FM + 4, PA_Q = PA_UR + 2,
+       PA_N = PA_Q + MAX_RX };
+
+// Stencil of a cell: neighbour kinds and indices of the distance-1 and distance-2 points on each
+// side of each axis (ghost points copy the cell or the distance-1 point; inlet ghosts are
+// constants).
+struct FDStencil2 {
   int k1[2][2], k2[2][2], i1[2][2], i2[2][2];
+};
+__device__ __forceinline__ void fd_stencil2(const Geo& g, uint32_t sw, int r, int x, int y, FDStencil2& S) {
+  const int pos[2] = {x, y}, dims[2] = {g.nx, g.ny}, strides[2] = {1, g.nx};
 #pragma unroll
   for (int ax = 0; ax < 2; ++ax)
 #pragma unroll
     for (int sd = 0; sd < 2; ++sd) {
       const uint32_t bits = (sw >> (4 * (2 * ax + sd))) & 15u;
-      k1[ax][sd] = (int)(bits & 3u);
-      k2[ax][sd] = (int)(bits >> 2);
+      const int kk1 = (int)(bits & 3u), kk2 = (int)(bits >> 2);
       const int sg = sd ? 1 : -1;
       int p1 = pos[ax] + sg;
       p1 = p1 < 0 ? p1 + dims[ax] : (p1 >= dims[ax] ? p1 - dims[ax] : p1);
       int p2 = p1 + sg;
       p2 = p2 < 0 ? p2 + dims[ax] : (p2 >= dims[ax] ? p2 - dims[ax] : p2);
-      const int j1 = k1[ax][sd] == NB_FLUID ? r + (p1 - pos[ax]) * strides[ax] : r;
-      i1[ax][sd] = j1;
-      i2[ax][sd] = k2[ax][sd] == 0 ? r + (p2 - pos[ax]) * strides[ax] : j1;
+      const int j1 = kk1 == NB_FLUID ? r + (p1 - pos[ax]) * strides[ax] : r;
+      S.k1[ax][sd] = kk1;
+      S.k2[ax][sd] = kk2;
+      S.i1[ax][sd] = j1;
+      S.i2[ax][sd] = kk2 == 0 ? r + (p2 - pos[ax]) * strides[ax] : j1;
     }
-  // target slot of the adjoint of each stencil point (fold ghosts onto the cell they copy)
-  int t1s[2][2], t2s[2][2];
+}
+
+// Rate q_j of one cell, the same arithmetic as reaction_rates of the forward kernel.
+template <typename R>
+__device__ __forceinline__ R rate_of(const FDConst<R>& c, int j, R T, const R* __restrict__ Y, size_t N, int r,
+                                     R rho_phys) {
+  R v;
+  if constexpr (sizeof(R) == 4) v = c.A[j] * arrhenius(c.ER_hi[j], c.ER_lo[j], T);
+  else v = c.A[j] * exp(-c.ER_hi[j] / T);
+  if (c.beta[j] != R(0)) v *= powr<R>(T, c.beta[j]);
 #pragma unroll
-  for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-    for (int sd = 0; sd < 2; ++sd) {
-      t1s[ax][sd] = k1[ax][sd] == NB_FLUID ? slot1(ax, sd) : (k1[ax][sd] == NB_INLET ? -1 : 0);
-      if (k2[ax][sd] == 0) t2s[ax][sd] = slot2(ax, sd);
-      else if (k2[ax][sd] == 2) t2s[ax][sd] = -1;
-      else t2s[ax][sd] = t1s[ax][sd];
-    }
+  for (int m = 0; m < MAX_ORD; ++m) {
+    if (m >= c.nord[j]) break;
+    const int k = c.ord_k[j][m];
+    const R n = c.ord_n[j][m];
+    const R conc = rho_phys * fmax(Y[(size_t)k * N + r], R(0)) * c.inv_W[k];
+    v *= (n == R(1)) ? conc : powr<R>(conc, n);
+  }
+  return v;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(FDA_THREADS) fd_adjoint_kernel(const FDAdjArgs<R> A) {
+  __shared__ R part[MAX_SP + 1][PA_N][FDA_CELLS];
+  __shared__ R sh_q[MAX_RX][FDA_CELLS];
+  __shared__ R sh_mu[5][FDA_CELLS];  // mu(T_r), then mu at the distance-1 points (-x, +x, -y, +y)
+  const FDArgs<R>& a = A.f;
+  const FDConst<R>& c = a.c;
+  const Geo& g = a.geo;
+  const int N = g.N, K = c.K;
+  const int tx = threadIdx.x, fi = threadIdx.y;
+  const int r = blockIdx.x * FDA_CELLS + tx;
+  const uint32_t sw = r < N ? __ldg(a.sword + r) : 0u;
+  const bool act = (sw >> 31) != 0u;  // every thread reaches the barriers below
+  const int x = r % g.nx, y = r / g.nx;
+  FDStencil2 S;
+  fd_stencil2(g, sw, r, x, y, S);
 
   // ------------------------------------------------------------ forward: shared quantities
-  const R Tr = a.T[r];
-  R Yr[MAX_SP];
-  R sW = R(0);
-  for (int k = 0; k < K; ++k) {
-    Yr[k] = a.Y[k * N + r];
-    sW += Yr[k] * c.inv_W[k];
-  }
-  const R W = R(1) / sW;
-  const R fdr = sizeof(R) == 4 ? (R)a.pth->fd_rho : (R)a.pth->fd_rho_d;
-  const R rho = fdr * W / Tr;
-  const R rho_phys = rho / c.inv_rho_ref;
-  const R inv_rho = R(1) / rho;
-  R q[MAX_RX];
-  for (int j = 0; j < c.nrx; ++j) {
-    R v = c.A[j] * exp(-(c.ER_hi[j] + c.ER_lo[j]) / Tr);
-    if (c.beta[j] != R(0)) v *= pow(Tr, c.beta[j]);
-    for (int m = 0; m < c.nord[j]; ++m) {
-      const int k = c.ord_k[j][m];
-      const R y = Yr[k];
-      v *= y > R(0) ? pow(rho_phys * y * c.inv_W[k], c.ord_n[j][m]) : R(0);
-    }
-    q[j] = v;
-  }
+  R Tr = R(1), W = R(1), rho = R(1), rho_phys = R(1), inv_rho = R(1);
   const R F = c.F;
-  const R mur = c.nu_lat * pow(Tr * c.T_ref_inv, c.mu_exp);
-  const R ur[2] = {a.u[r], a.u[N + r]};
-  const int f = y;
-  R FMf[2][2], uf[2][2], Tn[2][2], mun[2][2];
+  const R fdr = sizeof(R) == 4 ? (R)a.pth->fd_rho : (R)a.pth->fd_rho_d;
+  R Tn[2][2];
+  if (act) {
+    Tr = a.T[r];
+    R sW = R(0);
+    for (int k = 0; k < K; ++k) sW += a.Y[(size_t)k * N + r] * c.inv_W[k];
+    W = R(1) / sW;
+    rho = fdr * W / Tr;
+    rho_phys = rho / c.inv_rho_ref;
+    inv_rho = R(1) / rho;
 #pragma unroll
-  for (int ax = 0; ax < 2; ++ax)
+    for (int ax = 0; ax < 2; ++ax)
 #pragma unroll
-    for (int sd = 0; sd < 2; ++sd) {
-      const int kk = k1[ax][sd], j = i1[ax][sd];
-      Tn[ax][sd] = kk == NB_FLUID ? a.T[j] : (kk == NB_INLET ? c.T_in : Tr);
-      mun[ax][sd] = c.nu_lat * pow(Tn[ax][sd] * c.T_ref_inv, c.mu_exp);
-      FMf[ax][sd] = R(0.5) * (F * mur + F * mun[ax][sd]);
-      R un;
-      if (kk == NB_FLUID) un = a.u[ax * N + j];
-      else if (kk == NB_INLET) un = a.inlet_u[ax * g.ny + f];
-      else if (kk == NB_OUTLET) un = ur[ax];
-      else un = R(0);
-      uf[ax][sd] = R(0.5) * (ur[ax] + un);
+      for (int sd = 0; sd < 2; ++sd) {
+        const int kk = S.k1[ax][sd];
+        Tn[ax][sd] = kk == NB_FLUID ? a.T[S.i1[ax][sd]] : (kk == NB_INLET ? c.T_in : Tr);
+      }
+    // transcendental work shared out over the cell's threads: task 0 the rates, task 1 mu(T_r),
+    // tasks 2..5 mu at the distance-1 points
+    for (int t = fi; t < 6; t += K + 1) {
+      if (t == 0) {
+#pragma unroll
+        for (int j = 0; j < MAX_RX; ++j)
+          if (j < c.nrx) sh_q[j][tx] = rate_of<R>(c, j, Tr, a.Y, N, r, rho_phys);
+      } else {
+        const R Tt = t == 1 ? Tr : Tn[(t - 2) >> 1][(t - 2) & 1];
+        sh_mu[t - 1][tx] = c.nu_lat * powr<R>(Tt * c.T_ref_inv, c.mu_exp);
+      }
     }
+  }
+  __syncthreads();
+  R q[MAX_RX], mun[2][2], FMf[2][2], uf[2][2], ur[2] = {R(0), R(0)};
+  R mur = R(0), inv_rpF = R(0), qdot = R(0);
+  if (act) {
+#pragma unroll
+    for (int j = 0; j < MAX_RX; ++j) {
+      q[j] = j < c.nrx ? sh_q[j][tx] : R(0);
+      qdot += c.heat[j] * q[j];
+    }
+    mur = sh_mu[0][tx];
+    ur[0] = a.u[r];
+    ur[1] = a.u[N + r];
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int kk = S.k1[ax][sd], j = S.i1[ax][sd];
+        mun[ax][sd] = sh_mu[1 + 2 * ax + sd][tx];
+        FMf[ax][sd] = R(0.5) * (F * mur + F * mun[ax][sd]);
+        R un;
+        if (kk == NB_FLUID) un = a.u[ax * N + j];
+        else if (kk == NB_INLET) un = a.inlet_u[ax * g.ny + y];
+        else if (kk == NB_OUTLET) un = ur[ax];
+        else un = R(0);
+        uf[ax][sd] = R(0.5) * (ur[ax] + un);
+      }
+    inv_rpF = R(1) / (rho_phys * F);
+  }
   const R dt = c.dt_phys;
-  const R inv_rpF = R(1) / (rho_phys * F);
-  R qdot = R(0);
-  for (int j = 0; j < c.nrx; ++j) qdot += c.heat[j] * q[j];
 
-  // per-field values: NA and the diffusion sum, needed by the Lambda reverse
-  R NAv[MAX_SP + 1], difs[MAX_SP + 1];
-  for (int fi = 0; fi <= K; ++fi) {
-    const R* phi = fi == 0 ? a.T : a.Y + (size_t)(fi - 1) * N;
-    const R phin = fi == 0 ? c.T_in : c.Y_in[fi - 1];
-    const R gfac = c.inv_Pr * (fi == 0 ? R(1) : c.inv_Le[fi - 1]);
-    const R pr = phi[r];
-    R dif = R(0);
-    for (int ax = 0; ax < 2; ++ax) {
-      const R m1 = k1[ax][0] == NB_INLET ? phin : phi[i1[ax][0]];
-      const R p1 = k1[ax][1] == NB_INLET ? phin : phi[i1[ax][1]];
-      dif += FMf[ax][1] * (p1 - pr) - FMf[ax][0] * (pr - m1);
-    }
-    difs[fi] = dif;
-    R src;
-    if (fi == 0) {
-      src = dt * qdot * inv_rpF * c.inv_cp;
-    } else {
-      R om = R(0);
-      for (int j = 0; j < c.nrx; ++j) om += c.nu[j][fi - 1] * q[j];
-      src = dt * c.W[fi - 1] * om * inv_rpF;
-    }
-    NAv[fi] = gfac * inv_rho * dif + src;
-  }
-
-  // ------------------------------------------------------------------------- reverse
-  const R lamb = A.lam_bar[r];
-  // adjoint of rho^n: the cell's own part plus the density-gradient parts of the cells that
-  // hold it as their -x / +x / -y / +y neighbour (zero where that cell is solid or mirrored it)
-  R rhob = A.rho_own[r];
-  {
-    const int xm = x > 0 ? r - 1 : (g.bc_lo[0] == BC_PERIODIC ? r + g.nx - 1 : -1);
-    const int xp = x < g.nx - 1 ? r + 1 : (g.bc_hi[0] == BC_PERIODIC ? r - g.nx + 1 : -1);
-    const int ym = y > 0 ? r - g.nx : (g.bc_lo[1] == BC_PERIODIC ? r + (g.ny - 1) * g.nx : -1);
-    const int yp = y < g.ny - 1 ? r + g.nx : (g.bc_hi[1] == BC_PERIODIC ? r - (g.ny - 1) * g.nx : -1);
-    if (xm >= 0) rhob += A.rho_nb[xm];
-    if (xp >= 0) rhob += A.rho_nb[N + xp];
-    if (ym >= 0) rhob += A.rho_nb[2 * N + ym];
-    if (yp >= 0) rhob += A.rho_nb[3 * N + yp];
-  }
-  R Trb = R(0), Wb = R(0), inv_rhob = R(0), inv_rpFb = R(0), qdotb = R(0);
-  R qb[MAX_RX];
-  for (int j = 0; j < MAX_RX; ++j) qb[j] = R(0);
-  R Ycb[MAX_SP];  // center adjoint of Y from shared terms
-  for (int k = 0; k < MAX_SP; ++k) Ycb[k] = R(0);
-  R FMb[2][2] = {{R(0), R(0)}, {R(0), R(0)}};
-  R urb[2] = {R(0), R(0)};
-  // Lambda = NA_T / T + sum_k W / W_k NA_k
-  Trb -= lamb * NAv[0] / (Tr * Tr);
-  for (int k = 0; k < K; ++k) Wb += lamb * c.inv_W[k] * NAv[k + 1];
-
-  for (int fi = 0; fi <= K; ++fi) {
+  // ------------------------------------------------------------- this thread's field
+  // pointb: adjoints of the 9 stencil values (slot order), constant indices only
+  R pointb[9];
+#pragma unroll
+  for (int p = 0; p < 9; ++p) pointb[p] = R(0);
+  R pa[PA_N];
+#pragma unroll
+  for (int p = 0; p < PA_N; ++p) pa[p] = R(0);
+  if (act) {
     const R* phi = fi == 0 ? a.T : a.Y + (size_t)(fi - 1) * N;
     const R phin = fi == 0 ? c.T_in : c.Y_in[fi - 1];
     const R eps = fi == 0 ? c.eps_T : c.eps_Y;
     const R gfac = c.inv_Pr * (fi == 0 ? R(1) : c.inv_Le[fi - 1]);
-    const R outb = fi == 0 ? A.Tbar_out[r] : A.Ybar_out[(size_t)(fi - 1) * N + r];
-    const R NAb = outb + (fi == 0 ? lamb / Tr : lamb * W * c.inv_W[fi - 1]);
-    R pointb[9];
-#pragma unroll
-    for (int p = 0; p < 9; ++p) pointb[p] = R(0);
-    pointb[0] = outb;  // out = pr - adv + NA
     const R pr = phi[r];
-    // diffusion: NA += gfac inv_rho sum_a (FMp dp1 - FMm dm1)
-    inv_rhob += NAb * gfac * difs[fi];
-    const R gi = NAb * gfac * inv_rho;
+    R pm2[2], pm1[2], pp1[2], pp2[2];
+    R dif = R(0);
+#pragma unroll
     for (int ax = 0; ax < 2; ++ax) {
-      const R m2 = k2[ax][0] == 2 ? phin : phi[i2[ax][0]];
-      const R m1 = k1[ax][0] == NB_INLET ? phin : phi[i1[ax][0]];
-      const R p1 = k1[ax][1] == NB_INLET ? phin : phi[i1[ax][1]];
-      const R p2 = k2[ax][1] == 2 ? phin : phi[i2[ax][1]];
+      pm2[ax] = S.k2[ax][0] == 2 ? phin : phi[S.i2[ax][0]];
+      pm1[ax] = S.k1[ax][0] == NB_INLET ? phin : phi[S.i1[ax][0]];
+      pp1[ax] = S.k1[ax][1] == NB_INLET ? phin : phi[S.i1[ax][1]];
+      pp2[ax] = S.k2[ax][1] == 2 ? phin : phi[S.i2[ax][1]];
+      dif += FMf[ax][1] * (pp1[ax] - pr) - FMf[ax][0] * (pr - pm1[ax]);
+    }
+    R om = R(0), src;
+    if (fi == 0) {
+      src = dt * qdot * inv_rpF * c.inv_cp;
+    } else {
+#pragma unroll
+      for (int j = 0; j < MAX_RX; ++j) om += c.nu[j][fi - 1] * q[j];
+      src = dt * c.W[fi - 1] * om * inv_rpF;
+    }
+    const R NA = gfac * inv_rho * dif + src;
+    // reverse. Lambda = NA_T / T + sum_k W / W_k NA_k; out = phi - adv + NA
+    const R lamb = A.lam_bar[r];
+    const R outb = fi == 0 ? A.Tbar_out[r] : A.Ybar_out[(size_t)(fi - 1) * N + r];
+    R NAb;
+    if (fi == 0) {
+      pa[PA_TR] = -lamb * NA / (Tr * Tr);
+      NAb = outb + lamb / Tr;
+    } else {
+      pa[PA_W] = lamb * c.inv_W[fi - 1] * NA;
+      NAb = outb + lamb * W * c.inv_W[fi - 1];
+    }
+    pointb[0] = outb;
+    pa[PA_INVRHO] = NAb * gfac * dif;
+    const R gi = NAb * gfac * inv_rho;
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+      const R m2 = pm2[ax], m1 = pm1[ax], p1 = pp1[ax], p2 = pp2[ax];
       R m2b = R(0), m1b = R(0), p1b = R(0), p2b = R(0), prb = R(0);
-      FMb[ax][1] += gi * (p1 - pr);
-      FMb[ax][0] -= gi * (pr - m1);
+      pa[PA_FM + 2 * ax + 1] += gi * (p1 - pr);
+      pa[PA_FM + 2 * ax] -= gi * (pr - m1);
       p1b += gi * FMf[ax][1];
-      prb -= gi * FMf[ax][1];
-      prb -= gi * FMf[ax][0];
+      prb -= gi * (FMf[ax][1] + FMf[ax][0]);
       m1b += gi * FMf[ax][0];
-      // advection: out -= ur (fp - fm)
       const bool up = uf[ax][1] >= R(0), um = uf[ax][0] >= R(0);
       const R dm2 = m1 - m2, dm1 = pr - m1, dp1 = p1 - pr, dp2 = p2 - p1;
       const R fp = up ? weno_face<R>(pr, dm1, dp1, eps) : weno_face<R>(p1, -dp2, -dp1, eps);
       const R fm = um ? weno_face<R>(m1, dm2, dm1, eps) : weno_face<R>(pr, -dp1, -dm1, eps);
       const R advb = -outb;
-      urb[ax] += advb * (fp - fm);
+      pa[PA_UR + ax] += advb * (fp - fm);
       const R fpb = advb * ur[ax], fmb = -advb * ur[ax];
       R bb, dab, dbc;
       if (up) {
@@ -241,126 +263,176 @@ __global__ void __launch_bounds__(FD_BLOCK) fd_adjoint_kernel(const FDAdjArgs<R>
         prb += bb + dab - dbc; p1b -= dab; m1b += dbc;
       }
       pointb[0] += prb;
-      if (t1s[ax][0] >= 0) pointb[t1s[ax][0]] += m1b;
-      if (t1s[ax][1] >= 0) pointb[t1s[ax][1]] += p1b;
-      if (t2s[ax][0] >= 0) pointb[t2s[ax][0]] += m2b;
-      if (t2s[ax][1] >= 0) pointb[t2s[ax][1]] += p2b;
+      // distance-1 points: a fluid neighbour's slot, the cell itself (zero-gradient ghost) or
+      // nothing (inlet constant); distance-2 points likewise, or the distance-1 point they copy
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const R v1 = sd ? p1b : m1b, v2 = sd ? p2b : m2b;
+        const int kk1 = S.k1[ax][sd], kk2 = S.k2[ax][sd];
+        const R to1 = v1 + (kk2 == 1 ? v2 : R(0));
+        if (kk1 == NB_FLUID) pointb[slot1(ax, sd)] += to1;
+        else if (kk1 != NB_INLET) pointb[0] += to1;
+        if (kk2 == 0) pointb[slot2(ax, sd)] += v2;
+      }
     }
-    // sources
     if (fi == 0) {
-      qdotb += NAb * dt * inv_rpF * c.inv_cp;
-      inv_rpFb += NAb * dt * qdot * c.inv_cp;
+      pa[PA_QDOT] = NAb * dt * inv_rpF * c.inv_cp;
+      pa[PA_INVRPF] = NAb * dt * qdot * c.inv_cp;
     } else {
-      R om = R(0);
-      for (int j = 0; j < c.nrx; ++j) om += c.nu[j][fi - 1] * q[j];
       const R omb = NAb * dt * c.W[fi - 1] * inv_rpF;
-      inv_rpFb += NAb * dt * c.W[fi - 1] * om;
-      for (int j = 0; j < c.nrx; ++j) qb[j] += c.nu[j][fi - 1] * omb;
-    }
-    // the center adjoint of the shared terms (rho, W, chemistry) is added after the loop
+      pa[PA_INVRPF] = NAb * dt * c.W[fi - 1] * om;
 #pragma unroll
-    for (int p = 0; p < 9; ++p) A.slots[((size_t)p * (K + 1) + fi) * N + r] = pointb[p];
-  }
-  // chemistry and shared terms
-  for (int j = 0; j < c.nrx; ++j) qb[j] += c.heat[j] * qdotb;
-  R rho_physb = -inv_rpFb * inv_rpF / rho_phys;
-  for (int j = 0; j < c.nrx; ++j) {
-    const R qq = q[j] * qb[j];
-    Trb += qq * ((c.ER_hi[j] + c.ER_lo[j]) / (Tr * Tr) + c.beta[j] / Tr);
-    for (int m = 0; m < c.nord[j]; ++m) {
-      const int k = c.ord_k[j][m];
-      if (Yr[k] > R(0)) {
-        rho_physb += qq * c.ord_n[j][m] / rho_phys;
-        Ycb[k] += qq * c.ord_n[j][m] / Yr[k];
-      }
+      for (int j = 0; j < MAX_RX; ++j) pa[PA_Q + j] = c.nu[j][fi - 1] * omb;
     }
   }
-  rhob += rho_physb / c.inv_rho_ref;
-  rhob -= inv_rhob * inv_rho * inv_rho;
-  Wb += rhob * fdr / Tr;
-  Trb -= rhob * rho / Tr;
-  const R sWb = -Wb * W * W;
-  for (int k = 0; k < K; ++k) Ycb[k] += sWb * c.inv_W[k];
-  // face coefficients: FM = F (mu_r + mu_n) / 2
-  R murb = R(0);
 #pragma unroll
-  for (int ax = 0; ax < 2; ++ax)
+  for (int p = 0; p < PA_N; ++p) part[fi][p][tx] = pa[p];
+  __syncthreads();
+  // ---------------------- shared terms, once per cell (thread fi = 0): sums over the fields,
+  // reverse of the rate law, rho = P W / (R T), W and mu(T); the center adjoint of each species
+  // goes to the field threads through shared memory
+  __shared__ R sh_add[MAX_SP][FDA_CELLS];
+  if (act && fi == 0) {
+    R tot[PA_N];
 #pragma unroll
-    for (int sd = 0; sd < 2; ++sd) {
-      murb += R(0.5) * F * FMb[ax][sd];
-      const R munb = R(0.5) * F * FMb[ax][sd];
-      const R dmu = munb * c.mu_exp * mun[ax][sd] / Tn[ax][sd];
-      const int kk = k1[ax][sd];
-      if (kk == NB_FLUID) A.slots[((size_t)slot1(ax, sd) * (K + 1) + 0) * N + r] += dmu;
-      else if (kk != NB_INLET) Trb += dmu;
+    for (int p = 0; p < PA_N; ++p) {
+      R v = R(0);
+      for (int f = 0; f <= K; ++f) v += part[f][p][tx];
+      tot[p] = v;
     }
-  Trb += murb * c.mu_exp * mur / Tr;
-  A.slots[(size_t)0 * N + r] += Trb;
-  for (int k = 0; k < K; ++k) A.slots[((size_t)(k + 1)) * N + r] += Ycb[k];
-  A.u_bar[r] = urb[0];
-  A.u_bar[N + r] = urb[1];
-}
-
-// Sum of the slot adjoints for every cell: its own center slot plus the distance-1 and
-// distance-2 slots of the cells whose stencil points land on it.
-template <typename R>
-__global__ void fd_adjoint_gather(Geo g, const uint32_t* __restrict__ sword, int K, const R* __restrict__ slots,
-                                  const R* __restrict__ T_lb, const R* __restrict__ u_fd,
-                                  const R* __restrict__ u_lb, R* __restrict__ Tbar, R* __restrict__ Ybar,
-                                  R* __restrict__ ubar) {
-  const int s = blockIdx.x * FD_BLOCK + threadIdx.x;
-  if (s >= g.N) return;
-  const int N = g.N;
-  if (!(__ldg(sword + s) >> 31)) {
-    Tbar[s] = R(0);
-    for (int k = 0; k < K; ++k) Ybar[(size_t)k * N + s] = R(0);
-    ubar[s] = R(0);
-    ubar[N + s] = R(0);
-    return;
-  }
-  const int x = s % g.nx, y = s / g.nx;
-  const int pos[2] = {x, y}, dims[2] = {g.nx, g.ny}, strides[2] = {1, g.nx};
-  const int lo[2] = {g.bc_lo[0], g.bc_lo[1]};
-  // cells whose distance-1 / distance-2 point on side sd of axis ax is s
-  int c1[2][2], c2[2][2];
+    R Trb = tot[PA_TR], Wb = tot[PA_W];
+    R rho_physb = -tot[PA_INVRPF] * inv_rpF / rho_phys;
+    for (int k = 0; k < K; ++k) sh_add[k][tx] = R(0);
 #pragma unroll
-  for (int ax = 0; ax < 2; ++ax)
+    for (int j = 0; j < MAX_RX; ++j) {
+      if (j >= c.nrx) break;
+      const R qq = q[j] * (tot[PA_Q + j] + c.heat[j] * tot[PA_QDOT]);
+      Trb += qq * ((c.ER_hi[j] + c.ER_lo[j]) / (Tr * Tr) + c.beta[j] / Tr);
 #pragma unroll
-    for (int sd = 0; sd < 2; ++sd) {
-      const int sg = sd ? 1 : -1;
-      const bool per = lo[ax] == BC_PERIODIC;
-      int q1 = pos[ax] - sg, q2 = pos[ax] - 2 * sg;
-      bool ok1 = true, ok2 = true;
-      if (q1 < 0 || q1 >= dims[ax]) { if (per) q1 = (q1 + dims[ax]) % dims[ax]; else ok1 = false; }
-      if (q2 < 0 || q2 >= dims[ax]) { if (per) q2 = ((q2 % dims[ax]) + dims[ax]) % dims[ax]; else ok2 = false; }
-      int r1 = ok1 ? s + (q1 - pos[ax]) * strides[ax] : -1;
-      int r2 = ok2 ? s + (q2 - pos[ax]) * strides[ax] : -1;
-      // the cell's stencil point is s only when that point is a real (fluid) neighbour
-      if (r1 >= 0) {
-        const uint32_t w = __ldg(sword + r1);
-        if (!(w >> 31) || ((w >> (4 * (2 * ax + sd))) & 3u) != 0u) r1 = -1;
+      for (int m = 0; m < MAX_ORD; ++m) {
+        if (m >= c.nord[j]) break;
+        const int k = c.ord_k[j][m];
+        const R yk = a.Y[(size_t)k * N + r];
+        if (yk > R(0)) {
+          rho_physb += qq * c.ord_n[j][m] / rho_phys;
+          sh_add[k][tx] += qq * c.ord_n[j][m] / yk;
+        }
       }
-      if (r2 >= 0) {
-        const uint32_t w = __ldg(sword + r2);
-        if (!(w >> 31) || ((w >> (4 * (2 * ax + sd) + 2)) & 3u) != 0u) r2 = -1;
-      }
-      c1[ax][sd] = r1;
-      c2[ax][sd] = r2;
     }
-  for (int fi = 0; fi <= K; ++fi) {
-    R v = slots[((size_t)0 * (K + 1) + fi) * N + s];
+    // adjoint of rho^n: own LB part, density-gradient parts of the cells holding it as their
+    // -x / +x / -y / +y neighbour (zero where that cell is solid or mirrored it), this update
+    R rhob = A.rho_own[r];
+    {
+      const int xm = x > 0 ? r - 1 : (g.bc_lo[0] == BC_PERIODIC ? r + g.nx - 1 : -1);
+      const int xp = x < g.nx - 1 ? r + 1 : (g.bc_hi[0] == BC_PERIODIC ? r - g.nx + 1 : -1);
+      const int ym = y > 0 ? r - g.nx : (g.bc_lo[1] == BC_PERIODIC ? r + (g.ny - 1) * g.nx : -1);
+      const int yp = y < g.ny - 1 ? r + g.nx : (g.bc_hi[1] == BC_PERIODIC ? r - (g.ny - 1) * g.nx : -1);
+      if (xm >= 0) rhob += A.rho_nb[xm];
+      if (xp >= 0) rhob += A.rho_nb[N + xp];
+      if (ym >= 0) rhob += A.rho_nb[2 * N + ym];
+      if (yp >= 0) rhob += A.rho_nb[3 * N + yp];
+    }
+    rhob += rho_physb / c.inv_rho_ref;
+    rhob -= tot[PA_INVRHO] * inv_rho * inv_rho;
+    Wb += rhob * fdr / Tr;
+    Trb -= rhob * rho / Tr;
+    const R sWb = -Wb * W * W;
+    for (int k = 0; k < K; ++k) sh_add[k][tx] += sWb * c.inv_W[k];
+    // face coefficients FM = F (mu_r + mu_n) / 2, mu = nu (T / T_ref)^mu_exp
+    R murb = R(0);
 #pragma unroll
     for (int ax = 0; ax < 2; ++ax)
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
-        if (c1[ax][sd] >= 0) v += slots[((size_t)slot1(ax, sd) * (K + 1) + fi) * N + c1[ax][sd]];
-        if (c2[ax][sd] >= 0) v += slots[((size_t)slot2(ax, sd) * (K + 1) + fi) * N + c2[ax][sd]];
+        const R munb = R(0.5) * F * tot[PA_FM + 2 * ax + sd];
+        murb += munb;
+        const R dmu = munb * c.mu_exp * mun[ax][sd] / Tn[ax][sd];
+        const int kk = S.k1[ax][sd];
+        if (kk == NB_FLUID) pointb[slot1(ax, sd)] += dmu;
+        else if (kk != NB_INLET) Trb += dmu;
       }
-    if (fi == 0) Tbar[s] = v + T_lb[s];
-    else Ybar[(size_t)(fi - 1) * N + s] = v;
+    Trb += murb * c.mu_exp * mur / Tr;
+    pointb[0] += Trb;
+    A.u_bar[r] = tot[PA_UR];
+    A.u_bar[N + r] = tot[PA_UR + 1];
   }
-  ubar[s] = u_fd[s] + u_lb[s];
-  ubar[N + s] = u_fd[N + s] + u_lb[N + s];
+  __syncthreads();
+  if (!act) return;
+  if (fi > 0) pointb[0] += sh_add[fi - 1][tx];
+  const size_t fs = (size_t)(K + 1) * N;  // stride between slots
+  R* out = A.slots + (size_t)fi * N + r;
+#pragma unroll
+  for (int p = 0; p < 9; ++p) out[(size_t)p * fs] = pointb[p];
+}
+
+// Sum of the slot adjoints for every (cell, field): the cell's own center slot plus the
+// distance-1 and distance-2 slots of the cells whose stencil points land on it. Same thread
+// layout as fd_adjoint_kernel; the field-0 thread of each cell finds those cells once.
+template <typename R>
+__global__ void __launch_bounds__(FDA_THREADS)
+    fd_adjoint_gather(Geo g, const uint32_t* __restrict__ sword, int K, const R* __restrict__ slots,
+                      const R* __restrict__ T_lb, const R* __restrict__ u_fd, const R* __restrict__ u_lb,
+                      R* __restrict__ Tbar, R* __restrict__ Ybar, R* __restrict__ ubar) {
+  __shared__ int src[8][FDA_CELLS];  // cell whose (axis, side, distance) point is s, or -1
+  const int tx = threadIdx.x, fi = threadIdx.y;
+  const int s = blockIdx.x * FDA_CELLS + tx;
+  const int N = g.N;
+  const bool inside = s < N;
+  const bool fluid = inside && (__ldg(sword + s) >> 31);
+  if (fi == 0 && fluid) {
+    const int x = s % g.nx, y = s / g.nx;
+    const int pos[2] = {x, y}, dims[2] = {g.nx, g.ny}, strides[2] = {1, g.nx};
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int sg = sd ? 1 : -1;
+        const bool per = g.bc_lo[ax] == BC_PERIODIC;
+#pragma unroll
+        for (int dist = 1; dist <= 2; ++dist) {
+          int qd = pos[ax] - dist * sg;
+          bool ok = true;
+          if (qd < 0 || qd >= dims[ax]) {
+            if (per) qd = ((qd % dims[ax]) + dims[ax]) % dims[ax];
+            else ok = false;
+          }
+          int rc = -1;
+          if (ok) {
+            // that cell's stencil point is s only when the point is a real (fluid) neighbour
+            const int cand = s + (qd - pos[ax]) * strides[ax];
+            const uint32_t w = __ldg(sword + cand);
+            if ((w >> 31) && ((w >> (4 * (2 * ax + sd) + 2 * (dist - 1))) & 3u) == 0u) rc = cand;
+          }
+          src[2 * (2 * ax + sd) + dist - 1][tx] = rc;
+        }
+      }
+  }
+  __syncthreads();
+  if (!inside || fi > K) return;
+  R* dst = fi == 0 ? Tbar + s : Ybar + (size_t)(fi - 1) * N + s;
+  if (!fluid) {
+    *dst = R(0);
+    if (fi == 0) {
+      ubar[s] = R(0);
+      ubar[N + s] = R(0);
+    }
+    return;
+  }
+  const size_t fs = (size_t)(K + 1) * N;
+  const R* sl = slots + (size_t)fi * N;
+  R v = sl[s];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int rc = src[t][tx];
+    if (rc >= 0) v += sl[(size_t)(1 + t) * fs + rc];  // slot 1 + t: distance 1 + (t & 1), side t >> 1
+  }
+  if (fi == 0) {
+    *dst = v + T_lb[s];
+    ubar[s] = u_fd[s] + u_lb[s];
+    ubar[N + s] = u_fd[N + s] + u_lb[N + s];
+  } else {
+    *dst = v;
+  }
 }
 
 }  // namespace hlbm

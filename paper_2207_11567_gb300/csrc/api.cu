@@ -177,6 +177,7 @@ template <typename R> LBArgs<R> make_lb_args(lbm_ctx* c, int cur, bool want_out)
   a.T = (const R*)c->T[cur];
   a.inlet_u = (const R*)c->inlet_u;
   a.u = (R*)c->u;
+  a.u_in = a.u;
   a.write_u = (c->cfg.thermal || want_out) ? 1 : 0;
   a.ph_out = want_out ? (R*)c->ph : nullptr;
   a.pth = c->pth;
@@ -871,13 +872,14 @@ template <typename R> lbm_status adjoint_step_impl(lbm_ctx* ctx, const void* sta
   return LBM_OK;
 }
 
-// Reverse sweep over one checkpoint segment. Recompute: from the checkpoint, n steps, keeping
-// state k and the rho^k, Lambda^k its step computed in slot k. Reverse: the adjoint step over
-// slots n-1 .. 0, reading each slot in place, alternating between adj and the internal buffer.
+// Reverse sweep over one checkpoint segment. Recompute: n steps from the checkpoint, state k + 1
+// written straight into slot k + 1 (the checkpoint itself serves as state 0), rho^k, Lambda^k
+// into the segment's rho/Lambda arrays; the last step needs its FD pass only. Reverse: the
+// adjoint step over the states n - 1 .. 0, read in place, alternating between adj and the
+// internal buffer. The context's current state is not touched.
 template <typename R>
 lbm_status adjoint_segment_impl(lbm_ctx* ctx, const void* checkpoint, int n, void* adj, void* grad_inlet) {
   const size_t N = ctx->N;
-  const int K = ctx->K;
   const bool th = ctx->cfg.thermal != 0;
   R *scratch, *buf;
   lbm_status st = ensure_adj_ws<R>(ctx, &scratch, &buf);
@@ -889,54 +891,67 @@ lbm_status adjoint_segment_impl(lbm_ctx* ctx, const void* checkpoint, int n, voi
       return fail(ctx, LBM_ERR_ALLOC, "adjoint segment workspace allocation failed");
     ctx->seg_cap = n;
   }
-  R* seg = (R*)ctx->seg_ws;
-  if ((st = lbm_load_state(ctx, checkpoint)) != LBM_OK) return st;
-  auto state_copy = [&](CopyList<R>& l, R* slot) {
-    const int cur = ctx->cur;
-    int j = l.count;
-    l.src[j] = (const R*)ctx->g[cur]; l.dst[j] = slot; l.n[j++] = 9 * N;
-    l.src[j] = (const R*)ctx->u; l.dst[j] = slot + 9 * N; l.n[j++] = 2 * N;
-    if (th) {
-      l.src[j] = (const R*)ctx->T[cur]; l.dst[j] = slot + 11 * N; l.n[j++] = N;
-      l.src[j] = (const R*)ctx->Y[cur]; l.dst[j] = slot + 12 * N; l.n[j++] = (size_t)K * N;
-    }
-    l.count = j;
-  };
-  {
-    CopyList<R> l{};
-    state_copy(l, seg);
-    CK(launch_copy_list<R>(l, ctx->st), "segment snapshot");
-  }
+  R* ws = (R*)ctx->seg_ws;
+  // slot k: state k (k >= 1) then rho^k, Lambda^k; state 0 is the checkpoint
+  auto state_of = [&](int k) -> R* { return k == 0 ? (R*)checkpoint : ws + (size_t)k * slot_w; };
+  auto rho_of = [&](int k) -> R* { return ws + (size_t)k * slot_w + sw; };
+  // thermodynamic-pressure state of the checkpoint (constant in the supported open domain)
+  CK(cudaMemcpyAsync(ctx->pth, (const char*)checkpoint + sw * sizeof(R), sizeof(PthState),
+                     cudaMemcpyDeviceToDevice, ctx->st), "load P_th state");
+  const int other = 1 - ctx->cur;
+  const bool hi1 = ctx->cfg.omega_hi[0] == 1.0 && ctx->cfg.omega_hi[1] == 1.0 && ctx->cfg.omega_hi[2] == 1.0 &&
+                   ctx->cfg.omega_hi[3] == 1.0;
+  const int co = hi1 ? COLL_CUMULANT_FULL : COLL_CUMULANT;
   for (int k = 0; k < n; ++k) {
-    CK(enqueue_step(ctx, ctx->cur, false), "segment recompute");
-    ctx->cur ^= 1;
-    ++ctx->steps;
-    CopyList<R> l{};
+    R* sk = state_of(k);
+    const bool last = k + 1 == n;
+    R* sk1 = last ? nullptr : state_of(k + 1);
     if (th) {
-      R* slot = seg + (size_t)k * slot_w;
-      l.src[0] = (const R*)ctx->rho; l.dst[0] = slot + sw; l.n[0] = N;
-      l.src[1] = (const R*)ctx->lam; l.dst[1] = slot + sw + N; l.n[1] = N;
-      l.count = 2;
+      FDArgs<R> fdf = make_fd_args<R>(ctx, ctx->cur);
+      fdf.T = sk + 11 * N;
+      fdf.Y = sk + 12 * N;
+      fdf.u = sk + 9 * N;
+      fdf.T_out = last ? (R*)ctx->T[other] : sk1 + 11 * N;
+      fdf.Y_out = last ? (R*)ctx->Y[other] : sk1 + 12 * N;
+      fdf.rho_out = rho_of(k);
+      fdf.lam_out = rho_of(k) + N;
+      CK((launch_fd<2, R>(fdf, ctx->st, false)), "segment recompute (FD)");
     }
-    if (k + 1 < n) state_copy(l, seg + (size_t)(k + 1) * slot_w);
-    CK(launch_copy_list<R>(l, ctx->st), "segment snapshot");
+    if (!last) {
+      LBArgs<R> lbf = make_lb_args<R>(ctx, ctx->cur, false);
+      lbf.g_in = sk;
+      lbf.g_out = sk1;
+      lbf.u_in = sk + 9 * N;
+      lbf.u = sk1 + 9 * N;
+      if (th) {
+        lbf.rho = rho_of(k);
+        lbf.lam = rho_of(k) + N;
+        lbf.T = sk + 11 * N;
+      } else {
+        // isothermal: the step writes u at outlet cells only; carry the rest over
+        CK(cudaMemcpyAsync(sk1 + 9 * N, sk + 9 * N, 2 * N * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st),
+           "segment recompute (u)");
+      }
+      CK((launch_lb<2, R, R>(lbf, th ? 1 : 0, co, ctx->st)), "segment recompute (LB)");
+    }
   }
   CK(launch_zero_solid_pops<R>(ctx->geo, ctx->links, (R*)adj, ctx->st), "zero solid adjoint");
   const R* in = (const R*)adj;
   R* out = buf;
   for (int k = n - 1; k >= 0; --k) {
-    R* slot = seg + (size_t)k * slot_w;
-    LBArgs<R> lbf = make_lb_args<R>(ctx, 0, false);
-    lbf.g_in = slot;
-    lbf.u = slot + 9 * N;
-    FDArgs<R> fdf = make_fd_args<R>(ctx, 0);
-    fdf.u = slot + 9 * N;
+    R* sk = state_of(k);
+    LBArgs<R> lbf = make_lb_args<R>(ctx, ctx->cur, false);
+    lbf.g_in = sk;
+    lbf.u = sk + 9 * N;
+    lbf.u_in = lbf.u;
+    FDArgs<R> fdf = make_fd_args<R>(ctx, ctx->cur);
+    fdf.u = sk + 9 * N;
     if (th) {
-      lbf.T = slot + 11 * N;
-      lbf.rho = slot + sw;
-      lbf.lam = slot + sw + N;
-      fdf.T = slot + 11 * N;
-      fdf.Y = slot + 12 * N;
+      lbf.T = sk + 11 * N;
+      lbf.rho = rho_of(k);
+      lbf.lam = rho_of(k) + N;
+      fdf.T = sk + 11 * N;
+      fdf.Y = sk + 12 * N;
     }
     const AdjBuffers<R> b = adj_buffers<R>(ctx, scratch, in, out, grad_inlet);
     CK(launch_adjoint_step2d<R>(b, lbf, fdf, th, ctx->st), "adjoint kernels");

@@ -146,7 +146,8 @@ template <typename R> struct LBArgs {
   const R* lam;      // thermal: Lambda from the FD update (without the P_th term)
   const R* T;        // thermal: temperature at level n (viscosity law)
   const R* inlet_u;  // [D][ny*nz], low-x face
-  R* u;              // [D][N]: read at outlet cells (previous step), written as below
+  const R* u_in;     // [D][N]: velocity of the previous step, read at outlet cells
+  R* u;              // [D][N]: written as below (may alias u_in)
   int write_u;       // 1: write u of every cell; 0: outlet cells only
   R* ph_out;         // [N] or nullptr
   const PthState* pth;

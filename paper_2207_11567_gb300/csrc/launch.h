@@ -51,11 +51,6 @@ template <typename R> constexpr size_t adj_scratch_words(size_t N, int K) {
 template <typename R>
 cudaError_t launch_adjoint_step2d(const AdjBuffers<R>& b, const LBArgs<R>& lbf, const FDArgs<R>& fdf, bool thermal,
                                   cudaStream_t st);
-// copy up to 6 arrays of R in one launch (state snapshots of the reverse sweep)
-template <typename R> struct CopyList {
-  const R* src[6]; R* dst[6]; size_t n[6]; int count;
-};
-template <typename R> cudaError_t launch_copy_list(const CopyList<R>& l, cudaStream_t st);
 template <typename R> cudaError_t launch_zero_solid_pops(const Geo& g, const uint32_t* links, R* pops, cudaStream_t st);
 template <typename R>
 cudaError_t launch_initial_T_adjoint(const FDArgs<R>& fdf, const R* adj0, R* gradT, cudaStream_t st);

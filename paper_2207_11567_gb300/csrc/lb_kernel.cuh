@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
   // pressure outlet (anti-bounce-back at the half-way face, P_h = P_ref):
   // g_i = -g*_opp + 2 w_i (P_ref + rho (1.5 (c_i.u)^2 - 0.5 u^2)), u of the previous step
   if (outlet_cell) {
-    const R vx = a.u[r], vy = a.u[N + r], vz = (D == 3) ? a.u[2 * N + r] : R(0);
+    const R vx = a.u_in[r], vy = a.u_in[N + r], vz = (D == 3) ? a.u_in[2 * N + r] : R(0);
     const R vv = vx * vx + vy * vy + vz * vz;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
