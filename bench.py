@@ -185,7 +185,7 @@ def adjoint_bench(args):
     from paper_2207_11567_gb300 import AdjointProblem
     torch.cuda.set_device(0)
     wl = W.make("c5_adjoint_2d")
-    K, C = wl.steps, 100
+    K, C = (args.adj_steps or wl.steps), 100
     inlet0 = np.asarray(wl.inlet_u, dtype=np.float64).reshape(2, -1)
     T0 = np.asarray(wl.T, dtype=np.float64).reshape(-1)
 
@@ -276,6 +276,7 @@ def main():
                     help="benchmark configuration (default: the reactive swirl burner)")
     ap.add_argument("--no-fd-check", action="store_true", help="c5: skip the FP64 finite-difference check")
     ap.add_argument("--fd-dirs", type=int, default=16, help="c5: directions of the finite-difference check")
+    ap.add_argument("--adj-steps", type=int, default=0, help="c5: steps K (default: the workload's 2000)")
     args = ap.parse_args()
     if args.workload == "c5_adjoint_2d" and args.impl == "ours":
         adjoint_bench(args)
