@@ -299,8 +299,11 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
 
 // NK, NR > 0: species and reaction counts known at compile time (loops unroll exactly);
 // NK = NR = 0: counts read from the constants at run time.
+#ifndef HLBM_FD_MIN_BLOCKS
+#define HLBM_FD_MIN_BLOCKS 4  // FP32: resident blocks per SM the register budget is sized for
+#endif
 template <int D, typename R, int NK, int NR>
-__global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? 4 : 1) fd_step_kernel(const FDArgs<R> a) {
+__global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? HLBM_FD_MIN_BLOCKS : 1) fd_step_kernel(const FDArgs<R> a) {
   const FDConst<R>& c = a.c;
   const Geo& g = a.geo;
   const int x = blockIdx.x * FDShape<D>::X + threadIdx.x;

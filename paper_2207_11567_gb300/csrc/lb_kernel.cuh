@@ -164,11 +164,13 @@ __device__ __forceinline__ R delta_eq(const R* dx, const R* dy, const R* dz) {
   return -(ex * ky * kz + kx * ey * kz + kx * ky * ez + ex * ey * kz + ex * ky * ez + kx * ey * ez + ex * ey * ez);
 }
 
-template <int D, typename R, int J>
+// m[J] += sign * delta_eq for the moments whose order a + b + c lies in [LO, HI]
+template <int D, typename R, int J, int LO = 0, int HI = 6>
 __device__ __forceinline__ void add_delta_eq(R* m, const R* dx, const R* dy, const R* dz, const R sign) {
   if constexpr (J < Lat<D>::Q) {
-    m[J] += sign * delta_eq<D, J, R>(dx, dy, dz);
-    add_delta_eq<D, R, J + 1>(m, dx, dy, dz, sign);
+    constexpr int order = J % 3 + (J / 3) % 3 + J / 9;
+    if constexpr (order >= LO && order <= HI) m[J] += sign * delta_eq<D, J, R>(dx, dy, dz);
+    add_delta_eq<D, R, J + 1, LO, HI>(m, dx, dy, dz, sign);
   }
 }
 
@@ -310,8 +312,10 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
     Ssum += (R)wgt<D>(i) * q[i];
   }
   const R three_over_rho = R(3) * inv_rho;
+  // d_i = h_i / w_i - 1; the cumulant path works on w_i d_i (w_i folded into the factor)
 #pragma unroll
-  for (int i = 0; i < Q; ++i) q[i] = three_over_rho * (q[i] - Ssum);  // d_i
+  for (int i = 0; i < Q; ++i)
+    q[i] = (COLL == COLL_BGK ? three_over_rho : three_over_rho * (R)wgt<D>(i)) * (q[i] - Ssum);
 
   // ---------------------------------------------------------------- relaxation time
   R tau0;
@@ -328,8 +332,6 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
     // moments n of h - h_eq (h_eq: product-form equilibrium); see delta_eq
     const R dlx[3] = {R(0), -ux, ux * ux}, dly[3] = {R(0), -uy, uy * uy}, dlz[3] = {R(0), -uz, uz * uz};
 #pragma unroll
-    for (int i = 0; i < Q; ++i) q[i] *= (R)wgt<D>(i);
-#pragma unroll
     for (int j = 0; j < Q / 3; ++j) chim_fwd(q[3 * j], q[3 * j + 1], q[3 * j + 2], ux);
 #pragma unroll
     for (int kz = 0; kz < Q / 9; ++kz)
@@ -339,7 +341,11 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
 #pragma unroll
       for (int j = 0; j < 9; ++j) chim_fwd(q[j], q[j + 9], q[j + 18], uz);
     }
-    add_delta_eq<D, R, 0>(q, dlx, dly, dlz, R(-1));
+    // full relaxation of orders 3..6 reads only the second-order moments, and orders 0 and 1
+    // pass through unchanged: there the deviation is removed and restored for order 2 and
+    // restored for orders >= 2 only (the skipped terms cancel exactly in real arithmetic)
+    if constexpr (FULL) add_delta_eq<D, R, 0, 2, 2>(q, dlx, dly, dlz, R(-1));
+    else add_delta_eq<D, R, 0>(q, dlx, dly, dlz, R(-1));
     // Smagorinsky: deviatoric part of the second central moments (equilibrium is isotropic)
     R tau = tau0;
     if (a.smag_k > R(0)) {
@@ -358,7 +364,8 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
     const R om = R(1) / tau;
     if constexpr (D == 2) cumulant_relax2<FULL, R>(q, om, a.omega_b, a.om3, a.om4);
     else cumulant_relax3<FULL, R>(q, om, a.omega_b, a.om3, a.om4, a.om5, a.om6);
-    add_delta_eq<D, R, 0>(q, dlx, dly, dlz, R(1));
+    if constexpr (FULL) add_delta_eq<D, R, 0, 2, 6>(q, dlx, dly, dlz, R(1));
+    else add_delta_eq<D, R, 0>(q, dlx, dly, dlz, R(1));
     if constexpr (D == 3) {
 #pragma unroll
       for (int j = 0; j < 9; ++j) chim_bwd(q[j], q[j + 9], q[j + 18], uz);
@@ -369,9 +376,7 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
       for (int ax = 0; ax < 3; ++ax) chim_bwd(q[ax + 9 * kz], q[ax + 3 + 9 * kz], q[ax + 6 + 9 * kz], uy);
 #pragma unroll
     for (int j = 0; j < Q / 3; ++j) chim_bwd(q[3 * j], q[3 * j + 1], q[3 * j + 2], ux);
-    // back to d* = h*/w - 1
-#pragma unroll
-    for (int i = 0; i < Q; ++i) q[i] *= (R)(1.0 / wgt<D>(i));
+    // q now holds w_i d*_i; the 1 / w_i is folded into the store below
   } else {
     // single rate towards the polynomial equilibrium f^eq(1, u) of Eq. 4: E_i = f^eq_i / w_i - 1
     R tau = tau0;
@@ -418,7 +423,8 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
       const R e = cu + R(1.5) * cu * cu - R(0.5) * usq;
       half_xi = R(0.5) * (e * (cg - udg) + rl3);
     }
-    st_pop<S, R>(gout + i * Ni + r, rho3 * q[i] + Ssum + half_xi);
+    const R fac = COLL == COLL_BGK ? rho3 : rho3 * (R)(1.0 / wgt<D>(i));
+    st_pop<S, R>(gout + i * Ni + r, fac * q[i] + Ssum + half_xi);
   }
   if (a.write_u || outlet_cell) {
     a.u[r] = ux;
