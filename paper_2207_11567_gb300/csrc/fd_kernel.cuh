@@ -56,12 +56,20 @@ __device__ __forceinline__ float arrhenius(float ER_hi, float ER_lo, float T) {
 
 // x^y for x >= 0: FP32 as exp2(y log2 x) with the hardware log2 / exp2 (relative error a few
 // 1e-7, against ~50 instructions for powf); FP64 with pow.
+// Hardware reciprocal (PTX rcp.approx.ftz, relative error ~2^-23) for the WENO weights, whose
+// denominators lie in [1e-12, 1e14]: far from denormals and from overflow, so no range handling.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 template <typename R> __device__ __forceinline__ R powr(R x, R y);
 template <> __device__ __forceinline__ float powr<float>(float x, float y) { return exp2f(y * __log2f(x)); }
 template <> __device__ __forceinline__ double powr<double>(double x, double y) { return pow(x, y); }
 
 template <typename R> __device__ __forceinline__ R fdiv(R a, R b) { return a / b; }
-template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return a * rcp_approx(b); }
 
 template <typename R> __device__ __forceinline__ R weno3(R a, R b, R c, R eps) {
   const R q0 = R(-0.5) * a + R(1.5) * b;
