@@ -154,7 +154,8 @@ lbm_status lbm_get_fields(lbm_ctx* ctx, unsigned bits, double* dst, int dst_on_d
 lbm_status lbm_get_scalars(lbm_ctx* ctx, double out[4]);
 
 /* Per-cell link words (uint32, N): for a fluid cell bit i is set when direction i is a
- * bounce-back link (solid, wall or inlet source) and bit 31 is set; solid cells hold 0. */
+ * bounce-back link (solid, wall or inlet source) and bit 31 is set; bit 30 marks cells with
+ * interpolated bounce-back links (lbm_set_wall_fractions); solid cells hold 0. */
 lbm_status lbm_get_links(lbm_ctx* ctx, uint32_t* dst, int dst_on_device);
 
 /* Per-cell stencil words of the finite-difference update (uint32, N): for axis a and side s
@@ -163,6 +164,16 @@ lbm_status lbm_get_links(lbm_ctx* ctx, uint32_t* dst, int dst_on_device);
  * 1 zero-gradient copy of the distance-1 value, 2 inlet); bit 31 marks a fluid cell, solid cells
  * hold 0. Integer output, comparable bit for bit. */
 lbm_status lbm_get_stencil_words(lbm_ctx* ctx, uint32_t* dst, int dst_on_device);
+
+/* Curved or offset walls (the paper's curved-boundary treatment of the lattice Boltzmann solver,
+ * Section 1; formulas are a reading: linearly interpolated bounce-back). q: host array [Q][N]
+ * of doubles: for a fluid cell r and pull direction i whose source r - c_i is solid or outside
+ * a wall face, the fraction in (0, 1] of the link r -> r - c_i at which the wall lies; other
+ * entries are ignored, and q = 1/2 is half-way bounce-back (the default). A link with q < 1/2
+ * whose node r + c_i is not fluid, and links of the inlet and outlet faces, stay half-way.
+ * NULL clears the data. Must follow lbm_set_geometry (which clears it); synchronises the
+ * stream. The finite-difference walls stay zero-gradient. */
+lbm_status lbm_set_wall_fractions(lbm_ctx* ctx, const double* q);
 
 /* Checkpoint: bytes of device memory needed, save into / load from caller-owned device memory. */
 size_t lbm_state_bytes(const lbm_ctx* ctx);

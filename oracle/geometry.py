@@ -117,12 +117,32 @@ def lb_links(lat, grid):
     return code, src
 
 
-def pack_links(code, grid):
-    """Packed link words (int64 holding the uint32 bit pattern)."""
+def wall_links(lat, grid, code, src, qwall):
+    """Interpolated bounce-back data: wall fraction q [Q, N] of each code-1 link (0.5 elsewhere and
+    where no fraction is given) and the index of r + c_i when that node is fluid (else -1). The
+    node r + c_i is the pull source of the opposite direction."""
+    q = torch.as_tensor(qwall, dtype=torch.float64).reshape(lat.Q, grid.N).clone()
+    bb = code == 1
+    q = torch.where(bb & (q > 0) & (q <= 1), q, torch.full_like(q, 0.5))
+    far = torch.full((lat.Q, grid.N), -1, dtype=torch.int64)
+    for i in range(lat.Q):
+        o = int(lat.opp[i])
+        ok = code[o] == 0  # r + c_i = r - c_o is the pull source of direction o, a fluid node
+        far[i] = torch.where(ok, src[o], torch.full_like(src[o], -1))
+    return {"q": q, "far": far}
+
+
+def pack_links(code, grid, wall=None):
+    """Packed link words (int64 holding the uint32 bit pattern); bit 30 marks cells with an
+    interpolated bounce-back link (a code-1 link whose effective fraction is not 1/2)."""
     Q = code.shape[0]
     word = torch.zeros(grid.N, dtype=torch.int64)
     for i in range(Q):
         word |= (code[i] != 0).to(torch.int64) << i
+    if wall is not None:
+        eff = torch.where((wall["q"] < 0.5) & (wall["far"] < 0), torch.full_like(wall["q"], 0.5), wall["q"])
+        interp = ((code == 1) & (eff != 0.5)).any(0)
+        word |= interp.to(torch.int64) << 30
     word |= grid.fluid.to(torch.int64) << 31
     word[~grid.fluid] = 0
     return word

@@ -58,7 +58,7 @@ def moments(lat, g, rho, lam):
     return P_h, u
 
 
-def stream(g_post, code, src, lat, rho, uin_at_r, u_prev, P_out):
+def stream(g_post, code, src, lat, rho, uin_at_r, u_prev, P_out, wall=None):
     """Pull streaming with boundary links (Eq. 1 read as pull).
 
     g_post [Q, N] are the post-collision populations of the previous step. uin_at_r [dim, N]
@@ -66,6 +66,8 @@ def stream(g_post, code, src, lat, rho, uin_at_r, u_prev, P_out):
     bounce-back g_i = g*_opp + 2 w_i rho c_i.u_w, the first-order part of Eq. 6 doubled).
     Code 3 (outlet): anti-bounce-back g_i = -g*_opp + 2 w_i (P_out + rho (1.5 (c_i.u)^2 - 0.5 u^2)),
     twice the even part of Eq. 6 at the outlet pressure, with u the previous-step velocity.
+    wall (optional): {"q": [Q, N] wall fractions, "far": [Q, N] index of r + c_i or -1} for
+    interpolated bounce-back on code-1 links (see ``interp_bounce_back``).
     """
     Q = lat.Q
     g = torch.empty_like(g_post)
@@ -76,9 +78,26 @@ def stream(g_post, code, src, lat, rho, uin_at_r, u_prev, P_out):
         inlet_term = 2.0 * lat.w[i] * rho * (lat.c[i] @ uin_at_r)
         cu = lat.c[i] @ u_prev
         abb = -bb + 2.0 * lat.w[i] * (P_out + rho * (1.5 * cu * cu - 0.5 * usq))
-        g[i] = torch.where(code[i] == 0, pulled, torch.where(code[i] == 1, bb,
+        wbb = bb if wall is None else interp_bounce_back(g_post, lat, i, wall["q"][i], wall["far"][i])
+        g[i] = torch.where(code[i] == 0, pulled, torch.where(code[i] == 1, wbb,
                            torch.where(code[i] == 2, bb + inlet_term, abb)))
     return g
+
+
+def interp_bounce_back(g_post, lat, i, q, far):
+    """Linearly interpolated bounce-back (the curved-wall treatment; the paper names it without
+    formulas, reading c21) for the population i entering a fluid node r whose link r - c_i crosses
+    a wall at the fraction q of the link from r, o = opposite of i:
+        q <  1/2:  g_i(r) = 2q g*_o(r) + (1 - 2q) g*_o(r + c_i)
+        q >= 1/2:  g_i(r) = g*_o(r) / (2q) + (2q - 1) / (2q) g*_i(r)
+    q = 1/2 is half-way bounce-back. Where r + c_i is not a fluid node (far < 0) a link with
+    q < 1/2 falls back to half-way bounce-back."""
+    o = lat.opp[i]
+    own_o, own_i = g_post[o], g_post[i]
+    far_o = g_post[o][far.clamp(min=0)]
+    near = 2.0 * q * own_o + (1.0 - 2.0 * q) * far_o
+    away = own_o / (2.0 * q) + (2.0 * q - 1.0) / (2.0 * q) * own_i
+    return torch.where(q < 0.5, torch.where(far >= 0, near, own_o), away)
 
 
 def tau_smagorinsky(lat, h, u, tau0, cs_smag):

@@ -33,7 +33,7 @@ class Oracle:
     oracle is the error floor that storage precision alone imposes.
     """
 
-    def __init__(self, cfg, mask, inlet_u=None, store_round=None):
+    def __init__(self, cfg, mask, inlet_u=None, store_round=None, qwall=None):
         self.cfg = cfg
         self.store_round = store_round
         self.p = Params(cfg)
@@ -42,6 +42,7 @@ class Oracle:
         self.grid = geo.Grid(cfg, mask)
         self.code, self.src = geo.lb_links(self.lat, self.grid)
         self.nb = geo.FDNeighbours(self.grid)
+        self.wall = None if qwall is None else geo.wall_links(self.lat, self.grid, self.code, self.src, qwall)
         d = cfg["dim"]
         ny = cfg["ny"]
         nz = cfg["nz"] if d == 3 else 1
@@ -54,7 +55,7 @@ class Oracle:
         self.at_outlet = g.fluid & (g.coord[0] == g.shape[0] - 1) & torch.tensor(g.bc[0][1] == geo.OUTLET)
 
     def links_packed(self):
-        return geo.pack_links(self.code, self.grid)
+        return geo.pack_links(self.code, self.grid, self.wall)
 
     def stencil_words_packed(self):
         return geo.pack_stencil_words(self.grid, self.nb)
@@ -141,7 +142,8 @@ class Oracle:
             lam = torch.zeros(N, dtype=torch.float64)
             grad = torch.zeros(p.dim, N, dtype=torch.float64)
             tau0 = torch.full((N,), p.nu_lat / CS2 + 0.5, dtype=torch.float64)
-        g = lb.stream(st["g"], self.code, self.src, lat, rho, self.uin_r, st["u"], self.cfg.get("P_ref", 0.0))
+        g = lb.stream(st["g"], self.code, self.src, lat, rho, self.uin_r, st["u"], self.cfg.get("P_ref", 0.0),
+                      self.wall)
         P_h, u = lb.moments(lat, g, rho, lam)
         xi = lb.source_xi(lat, rho, u, grad, lam)
         gs = lb.collide(lat, self.cs, g, rho, u, xi, tau0, p.as_lb())

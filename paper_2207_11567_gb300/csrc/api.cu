@@ -40,6 +40,9 @@ struct lbm_ctx {
   void* ph = nullptr;
   void* Floc = nullptr;
   uint32_t* links = nullptr;
+  int* wall_idx = nullptr;     // interpolated bounce-back table (lbm_set_wall_fractions)
+  void* wall_q = nullptr;
+  size_t wall_rows_cap = 0, n_wall = 0;
   uint32_t* sword = nullptr;
   uint8_t* mask = nullptr;
   void* inlet_u = nullptr;
@@ -172,6 +175,9 @@ template <typename R> LBArgs<R> make_lb_args(lbm_ctx* c, int cur, bool want_out)
   a.g_in = c->g[cur];
   a.g_out = c->g[1 - cur];
   a.links = c->links;
+  a.wall_idx = c->wall_idx;
+  a.wall_q = (const R*)c->wall_q;
+  a.walls = c->n_wall > 0 ? 1 : 0;
   a.rho = (const R*)c->rho;
   a.lam = (const R*)c->lam;
   a.T = (const R*)c->T[cur];
@@ -510,6 +516,7 @@ lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* mask, const double* inl
   for (size_t i = 0; i < N; ++i) nfl += hm[i] == 0;
   ctx->n_fluid = nfl;
   ctx->have_geo = true;
+  ctx->n_wall = 0;  // the rebuilt link words carry no interpolated walls
   drop_graphs(ctx);
   return LBM_OK;
 }
@@ -990,14 +997,76 @@ template <typename R> lbm_status initial_T_adjoint_impl(lbm_ctx* ctx, const void
   return LBM_OK;
 }
 
+template <typename R> lbm_status set_wall_impl(lbm_ctx* ctx, const double* q) {
+  const size_t N = ctx->N;
+  const int Q = ctx->Q, D = ctx->D;
+  const Geo& g = ctx->geo;
+  std::vector<uint32_t> lw(N);
+  CK(cudaMemcpyAsync(lw.data(), ctx->links, N * 4, cudaMemcpyDeviceToHost, ctx->st), "copy links");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  for (size_t r = 0; r < N; ++r) lw[r] &= ~LINK_WALL;
+  std::vector<int> idx;
+  std::vector<R> rows;
+  std::vector<int> cells;
+  if (q) {
+    for (size_t r = 0; r < N; ++r) {
+      const uint32_t w = lw[r];
+      if (!(w >> 31) || !(w & ((1u << Q) - 1u))) continue;
+      const int x = (int)(r % g.nx);
+      bool any = false;
+      R row[27];
+      for (int i = 0; i < Q; ++i) {
+        R f = R(0.5);
+        if ((w >> i) & 1u) {
+          const bool inlet = x == 0 && g.bc_lo[0] == BC_INLET && cx(i) == 1;
+          const bool outlet = x == g.nx - 1 && g.bc_hi[0] == BC_OUTLET && cx(i) == -1;
+          const double v = q[(size_t)i * N + r];
+          if (!inlet && !outlet && v > 0.0 && v <= 1.0) {
+            f = (R)v;
+            // f < 1/2 needs r + c_i as a fluid pull source of the opposite direction
+            if (f < R(0.5) && ((w >> (Q - 1 - i)) & 1u)) f = R(0.5);
+          }
+        }
+        row[i] = f;
+        any = any || f != R(0.5);
+      }
+      if (!any) continue;
+      cells.push_back((int)r);
+      for (int i = 0; i < Q; ++i) rows.push_back(row[i]);
+    }
+  }
+  (void)D;
+  const size_t n = cells.size();
+  if (n > 0) {
+    if (!ctx->wall_idx && !(ctx->wall_idx = (int*)dalloc(ctx, N * sizeof(int))))
+      return fail(ctx, LBM_ERR_ALLOC, "wall table allocation failed");
+    if (n > ctx->wall_rows_cap) {
+      if (!(ctx->wall_q = dalloc(ctx, n * Q * sizeof(R)))) return fail(ctx, LBM_ERR_ALLOC, "wall table allocation failed");
+      ctx->wall_rows_cap = n;
+    }
+    idx.assign(N, -1);
+    for (size_t k = 0; k < n; ++k) {
+      idx[cells[k]] = (int)k;
+      lw[cells[k]] |= LINK_WALL;
+    }
+    CK(cudaMemcpyAsync(ctx->wall_idx, idx.data(), N * sizeof(int), cudaMemcpyHostToDevice, ctx->st), "copy wall index");
+    CK(cudaMemcpyAsync(ctx->wall_q, rows.data(), n * Q * sizeof(R), cudaMemcpyHostToDevice, ctx->st), "copy wall table");
+  }
+  CK(cudaMemcpyAsync(ctx->links, lw.data(), N * 4, cudaMemcpyHostToDevice, ctx->st), "copy links");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  ctx->n_wall = n;
+  drop_graphs(ctx);
+  return LBM_OK;
+}
+
 lbm_status adjoint_supported(lbm_ctx* ctx) {
   const lbm_config& c = ctx->cfg;
   const bool hi1 = c.omega_hi[0] == 1.0 && c.omega_hi[1] == 1.0;
   if (c.dim != 2 || c.storage == LBM_STORE_F16 || c.collision != LBM_COLL_CUMULANT || !hi1 || c.closed_domain ||
-      c.flame_sensor)
+      c.flame_sensor || ctx->n_wall > 0)
     return fail(ctx, LBM_ERR_UNSUPPORTED,
                 "adjoint: 2-D, FP32/FP64 storage, cumulant collision with default higher-order rates, open domain, "
-                "no flame sensor");
+                "no flame sensor, half-way walls");
   return LBM_OK;
 }
 }  // namespace
@@ -1046,6 +1115,13 @@ lbm_status lbm_initial_T_adjoint(lbm_ctx* ctx, const void* state0, const void* a
   CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
   return ctx->f64 ? initial_T_adjoint_impl<double>(ctx, state0, adj0, grad_T0)
                   : initial_T_adjoint_impl<float>(ctx, state0, adj0, grad_T0);
+}
+
+lbm_status lbm_set_wall_fractions(lbm_ctx* ctx, const double* q) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (!ctx->have_geo) return fail(ctx, LBM_ERR_STATE, "set_geometry must come first");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  return ctx->f64 ? set_wall_impl<double>(ctx, q) : set_wall_impl<float>(ctx, q);
 }
 
 lbm_status lbm_use_graphs(lbm_ctx* ctx, int enable) {

@@ -137,11 +137,17 @@ constexpr int LB_BLOCK = 128;
 #define LB_MIN_BLOCKS 6
 #endif
 
+// link word bit 30: the cell has interpolated bounce-back links (entry wall_idx[r] of the table)
+constexpr uint32_t LINK_WALL = 1u << 30;
+
 template <typename R> struct LBArgs {
   Geo geo;
   const void* g_in;
   void* g_out;
   const uint32_t* links;
+  const int* wall_idx;  // [N] table row of cells flagged LINK_WALL (read for those only)
+  const R* wall_q;      // [rows][Q] wall fraction per pull direction (0.5: half-way)
+  int walls;            // 1: some cells carry interpolated links
   const R* rho;      // thermal: density at level n (lattice units)
   const R* lam;      // thermal: Lambda from the FD update (without the P_th term)
   const R* T;        // thermal: temperature at level n (viscosity law)

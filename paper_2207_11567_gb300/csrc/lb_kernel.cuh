@@ -174,7 +174,9 @@ __device__ __forceinline__ void add_delta_eq(R* m, const R* dx, const R* dy, con
   }
 }
 
-template <int D, typename S, typename R, bool THERMAL, int COLL>
+// WALLS: the interpolated bounce-back fix-up is compiled in (launched only for contexts that
+// have wall fractions, so that it costs the other runs no registers)
+template <int D, typename S, typename R, bool THERMAL, int COLL, bool WALLS>
 __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const LBArgs<R> a) {
   constexpr int Q = Lat<D>::Q;
   const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz;
@@ -239,6 +241,34 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
   R q[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) q[i] = cvt_pop<S, R>(raw[i]);
+  // interpolated bounce-back (curved or offset walls) on flagged cells: for a link whose wall
+  // lies at the fraction f of r -> r - c_i, with o the opposite direction and q_i = g*_o(r) above,
+  //   f <  1/2:  g_i = 2 f g*_o(r) + (1 - 2 f) g*_o(r + c_i) = g*_o(r + c_i) + 2 f (g*_o(r) - g*_o(r + c_i))
+  //   f >= 1/2:  g_i = g*_o(r) / (2 f) + (2 f - 1) / (2 f) g*_i(r) = g*_i(r) + (g*_o(r) - g*_i(r)) / (2 f)
+  // (affine with weights summing to 1, so it holds for the shifted stored form as well; the
+  // right-hand forms round once, on a difference of neighbouring populations)
+  if (WALLS && (lw & LINK_WALL)) {
+    const R* __restrict__ wq = a.wall_q + (size_t)__ldg(a.wall_idx + r) * Q;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if ((lw >> i) & 1u) {
+        const R f = wq[i];
+        if (f != R(0.5)) {
+          const int ci = cx(i), cj = cy(i), ck = (D == 3) ? cz(i) : 0;
+          if (f < R(0.5)) {
+            // r + c_i: the pull source of the opposite direction (a fluid node, checked at set-up)
+            const int s = r + (ci == -1 ? oxm : (ci == 1 ? oxp : 0)) + (cj == -1 ? oym : (cj == 1 ? oyp : 0)) +
+                          (ck == -1 ? ozm : (ck == 1 ? ozp : 0));
+            const R far_o = cvt_pop<S, R>(ld_raw<S>(gin + (Q - 1 - i) * Ni + s));
+            q[i] = far_o + R(2) * f * (q[i] - far_o);  // one rounding on a small difference
+          } else {
+            const R own_i = cvt_pop<S, R>(ld_raw<S>(gin + i * Ni + r));
+            q[i] = own_i + (q[i] - own_i) / (R(2) * f);
+          }
+        }
+      }
+    }
+  }
   // moving-wall term of the low-x inlet: g_i += 2 w_i rho (c_i . u_w)
   if (x == 0 && a.geo.bc_lo[0] == BC_INLET) {
     const int f = y + ny * z;
@@ -438,7 +468,11 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
 template <int D, typename S, typename R>
 cudaError_t launch_lb(const LBArgs<R>& a, int thermal, int coll, cudaStream_t st) {
   const dim3 grid((a.geo.nx + LB_BLOCK - 1) / LB_BLOCK, a.geo.ny, a.geo.nz);
-#define LB_LAUNCH(TH, CO) lb_step_kernel<D, S, R, TH, CO><<<grid, LB_BLOCK, 0, st>>>(a)
+#define LB_LAUNCH(TH, CO)                                                 \
+  do {                                                                    \
+    if (a.walls) lb_step_kernel<D, S, R, TH, CO, true><<<grid, LB_BLOCK, 0, st>>>(a); \
+    else lb_step_kernel<D, S, R, TH, CO, false><<<grid, LB_BLOCK, 0, st>>>(a);        \
+  } while (0)
   if (thermal) {
     if (coll == COLL_CUMULANT_FULL) LB_LAUNCH(true, COLL_CUMULANT_FULL);
     else if (coll == COLL_CUMULANT) LB_LAUNCH(true, COLL_CUMULANT);

@@ -91,6 +91,14 @@ class Solver:
             _check(self.ctx, L.lib.lbm_set_geometry(self.ctx, m.ctypes.data_as(C.c_void_p), ptr, 0))
         del keep
 
+    def set_wall_fractions(self, q):
+        """Interpolated bounce-back: q [Q][N] wall fraction per bounce-back link (0.5 half-way),
+        or None to clear (lbm_set_wall_fractions). Call after set_geometry."""
+        keep, ptr = (None, None) if q is None else _as_c_double(q)
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_set_wall_fractions(self.ctx, ptr))
+        del keep
+
     def set_fields(self, T=None, Y=None, u=None, P_h=None, g_pert=None):
         keep = []
 
@@ -250,5 +258,7 @@ class Solver:
 def from_workload(wl, **kw):
     """Solver initialised with a ``workloads.Workload``'s geometry and fields."""
     s = Solver(wl.cfg, wl.mask, wl.inlet_u, **kw)
+    if getattr(wl, "qwall", None) is not None:
+        s.set_wall_fractions(wl.qwall)
     s.set_fields(T=wl.T, Y=wl.Y, u=wl.u, P_h=wl.P_h, g_pert=wl.g_pert)
     return s

@@ -402,3 +402,37 @@ def test_species_sum_and_conservation():
     s0 = st["Y"].sum(1)
     st = o.run(st, 20)
     assert (st["Y"].sum(1) - s0).abs().max().item() < 1e-12
+
+
+def test_interpolated_bounce_back_at_half_is_half_way():
+    """Wall fraction 1/2 on every link reduces the interpolated rule to half-way bounce-back
+    exactly (reading c21): identical oracle states with and without the wall data."""
+    wl = W.generate.chamber_2d(nx=40, ny=20, inlet=True, storage="f64", seed=4, n_rows=1, per_row=2)
+    q = np.full((9, wl.N), 0.5)
+    a = Oracle(wl.cfg, wl.mask, wl.inlet_u)
+    b = Oracle(wl.cfg, wl.mask, wl.inlet_u, qwall=q)
+    sa = a.run(a.init_state(T=wl.T, Y=wl.Y, u=wl.u, P_h=wl.P_h), 5)
+    sb = b.run(b.init_state(T=wl.T, Y=wl.Y, u=wl.u, P_h=wl.P_h), 5)
+    for k in ("g", "u", "T", "Y"):
+        assert torch.equal(sa[k], sb[k]), k
+
+
+@pytest.mark.parametrize("q", [0.2, 0.8])
+def test_poiseuille_between_offset_walls(q):
+    """Plane Poiseuille flow with the walls at the fraction q of the boundary links (y = 0.5 - q
+    and H - 0.5 + q): with interpolated bounce-back the mid-channel profile converges to the
+    parabola of that width at second order; half-way bounce-back on the same grid keeps an error
+    of order |q - 1/2| / H (its walls sit at y = 0 and H)."""
+    errs, errs_hw = [], []
+    for H in (8, 16):
+        wl = W.generate.channel_2d(H=H, nx=4 * H, q=q, U=0.01, tau=1.0)
+        nu = wl.cfg["nu_ref"]
+        steps = int(2.0 * H * H / nu)
+        prof = wl.info["profile"]
+        for qw, out in ((wl.qwall, errs), (None, errs_hw)):
+            o = Oracle(wl.cfg, wl.mask, wl.inlet_u, qwall=qw)
+            st = o.run(o.init_state(u=wl.u, P_h=wl.P_h), steps)
+            mid = st["u"][0].numpy().reshape(H, 4 * H)[:, 2 * H]
+            out.append(np.abs(mid - prof).max() / 0.01)
+    assert errs[1] < 0.01 and errs[0] / errs[1] > 3.0, errs
+    assert errs_hw[1] > 5.0 * errs[1], (errs, errs_hw)

@@ -29,6 +29,7 @@ class Workload:
     T: np.ndarray = None
     Y: np.ndarray = None
     g_pert: np.ndarray = None
+    qwall: np.ndarray = None  # [Q][N] wall fraction of bounce-back links (interpolated walls)
     steps: int = 0
     info: dict = field(default_factory=dict)
 
@@ -254,6 +255,111 @@ def box(dim, n, storage="f64", collision="cumulant", tau=0.8, seed=0, pert=0.0, 
     if pert:
         wl.g_pert = perturbation(rng, 3 ** dim, N, pert)
     return wl
+
+
+# ------------------------------------------------------------------- curved/offset walls
+_D2 = [(cx, cy) for cy in (-1, 0, 1) for cx in (-1, 0, 1)]  # D2Q9 order of the library (x fastest)
+
+
+def channel_2d(H=16, nx=64, q=0.5, U=0.01, tau=0.8, collision="bgk", storage="f64"):
+    """Plane channel, velocity inlet (low x), pressure outlet (high x), walls in y placed at the
+    fraction q of the boundary links (walls at y = 0.5 - q and y = H - 0.5 + q in cell units,
+    cell centres at j + 0.5): the fully developed Poiseuille parabola of that width as inlet
+    profile and initial state (pressure gradient included)."""
+    cfg = _base_cfg(2, nx, H, 1, storage, collision)
+    nu = (tau - 0.5) / 3.0
+    cfg.update({"bc": {"x": ("inlet", "outlet"), "y": ("wall", "wall")}, "dx": 1.0, "dt": 1.0, "nu_ref": nu})
+    lo, hi = 0.5 - q, H - 0.5 + q
+    Wd = hi - lo
+    yy = np.arange(H) + 0.5
+    prof = 4.0 * U * (yy - lo) * (hi - yy) / Wd ** 2
+    N = nx * H
+    x, y, _ = _coords(nx, H, 1)
+    u = np.zeros((2, N))
+    u[0] = prof[y]
+    P = 8.0 * nu * U / Wd ** 2 * (nx - 0.5 - x)
+    inlet = np.zeros((2, H))
+    inlet[0] = prof
+    qw = np.zeros((9, N))
+    for i, (cx, cy) in enumerate(_D2):
+        # pull direction i: the link r - c_i leaves through the low wall when cy = +1 at y = 0
+        qw[i, (y == 0) & (cy == 1)] = q
+        qw[i, (y == H - 1) & (cy == -1)] = q
+    return Workload("channel_2d", cfg, np.zeros(N, np.uint8), inlet, u, P, qwall=qw,
+                    info={"profile": prof, "walls": (lo, hi)})
+
+
+def cylinder_2d(nx=96, ny=48, radius=7.3, center=None, U=0.02, tau=0.6, collision="cumulant", storage="f32",
+                seed=0):
+    """Channel with a circular cylinder: solid cells are those whose centre lies inside the
+    circle; every bounce-back link toward the cylinder gets the exact fraction at which the
+    segment from the fluid node to its solid neighbour enters the circle. Walls in y half-way,
+    parabolic inlet, pressure outlet; a seeded offset of the centre breaks the symmetry."""
+    rng = np.random.default_rng(seed)
+    cfg = _base_cfg(2, nx, ny, 1, storage, collision)
+    nu = (tau - 0.5) / 3.0
+    cfg.update({"bc": {"x": ("inlet", "outlet"), "y": ("wall", "wall")}, "dx": 1.0, "dt": 1.0, "nu_ref": nu,
+                "smag_cs": 0.17})
+    if center is None:
+        center = (nx * 0.3 + rng.uniform(-0.5, 0.5), ny * 0.5 + rng.uniform(-0.5, 0.5))
+    xc, yc = center
+    N = nx * ny
+    x, y, _ = _coords(nx, ny, 1)
+    px, py = x + 0.5, y + 0.5
+    solid = (px - xc) ** 2 + (py - yc) ** 2 < radius ** 2
+    mask = solid.astype(np.uint8)
+    qw = np.zeros((9, N))
+    for i, (cx, cy) in enumerate(_D2):
+        if cx == 0 and cy == 0:
+            continue
+        # the link from r to r - c_i; solve |p - t c - center| = R for the entering t in (0, 1]
+        sx, sy = x - cx, y - cy
+        inside = (sx >= 0) & (sx < nx) & (sy >= 0) & (sy < ny)
+        nb_solid = np.zeros(N, bool)
+        nb_solid[inside] = solid[(sy * nx + sx)[inside]]
+        sel = (~solid) & nb_solid
+        dx_, dy_ = px - xc, py - yc
+        a = cx * cx + cy * cy
+        b = -2.0 * (dx_ * cx + dy_ * cy)
+        c = dx_ * dx_ + dy_ * dy_ - radius ** 2
+        disc = np.maximum(b * b - 4 * a * c, 0.0)
+        t = (-b - np.sqrt(disc)) / (2 * a)
+        qw[i, sel] = np.clip(t[sel], 1e-3, 1.0)
+    yy = np.arange(ny) + 0.5
+    prof = 4.0 * U * yy * (ny - yy) / ny ** 2
+    inlet = np.zeros((2, ny))
+    inlet[0] = prof
+    u = np.zeros((2, N))
+    u[0] = np.where(solid, 0.0, prof[y])
+    return Workload("cylinder_2d", cfg, mask, inlet, u, np.zeros(N), qwall=qw, steps=2000,
+                    info={"center": center, "radius": radius})
+
+
+def duct_3d(nx=32, ny=12, nz=8, q=0.3, U=0.01, tau=0.8, collision="cumulant", storage="f64"):
+    """3-D duct: velocity inlet / pressure outlet in x, walls in y at the fraction q of the
+    boundary links (as channel_2d), periodic in z; plane Poiseuille initial state."""
+    cfg = _base_cfg(3, nx, ny, nz, storage, collision)
+    nu = (tau - 0.5) / 3.0
+    cfg.update({"bc": {"x": ("inlet", "outlet"), "y": ("wall", "wall"), "z": ("periodic", "periodic")},
+                "dx": 1.0, "dt": 1.0, "nu_ref": nu})
+    lo, hi = 0.5 - q, ny - 0.5 + q
+    Wd = hi - lo
+    yy = np.arange(ny) + 0.5
+    prof = 4.0 * U * (yy - lo) * (hi - yy) / Wd ** 2
+    N = nx * ny * nz
+    x, y, z = _coords(nx, ny, nz)
+    u = np.zeros((3, N))
+    u[0] = prof[y]
+    P = 8.0 * nu * U / Wd ** 2 * (nx - 0.5 - x)
+    inlet = np.zeros((3, ny * nz))
+    inlet[0] = np.tile(prof, nz)
+    qw = np.zeros((27, N))
+    for i in range(27):
+        cy = (i // 3) % 3 - 1
+        qw[i, (y == 0) & (cy == 1)] = q
+        qw[i, (y == ny - 1) & (cy == -1)] = q
+    return Workload("duct_3d", cfg, np.zeros(N, np.uint8), inlet, u, P, qwall=qw,
+                    info={"profile": prof, "walls": (lo, hi)})
 
 
 _NAMED = {
