@@ -333,6 +333,8 @@ def main():
     ap.add_argument("--no-fd-check", action="store_true", help="c5: skip the FP64 finite-difference check")
     ap.add_argument("--fd-dirs", type=int, default=16, help="c5: directions of the finite-difference check")
     ap.add_argument("--adj-steps", type=int, default=0, help="c5: steps K (default: the workload's 2000)")
+    ap.add_argument("--curved", action="store_true",
+                    help="c3/c4: interpolated bounce-back on the injector cylinders and the exhaust cone")
     args = ap.parse_args()
     if args.workload == "c5_adjoint_2d" and args.impl == "ours":
         adjoint_bench(args)
@@ -369,7 +371,12 @@ def main():
 
     def make():
         if args.case == "mid":
-            return W.generate.swirl_3d(192, 96, 96, reactive=args.workload != "c3_swirl_cold_3d", seed=0)
+            return W.generate.swirl_3d(192, 96, 96, reactive=args.workload != "c3_swirl_cold_3d", seed=0,
+                                       curved=args.curved)
+        if args.curved:
+            size = (384, 192, 192) if args.workload == "c4_swirl_reactive_3d" else (256, 128, 128)
+            return W.generate.swirl_3d(*size, reactive=args.workload == "c4_swirl_reactive_3d", seed=0,
+                                       curved=True)
         return W.make(args.workload)
 
     if args.only:
@@ -418,7 +425,7 @@ def main():
                    "reactions": len(wl.cfg.get("reactions", [])) if wl.cfg.get("thermal") else 0,
                    "thicken_F": wl.cfg.get("thicken_F"), "flame_sensor": wl.cfg.get("flame_sensor"),
                    "closed_domain": wl.cfg.get("closed_domain"), "storage": "f32",
-                   "parallelism": f"replicas{world}",
+                   "parallelism": f"replicas{world}", "walls": "interpolated" if args.curved else "half-way",
                    "l2": f"state {wl.N * (27 if wl.cfg['dim'] == 3 else 9) * 8 / 1e9:.2f} GB of populations > L2, no flush needed"},
         "e2e": {"value": N * args.steps / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps,

@@ -175,6 +175,12 @@ lbm_status lbm_get_stencil_words(lbm_ctx* ctx, uint32_t* dst, int dst_on_device)
  * stream. The finite-difference walls stay zero-gradient. */
 lbm_status lbm_set_wall_fractions(lbm_ctx* ctx, const double* q);
 
+/* The same as a list of n_links links (host arrays): cell index r, pull direction i and the wall
+ * fraction q of the link r -> r - c_i. Entries that are not bounce-back links of fluid cells, or
+ * with q outside (0, 1], are ignored; n_links = 0 clears the data. For large grids, where a dense
+ * [Q][N] array would not fit in host memory. */
+lbm_status lbm_set_wall_links(lbm_ctx* ctx, long long n_links, const int* cell, const int* dir, const double* q);
+
 /* Checkpoint: bytes of device memory needed, save into / load from caller-owned device memory. */
 size_t lbm_state_bytes(const lbm_ctx* ctx);
 lbm_status lbm_save_state(lbm_ctx* ctx, void* dst_device);

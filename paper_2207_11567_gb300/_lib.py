@@ -84,6 +84,7 @@ def _load():
         "lbm_initial_T_adjoint": (C.c_int, [P, P, P, P]),
         "lbm_adjoint_segment": (C.c_int, [P, P, C.c_int, P, P]),
         "lbm_set_wall_fractions": (C.c_int, [P, P]),
+        "lbm_set_wall_links": (C.c_int, [P, C.c_longlong, P, P, P]),
         "lbm_pth_integral_noalloc": (C.c_int, [P, P, P, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_double,
                                                C.c_double, P, P, C.c_char_p, C.c_size_t]),
     }
@@ -100,7 +101,8 @@ EXPORTED = ("lbm_init", "lbm_destroy", "lbm_last_error", "lbm_set_geometry", "lb
             "lbm_state_bytes",
             "lbm_save_state", "lbm_load_state", "lbm_profile", "lbm_kernel_times", "lbm_kernel_bytes",
             "lbm_use_graphs", "lbm_pth_integral_noalloc", "lbm_adjoint_step", "lbm_fuel_objective",
-            "lbm_initial_T_adjoint", "lbm_adjoint_segment", "lbm_set_wall_fractions")
+            "lbm_initial_T_adjoint", "lbm_adjoint_segment", "lbm_set_wall_fractions",
+            "lbm_set_wall_links")
 
 
 class HLBMError(RuntimeError):

@@ -40,7 +40,7 @@ struct lbm_ctx {
   void* ph = nullptr;
   void* Floc = nullptr;
   uint32_t* links = nullptr;
-  int* wall_idx = nullptr;     // interpolated bounce-back table (lbm_set_wall_fractions)
+  int* wall_cells = nullptr;   // interpolated bounce-back list and table (lbm_set_wall_links)
   void* wall_q = nullptr;
   size_t wall_rows_cap = 0, n_wall = 0;
   uint32_t* sword = nullptr;
@@ -175,9 +175,9 @@ template <typename R> LBArgs<R> make_lb_args(lbm_ctx* c, int cur, bool want_out)
   a.g_in = c->g[cur];
   a.g_out = c->g[1 - cur];
   a.links = c->links;
-  a.wall_idx = c->wall_idx;
+  a.wall_cells = c->wall_cells;
   a.wall_q = (const R*)c->wall_q;
-  a.walls = c->n_wall > 0 ? 1 : 0;
+  a.n_wall = (int)c->n_wall;
   a.rho = (const R*)c->rho;
   a.lam = (const R*)c->lam;
   a.T = (const R*)c->T[cur];
@@ -997,59 +997,62 @@ template <typename R> lbm_status initial_T_adjoint_impl(lbm_ctx* ctx, const void
   return LBM_OK;
 }
 
-template <typename R> lbm_status set_wall_impl(lbm_ctx* ctx, const double* q) {
+// Build the interpolated-wall table from a list of links (cell, pull direction, fraction);
+// later entries for the same link replace earlier ones.
+template <typename R>
+lbm_status set_wall_impl(lbm_ctx* ctx, long long n_links, const int* cell, const int* dir, const double* q) {
   const size_t N = ctx->N;
-  const int Q = ctx->Q, D = ctx->D;
+  const int Q = ctx->Q;
   const Geo& g = ctx->geo;
   std::vector<uint32_t> lw(N);
   CK(cudaMemcpyAsync(lw.data(), ctx->links, N * 4, cudaMemcpyDeviceToHost, ctx->st), "copy links");
   CK(cudaStreamSynchronize(ctx->st), "sync");
   for (size_t r = 0; r < N; ++r) lw[r] &= ~LINK_WALL;
-  std::vector<int> idx;
+  std::vector<int> row_of(N, -1);
   std::vector<R> rows;
   std::vector<int> cells;
-  if (q) {
-    for (size_t r = 0; r < N; ++r) {
-      const uint32_t w = lw[r];
-      if (!(w >> 31) || !(w & ((1u << Q) - 1u))) continue;
-      const int x = (int)(r % g.nx);
-      bool any = false;
-      R row[27];
-      for (int i = 0; i < Q; ++i) {
-        R f = R(0.5);
-        if ((w >> i) & 1u) {
-          const bool inlet = x == 0 && g.bc_lo[0] == BC_INLET && cx(i) == 1;
-          const bool outlet = x == g.nx - 1 && g.bc_hi[0] == BC_OUTLET && cx(i) == -1;
-          const double v = q[(size_t)i * N + r];
-          if (!inlet && !outlet && v > 0.0 && v <= 1.0) {
-            f = (R)v;
-            // f < 1/2 needs r + c_i as a fluid pull source of the opposite direction
-            if (f < R(0.5) && ((w >> (Q - 1 - i)) & 1u)) f = R(0.5);
-          }
-        }
-        row[i] = f;
-        any = any || f != R(0.5);
-      }
-      if (!any) continue;
-      cells.push_back((int)r);
-      for (int i = 0; i < Q; ++i) rows.push_back(row[i]);
+  for (long long k = 0; k < n_links; ++k) {
+    const int r = cell[k], i = dir[k];
+    if (r < 0 || (size_t)r >= N || i < 0 || i >= Q) return fail(ctx, LBM_ERR_ARG, "wall link out of range");
+    const double v = q[k];
+    const uint32_t w = lw[r];
+    if (!(w >> 31) || !((w >> i) & 1u) || !(v > 0.0 && v <= 1.0)) continue;
+    const int x = r % g.nx;
+    if ((x == 0 && g.bc_lo[0] == BC_INLET && cx(i) == 1) || (x == g.nx - 1 && g.bc_hi[0] == BC_OUTLET && cx(i) == -1))
+      continue;
+    R f = (R)v;
+    // f < 1/2 needs r + c_i as a fluid pull source of the opposite direction
+    if (f < R(0.5) && ((w >> (Q - 1 - i)) & 1u)) f = R(0.5);
+    if (row_of[r] < 0) {
+      if (f == R(0.5)) continue;
+      row_of[r] = (int)cells.size();
+      cells.push_back(r);
+      rows.insert(rows.end(), Q, R(0.5));
     }
+    rows[(size_t)row_of[r] * Q + i] = f;
   }
-  (void)D;
   const size_t n = cells.size();
   if (n > 0) {
-    if (!ctx->wall_idx && !(ctx->wall_idx = (int*)dalloc(ctx, N * sizeof(int))))
-      return fail(ctx, LBM_ERR_ALLOC, "wall table allocation failed");
+    // list (and table rows) in cell order, so that the wall-list launch reads coalesced
+    std::vector<size_t> order(n);
+    for (size_t k = 0; k < n; ++k) order[k] = k;
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cells[a] < cells[b]; });
+    std::vector<int> sc(n);
+    std::vector<R> sr(n * Q);
+    for (size_t k = 0; k < n; ++k) {
+      sc[k] = cells[order[k]];
+      std::copy(rows.begin() + order[k] * Q, rows.begin() + (order[k] + 1) * Q, sr.begin() + k * Q);
+    }
+    cells.swap(sc);
+    rows.swap(sr);
     if (n > ctx->wall_rows_cap) {
-      if (!(ctx->wall_q = dalloc(ctx, n * Q * sizeof(R)))) return fail(ctx, LBM_ERR_ALLOC, "wall table allocation failed");
+      // grow: the old blocks stay with the context's allocations until lbm_destroy
+      if (!(ctx->wall_q = dalloc(ctx, n * Q * sizeof(R))) || !(ctx->wall_cells = (int*)dalloc(ctx, n * sizeof(int))))
+        return fail(ctx, LBM_ERR_ALLOC, "wall table allocation failed");
       ctx->wall_rows_cap = n;
     }
-    idx.assign(N, -1);
-    for (size_t k = 0; k < n; ++k) {
-      idx[cells[k]] = (int)k;
-      lw[cells[k]] |= LINK_WALL;
-    }
-    CK(cudaMemcpyAsync(ctx->wall_idx, idx.data(), N * sizeof(int), cudaMemcpyHostToDevice, ctx->st), "copy wall index");
+    for (size_t k = 0; k < n; ++k) lw[cells[k]] |= LINK_WALL;
+    CK(cudaMemcpyAsync(ctx->wall_cells, cells.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->st), "copy wall list");
     CK(cudaMemcpyAsync(ctx->wall_q, rows.data(), n * Q * sizeof(R), cudaMemcpyHostToDevice, ctx->st), "copy wall table");
   }
   CK(cudaMemcpyAsync(ctx->links, lw.data(), N * 4, cudaMemcpyHostToDevice, ctx->st), "copy links");
@@ -1117,11 +1120,32 @@ lbm_status lbm_initial_T_adjoint(lbm_ctx* ctx, const void* state0, const void* a
                   : initial_T_adjoint_impl<float>(ctx, state0, adj0, grad_T0);
 }
 
+lbm_status lbm_set_wall_links(lbm_ctx* ctx, long long n_links, const int* cell, const int* dir, const double* q) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (!ctx->have_geo) return fail(ctx, LBM_ERR_STATE, "set_geometry must come first");
+  if (n_links < 0 || (n_links > 0 && (!cell || !dir || !q))) return fail(ctx, LBM_ERR_ARG, "null argument");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  return ctx->f64 ? set_wall_impl<double>(ctx, n_links, cell, dir, q)
+                  : set_wall_impl<float>(ctx, n_links, cell, dir, q);
+}
+
 lbm_status lbm_set_wall_fractions(lbm_ctx* ctx, const double* q) {
   if (!ctx) return LBM_ERR_ARG;
   if (!ctx->have_geo) return fail(ctx, LBM_ERR_STATE, "set_geometry must come first");
-  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
-  return ctx->f64 ? set_wall_impl<double>(ctx, q) : set_wall_impl<float>(ctx, q);
+  std::vector<int> cell, dir;
+  std::vector<double> val;
+  if (q) {
+    for (int i = 0; i < ctx->Q; ++i)
+      for (size_t r = 0; r < ctx->N; ++r) {
+        const double v = q[(size_t)i * ctx->N + r];
+        if (v > 0.0 && v <= 1.0 && v != 0.5) {
+          cell.push_back((int)r);
+          dir.push_back(i);
+          val.push_back(v);
+        }
+      }
+  }
+  return lbm_set_wall_links(ctx, (long long)cell.size(), cell.data(), dir.data(), val.data());
 }
 
 lbm_status lbm_use_graphs(lbm_ctx* ctx, int enable) {

@@ -137,7 +137,7 @@ constexpr int LB_BLOCK = 128;
 #define LB_MIN_BLOCKS 6
 #endif
 
-// link word bit 30: the cell has interpolated bounce-back links (entry wall_idx[r] of the table)
+// link word bit 30: the cell has interpolated bounce-back links (it is on the wall list)
 constexpr uint32_t LINK_WALL = 1u << 30;
 
 template <typename R> struct LBArgs {
@@ -145,9 +145,9 @@ template <typename R> struct LBArgs {
   const void* g_in;
   void* g_out;
   const uint32_t* links;
-  const int* wall_idx;  // [N] table row of cells flagged LINK_WALL (read for those only)
-  const R* wall_q;      // [rows][Q] wall fraction per pull direction (0.5: half-way)
-  int walls;            // 1: some cells carry interpolated links
+  const int* wall_cells;  // [n_wall] cells flagged LINK_WALL (interpolated bounce-back)
+  const R* wall_q;        // [n_wall][Q] their wall fraction per pull direction (0.5: half-way)
+  int n_wall;
   const R* rho;      // thermal: density at level n (lattice units)
   const R* lam;      // thermal: Lambda from the FD update (without the P_th term)
   const R* T;        // thermal: temperature at level n (viscosity law)

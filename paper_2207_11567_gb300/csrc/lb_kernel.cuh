@@ -174,20 +174,33 @@ __device__ __forceinline__ void add_delta_eq(R* m, const R* dx, const R* dy, con
   }
 }
 
-// WALLS: the interpolated bounce-back fix-up is compiled in (launched only for contexts that
-// have wall fractions, so that it costs the other runs no registers)
+// WALLS = false: every fluid cell except those flagged LINK_WALL, one block row per (y, z).
+// WALLS = true: the flagged cells only, one thread per entry of the wall list, with the
+// interpolated bounce-back fix-up compiled in (so that it costs the other cells no registers).
 template <int D, typename S, typename R, bool THERMAL, int COLL, bool WALLS>
 __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const LBArgs<R> a) {
   constexpr int Q = Lat<D>::Q;
   const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz;
-  // one block row of LB_BLOCK cells along x; y and z come from the grid (no integer division)
-  const int x = blockIdx.x * LB_BLOCK + threadIdx.x;
-  const int y = blockIdx.y;
-  const int z = blockIdx.z;
-  if (x >= nx) return;
-  const int r = x + nx * (y + ny * z);
+  int x, y, z, r, wrow = 0;
+  if constexpr (WALLS) {
+    // one thread per cell of the interpolated-wall list (its position is the table row)
+    wrow = blockIdx.x * LB_BLOCK + threadIdx.x;
+    if (wrow >= a.n_wall) return;
+    r = __ldg(a.wall_cells + wrow);
+    x = r % nx;
+    y = (r / nx) % ny;
+    z = r / (nx * ny);
+  } else {
+    // one block row of LB_BLOCK cells along x; y and z come from the grid (no integer division)
+    x = blockIdx.x * LB_BLOCK + threadIdx.x;
+    y = blockIdx.y;
+    z = blockIdx.z;
+    if (x >= nx) return;
+    r = x + nx * (y + ny * z);
+  }
   const uint32_t lw = __ldg(a.links + r);
   if (!(lw >> 31)) return;
+  if (!WALLS && (lw & LINK_WALL)) return;  // done by the wall-list launch
   const size_t N = (size_t)a.geo.N;
   const S* __restrict__ gin = (const S*)a.g_in;
   const R third = R(1) / R(3);
@@ -247,8 +260,8 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
   //   f >= 1/2:  g_i = g*_o(r) / (2 f) + (2 f - 1) / (2 f) g*_i(r) = g*_i(r) + (g*_o(r) - g*_i(r)) / (2 f)
   // (affine with weights summing to 1, so it holds for the shifted stored form as well; the
   // right-hand forms round once, on a difference of neighbouring populations)
-  if (WALLS && (lw & LINK_WALL)) {
-    const R* __restrict__ wq = a.wall_q + (size_t)__ldg(a.wall_idx + r) * Q;
+  if constexpr (WALLS) {
+    const R* __restrict__ wq = a.wall_q + (size_t)wrow * Q;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if ((lw >> i) & 1u) {
@@ -468,10 +481,11 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
 template <int D, typename S, typename R>
 cudaError_t launch_lb(const LBArgs<R>& a, int thermal, int coll, cudaStream_t st) {
   const dim3 grid((a.geo.nx + LB_BLOCK - 1) / LB_BLOCK, a.geo.ny, a.geo.nz);
-#define LB_LAUNCH(TH, CO)                                                 \
-  do {                                                                    \
-    if (a.walls) lb_step_kernel<D, S, R, TH, CO, true><<<grid, LB_BLOCK, 0, st>>>(a); \
-    else lb_step_kernel<D, S, R, TH, CO, false><<<grid, LB_BLOCK, 0, st>>>(a);        \
+#define LB_LAUNCH(TH, CO)                                                                         \
+  do {                                                                                            \
+    lb_step_kernel<D, S, R, TH, CO, false><<<grid, LB_BLOCK, 0, st>>>(a);                          \
+    if (a.n_wall > 0)                                                                             \
+      lb_step_kernel<D, S, R, TH, CO, true><<<(a.n_wall + LB_BLOCK - 1) / LB_BLOCK, LB_BLOCK, 0, st>>>(a); \
   } while (0)
   if (thermal) {
     if (coll == COLL_CUMULANT_FULL) LB_LAUNCH(true, COLL_CUMULANT_FULL);

@@ -99,6 +99,18 @@ class Solver:
             _check(self.ctx, L.lib.lbm_set_wall_fractions(self.ctx, ptr))
         del keep
 
+    def set_wall_links(self, cell, direction, q):
+        """Interpolated bounce-back from a list of links (lbm_set_wall_links): cell index, pull
+        direction and wall fraction of each link."""
+        c = np.ascontiguousarray(np.asarray(cell, dtype=np.int32))
+        d = np.ascontiguousarray(np.asarray(direction, dtype=np.int32))
+        v = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
+        if not (c.size == d.size == v.size):
+            raise ValueError("cell, direction and q must have the same length")
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_set_wall_links(self.ctx, int(c.size), c.ctypes.data_as(C.c_void_p),
+                                                      d.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p)))
+
     def set_fields(self, T=None, Y=None, u=None, P_h=None, g_pert=None):
         keep = []
 
@@ -260,5 +272,7 @@ def from_workload(wl, **kw):
     s = Solver(wl.cfg, wl.mask, wl.inlet_u, **kw)
     if getattr(wl, "qwall", None) is not None:
         s.set_wall_fractions(wl.qwall)
+    elif wl.info.get("wall_links") is not None:
+        s.set_wall_links(*wl.info["wall_links"])
     s.set_fields(T=wl.T, Y=wl.Y, u=wl.u, P_h=wl.P_h, g_pert=wl.g_pert)
     return s

@@ -80,3 +80,45 @@ def test_duct3d_offset_walls_f64():
     _links_match(o, gpu)
     errs = compare(wl, gpu, st)
     assert max(errs.values()) < 1e-10, errs
+
+
+def _swirl_curved(storage, seed=4):
+    """Small swirl burner with interpolated walls on the injector cylinders and the exhaust cone;
+    the GPU gets the links as a list (lbm_set_wall_links), the oracle the equivalent dense array."""
+    wl = W.generate.swirl_3d(40, 20, 20, curved=True, storage=storage, seed=seed)
+    c, d, q = wl.info["wall_links"]
+    if storage != "f64":
+        q = np.asarray(q, dtype=np.float32).astype(np.float64)
+        wl.info["wall_links"] = (c, d, q)
+    dense = np.zeros((27, wl.N))
+    dense[d, c] = q
+    return wl, dense
+
+
+def _oracle_q(wl, qwall, steps, store_round=None):
+    from oracle.step import Oracle
+    o = Oracle(wl.cfg, wl.mask, wl.inlet_u, store_round=store_round, qwall=qwall)
+    st = o.round_state(o.init_state(T=wl.T, Y=wl.Y, u=wl.u, P_h=wl.P_h, g_pert=wl.g_pert))
+    return o, o.run(st, steps)
+
+
+def test_swirl3d_curved_walls_f64():
+    wl, dense = _swirl_curved("f64")
+    o, st = _oracle_q(wl, dense, 30)
+    gpu = gpu_run(wl, 30)
+    _links_match(o, gpu)
+    assert ((gpu["links"] >> 30) & 1).sum() > 100
+    errs = compare(wl, gpu, st)
+    assert max(errs.values()) < 1e-10, errs
+
+
+def test_swirl3d_curved_walls_f32():
+    wl, dense = _swirl_curved("f32")
+    o, st = _oracle_q(wl, dense, 60)
+    gpu = gpu_run(wl, 60)
+    _links_match(o, gpu)
+    errs = compare(wl, gpu, st)
+    _, st32 = _oracle_q(wl, dense, 60, store_round="f32")
+    floor = compare(wl, {"u": st32["u"].numpy(), "P_h": st32["P_h"].numpy(), "g": st32["g"].numpy()}, st)
+    bad = {k: (v, floor[k]) for k, v in errs.items() if not v <= max(3e-5, 3.0 * floor[k])}
+    assert not bad, (errs, floor)

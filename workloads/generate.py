@@ -173,11 +173,13 @@ def swirl_k(S, Ri, Ro):
 def swirl_3d(nx=256, ny=128, nz=128, reactive=False, storage="f32", seed=0,
              collision="cumulant", u_axial=0.05, swirl=0.6, noise=0.05, smag=0.17, F=8.0,
              steps=None, dx=None, dt=None, A1=1.0e9, A2=5.0e6, T_in=320.0, T_hot=1970.0,
-             sensor_wref=1e-5):
+             sensor_wref=1e-5, curved=False):
     """Swirl-burner-like domain along x: annular swirling inlet (radii 8 and 16 cells at the
     128-cell scale) through an injector duct, square confined chamber, contracting exhaust to
     an outlet; cold (LB only) or reactive (2-step chemistry, thickened flame with sensor,
-    closed-domain thermodynamic pressure)."""
+    closed-domain thermodynamic pressure). curved: wall fractions of every link toward the
+    injector cylinders and the exhaust cone (info["wall_links"] = cells, directions, fractions),
+    found by bisection on the continuous shapes of which the mask samples the cell centres."""
     rng = np.random.default_rng(seed)
     s = ny / 128.0
     cfg = _base_cfg(3, nx, ny, nz, storage, collision)
@@ -220,6 +222,15 @@ def swirl_3d(nx=256, ny=128, nz=128, reactive=False, storage="f32", seed=0,
     wl = Workload("swirl_3d", cfg, mask, inlet, u, np.zeros(N),
                   steps=steps or (5000 if reactive else 10000),
                   info={"L1": L1, "L2": L2, "Re": Re, "swirl_k": k})
+    if curved:
+        span = max(1, nx - 1 - L2)
+
+        def solid(X, Y, Z):
+            rr = np.sqrt((Y - yc) ** 2 + (Z - zc) ** 2)
+            return ((X < L1) & ((rr < Ri) | (rr > Ro))) | ((X >= L2) & (rr > Rc + (Re - Rc) * (X - 0.5 - L2) / span))
+
+        assert np.array_equal(solid(x + 0.5, y + 0.5, z + 0.5), mask.astype(bool))
+        wl.info["wall_links"] = link_fractions(mask, (nx, ny, nz), solid)
     if reactive:
         names = SPECIES["6sp"]
         Yu, Yb = np.array(mixture_phi(names, 0.83)), np.array(burnt_mixture(names, 0.83))
@@ -234,6 +245,42 @@ def swirl_3d(nx=256, ny=128, nz=128, reactive=False, storage="f32", seed=0,
         wl.T = T_in + (T_hot - T_in) * b
         wl.Y = Yu[:, None] * (1 - b)[None, :] + Yb[:, None] * b[None, :]
     return wl
+
+
+def link_fractions(mask, dims, solid, iters=40):
+    """Links from fluid cells to solid cells inside the grid, as (cells, directions, fractions):
+    for pull direction i the link r -> r - c_i, fraction t in (0, 1] where the segment from the
+    centre of r enters the solid region solid(X, Y, Z) (continuous coordinates, cell centres at
+    index + 0.5), by bisection. D3Q27 order: c = (i % 3 - 1, (i // 3) % 3 - 1, i // 9 - 1)."""
+    nx, ny, nz = dims
+    m = np.asarray(mask).astype(bool)
+    x, y, z = _coords(nx, ny, nz)
+    cells, dirs, qs = [], [], []
+    for i in range(27):
+        cx, cy, cz = i % 3 - 1, (i // 3) % 3 - 1, i // 9 - 1
+        if cx == 0 and cy == 0 and cz == 0:
+            continue
+        sx, sy, sz = x - cx, y - cy, z - cz
+        ins = (sx >= 0) & (sx < nx) & (sy >= 0) & (sy < ny) & (sz >= 0) & (sz < nz)
+        sel = np.zeros(m.size, bool)
+        sel[ins] = m[(sx + nx * (sy + ny * sz))[ins]]
+        sel &= ~m
+        r = np.nonzero(sel)[0]
+        if r.size == 0:
+            continue
+        X0, Y0, Z0 = x[r] + 0.5, y[r] + 0.5, z[r] + 0.5
+        lo, hi = np.zeros(r.size), np.ones(r.size)
+        for _ in range(iters):
+            mid = 0.5 * (lo + hi)
+            inside = solid(X0 - mid * cx, Y0 - mid * cy, Z0 - mid * cz)
+            hi = np.where(inside, mid, hi)
+            lo = np.where(inside, lo, mid)
+        cells.append(r)
+        dirs.append(np.full(r.size, i))
+        qs.append(np.clip(hi, 1e-3, 1.0))
+    if not cells:
+        return np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0)
+    return (np.concatenate(cells).astype(np.int32), np.concatenate(dirs).astype(np.int32), np.concatenate(qs))
 
 
 # ------------------------------------------------------------------------ periodic box
