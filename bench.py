@@ -115,10 +115,12 @@ def _timed_steps(solver, steps, torch):
     return e0.elapsed_time(e1)
 
 
-def run_variant(wl, storage, steps, warmup, torch, profile_steps):
+def run_variant(wl, storage, steps, warmup, torch, profile_steps, stats=0):
     from paper_2207_11567_gb300 import from_workload
     wl.cfg["storage"] = storage
     s = from_workload(wl)
+    if stats:
+        s.stats_control(1, stats)
     s.step(warmup)
     s.synchronize()
     ms = _timed_steps(s, steps, torch)
@@ -290,6 +292,13 @@ def small_bench(args):
     kt = s.kernel_times()
     s.profile(False)
     kb = s.kernel_bytes()
+    flame = None
+    if wl.cfg.get("thermal") and wl.cfg["dim"] == 2:
+        s.synchronize()
+        t0 = time.perf_counter()
+        L = s.flame_length(0.5, wl.cfg.get("T_in", 300.0), 1950.0)
+        flame = {"length_cells": L, "ms_wall": 1e3 * (time.perf_counter() - t0),
+                 "note": "lbm_flame_length at c = 0.5, wall time including the host read of the partial sums"}
     s.close()
     ms = statistics.mean(per_step)
     kern = {k: {"ms": t / n, "GB/s": kb[k] / (t / n * 1e-3) / 1e9} for k, (t, n) in kt.items() if n}
@@ -311,7 +320,7 @@ def small_bench(args):
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": ach, "peak": peak, "unit": "GB/s",
                          "frac": ach / peak, "peak_kind": peak_kind, "traffic": None,
                          "note": "algorithmic bytes / CUDA-event time of the kernel in a back-to-back step"},
-            "kernels": kern, "clocks": clk.summary()}
+            "kernels": kern, "clocks": clk.summary(), "flame_length": flame}
     print(json.dumps(line))
 
 
@@ -333,6 +342,8 @@ def main():
     ap.add_argument("--no-fd-check", action="store_true", help="c5: skip the FP64 finite-difference check")
     ap.add_argument("--fd-dirs", type=int, default=16, help="c5: directions of the finite-difference check")
     ap.add_argument("--adj-steps", type=int, default=0, help="c5: steps K (default: the workload's 2000)")
+    ap.add_argument("--stats", type=int, default=0,
+                    help="with --only: sample running statistics every N steps during the timed steps")
     ap.add_argument("--curved", action="store_true",
                     help="c3/c4: interpolated bounce-back on the injector cylinders and the exhaust cone")
     args = ap.parse_args()
@@ -380,7 +391,7 @@ def main():
         return W.make(args.workload)
 
     if args.only:
-        r = run_variant(make(), args.only, args.steps, args.warmup, torch, profile_steps=2)
+        r = run_variant(make(), args.only, args.steps, args.warmup, torch, profile_steps=2, stats=args.stats)
         print(json.dumps({"case": args.case, "storage": args.only, "ms_per_step": r["ms"] / args.steps,
                           "kernels": r["kernels"]}))
         return
@@ -407,13 +418,25 @@ def main():
     dominant = max(kern, key=lambda k: kern[k]["ms_avg"] * kern[k]["launches"])
     dk = kern[dominant]
     achieved = dk["bytes"] / (dk["ms_avg"] * 1e-3) / 1e9
-    traffic = None
+    traffic, warp_inst = None, None
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
-            tr = json.load(f).get(f"{dominant}:{args.workload}:f32")
-            traffic = tr if tr else None
+            prof = json.load(f)
+            traffic = prof.get(f"{dominant}:{args.workload}:f32") or None
+            warp_inst = prof.get(f"{dominant}:{args.workload}:f32:warp_inst") or None
     except Exception:
         traffic = None
+    # instruction-issue roof: 152 SMs x 4 schedulers x 1 warp instruction per cycle x 32 lanes at
+    # the sampled SM clock (thread instructions per second)
+    clk_summary = clk.summary()
+    sm_hz = (clk_summary.get("sm_mhz") or 2070.0) * 1e6
+    issue_peak = 152 * 4 * 32 * sm_hz
+    issue = None
+    if warp_inst and not args.curved:
+        ach = warp_inst * 32 / (dk["ms_avg"] * 1e-3)
+        issue = {"achieved": ach / 1e12, "peak": issue_peak / 1e12, "unit": "T thread-instructions/s",
+                 "frac": ach / issue_peak, "warp_inst_per_launch": warp_inst,
+                 "note": "ncu instruction count of the same kernel (192x96x96 capture x8), live CUDA-event time"}
     per_step_launches = sum(1 for k in kern.values() if k["launches"])
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -433,7 +456,7 @@ def main():
         "gpu_launches": per_step_launches * args.steps,
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
-                     "bytes_per_launch": dk["bytes"], "ms_per_launch": dk["ms_avg"]},
+                     "bytes_per_launch": dk["bytes"], "ms_per_launch": dk["ms_avg"], "issue": issue},
         "kernels": {k: {"ms": v["ms_avg"], "GB/s": (v["bytes"] / (v["ms_avg"] * 1e-3) / 1e9) if v["ms_avg"] else 0.0}
                     for k, v in kern.items() if v["launches"]},
         "fp16_storage": {"value": N * args.steps * world / (f16["ms"] * 1e-3) / 1e6, "unit": "MLUPS",
@@ -441,7 +464,7 @@ def main():
                          "lb_ms": f16["kernels"]["lb_stream_collide"]["ms_avg"],
                          "lb_GB/s": f16["kernels"]["lb_stream_collide"]["bytes"]
                          / (f16["kernels"]["lb_stream_collide"]["ms_avg"] * 1e-3) / 1e9},
-        "clocks": clk.summary(),
+        "clocks": clk_summary,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample()

@@ -181,6 +181,26 @@ lbm_status lbm_set_wall_fractions(lbm_ctx* ctx, const double* q);
  * [Q][N] array would not fit in host memory. */
 lbm_status lbm_set_wall_links(lbm_ctx* ctx, long long n_links, const int* cell, const int* dir, const double* q);
 
+/* Running statistics (the paper's diagnostics, Section 3: time-averaged and RMS fields).
+ * op 0: reset the accumulators (allocated on first use); op 1: sample after every `interval`-th
+ * step from now on (steps counted since set_fields; sampled steps run without CUDA graphs);
+ * op 2: stop sampling. Per fluid cell and field (u components, P_h, and T for thermal runs):
+ * mean and sum of squared deviations in FP32 by Welford's update. */
+lbm_status lbm_stats_control(lbm_ctx* ctx, int op, int interval);
+
+/* Statistics so far: dst holds 2 * nf * N doubles, the nf mean fields then the nf RMS
+ * fluctuation fields (population standard deviation over the samples), fields in the order
+ * u_x, u_y[, u_z], P_h[, T]; solid cells hold 0. n_samples (may be NULL) receives the count.
+ * Synchronises the stream when dst is host memory. */
+lbm_status lbm_get_stats(lbm_ctx* ctx, double* dst, int dst_on_device, long long* n_samples);
+
+/* Flame surface in 2-D (Section 3.1 tracks the c = 0.2 and 0.8 iso-lines): length, in cells, of
+ * the iso-line c = level of the progress variable c = (T - T_u) / (T_b - T_u) of the current
+ * state, by marching squares over squares of four fluid cell centres (a corner equal to the
+ * level counts as above; saddles are split by the mean of the corners). 2-D thermal runs only;
+ * synchronises the stream. */
+lbm_status lbm_flame_length(lbm_ctx* ctx, double level, double T_u, double T_b, double* length);
+
 /* Checkpoint: bytes of device memory needed, save into / load from caller-owned device memory. */
 size_t lbm_state_bytes(const lbm_ctx* ctx);
 lbm_status lbm_save_state(lbm_ctx* ctx, void* dst_device);

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhlbm.so")
-SOURCES = ["api.cu", "aux_kernels.cu", "fd_kernels.cu", "lb_d2q9.cu", "lb_d3q27_f64.cu",
+SOURCES = ["api.cu", "aux_kernels.cu", "stats.cu", "fd_kernels.cu", "lb_d2q9.cu", "lb_d3q27_f64.cu",
            "lb_d3q27_f32.cu", "lb_d3q27_f16.cu", "noalloc.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -72,6 +72,13 @@ struct lbm_ctx {
   void* seg_ws = nullptr;
   int seg_cap = 0;
   double* obj_partials = nullptr;
+  // running statistics (lbm_stats_control) and flame length
+  float* st_mean = nullptr;
+  float* st_m2 = nullptr;
+  int st_nf = 0, st_interval = 1;
+  long long st_n = 0;
+  bool st_on = false;
+  double* fl_partials = nullptr;
   // profiling
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -629,6 +636,30 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
   if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "set_fields must come first");
   if (n_steps == 0) return LBM_OK;
   CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  if (ctx->st_on) {
+    // statistics: direct launches; a sampled step also writes P_h, then the accumulators update
+    for (int k = 0; k < n_steps; ++k) {
+      const bool sample = (ctx->steps + 1) % ctx->st_interval == 0;
+      CK(enqueue_step(ctx, ctx->cur, sample || k == n_steps - 1), "step launch");
+      ctx->cur ^= 1;
+      ++ctx->steps;
+      if (sample) {
+        ++ctx->st_n;
+        const int cur = ctx->cur;
+        if (ctx->f64)
+          CK(launch_stats<double>((int)ctx->N, ctx->st_nf, ctx->links, (const double*)ctx->u, ctx->D,
+                                  (const double*)ctx->ph, (const double*)ctx->T[cur], ctx->st_n, ctx->st_mean,
+                                  ctx->st_m2, ctx->st),
+             "statistics");
+        else
+          CK(launch_stats<float>((int)ctx->N, ctx->st_nf, ctx->links, (const float*)ctx->u, ctx->D,
+                                 (const float*)ctx->ph, (const float*)ctx->T[cur], ctx->st_n, ctx->st_mean,
+                                 ctx->st_m2, ctx->st),
+             "statistics");
+      }
+    }
+    return LBM_OK;
+  }
   int left = n_steps - 1;  // the last step also writes the output-only fields
   if (ctx->use_graphs && !ctx->prof) {
     while (left >= 2) {
@@ -1146,6 +1177,84 @@ lbm_status lbm_set_wall_fractions(lbm_ctx* ctx, const double* q) {
       }
   }
   return lbm_set_wall_links(ctx, (long long)cell.size(), cell.data(), dir.data(), val.data());
+}
+
+lbm_status lbm_stats_control(lbm_ctx* ctx, int op, int interval) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (op < 0 || op > 2 || (op == 1 && interval < 1)) return fail(ctx, LBM_ERR_ARG, "op 0|1|2, interval >= 1");
+  if (!ctx->have_geo) return fail(ctx, LBM_ERR_STATE, "set_geometry must come first");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  const int nf = ctx->D + 1 + (ctx->cfg.thermal ? 1 : 0);
+  if (!ctx->st_mean) {
+    if (!(ctx->st_mean = (float*)dalloc(ctx, (size_t)nf * ctx->N * sizeof(float))) ||
+        !(ctx->st_m2 = (float*)dalloc(ctx, (size_t)nf * ctx->N * sizeof(float))))
+      return fail(ctx, LBM_ERR_ALLOC, "statistics allocation failed");
+    ctx->st_nf = nf;
+    CK(cudaMemsetAsync(ctx->st_mean, 0, (size_t)nf * ctx->N * sizeof(float), ctx->st), "memset");
+    CK(cudaMemsetAsync(ctx->st_m2, 0, (size_t)nf * ctx->N * sizeof(float), ctx->st), "memset");
+  }
+  if (op == 0) {
+    CK(cudaMemsetAsync(ctx->st_mean, 0, (size_t)nf * ctx->N * sizeof(float), ctx->st), "memset");
+    CK(cudaMemsetAsync(ctx->st_m2, 0, (size_t)nf * ctx->N * sizeof(float), ctx->st), "memset");
+    ctx->st_n = 0;
+  } else if (op == 1) {
+    ctx->st_on = true;
+    ctx->st_interval = interval;
+  } else {
+    ctx->st_on = false;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_stats(lbm_ctx* ctx, double* dst, int dst_on_device, long long* n_samples) {
+  if (!ctx || !dst) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->st_mean) return fail(ctx, LBM_ERR_STATE, "statistics were never started");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  const size_t n = 2 * (size_t)ctx->st_nf * ctx->N;
+  double* out = dst;
+  if (!dst_on_device) {
+    if (ctx->scratch_out_n < n) {
+      if (!(ctx->scratch_out = (double*)dalloc(ctx, n * sizeof(double))))
+        return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+      ctx->scratch_out_n = n;
+    }
+    out = ctx->scratch_out;
+  }
+  CK(launch_stats_finalize((int)ctx->N, ctx->st_nf, ctx->links, ctx->st_mean, ctx->st_m2, ctx->st_n, out, ctx->st),
+     "statistics");
+  if (!dst_on_device) {
+    CK(cudaMemcpyAsync(dst, out, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "copy statistics");
+    CK(cudaStreamSynchronize(ctx->st), "sync");
+  }
+  if (n_samples) *n_samples = ctx->st_n;
+  return LBM_OK;
+}
+
+lbm_status lbm_flame_length(lbm_ctx* ctx, double level, double T_u, double T_b, double* length) {
+  if (!ctx || !length) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "set_fields must come first");
+  if (ctx->D != 2 || !ctx->cfg.thermal) return fail(ctx, LBM_ERR_UNSUPPORTED, "flame length: 2-D thermal runs");
+  if (!(T_b != T_u)) return fail(ctx, LBM_ERR_ARG, "T_b must differ from T_u");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  const int nb = (int)((ctx->N + stats_block() - 1) / stats_block());
+  if (!ctx->fl_partials && !(ctx->fl_partials = (double*)dalloc(ctx, (size_t)nb * sizeof(double))))
+    return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+  const int cur = ctx->cur;
+  if (ctx->f64)
+    CK(launch_flame_length<double>(ctx->geo, ctx->links, (const double*)ctx->T[cur], T_u, T_b, level, ctx->fl_partials,
+                                   ctx->st),
+       "flame length");
+  else
+    CK(launch_flame_length<float>(ctx->geo, ctx->links, (const float*)ctx->T[cur], T_u, T_b, level, ctx->fl_partials,
+                                  ctx->st),
+       "flame length");
+  std::vector<double> h(nb);
+  CK(cudaMemcpyAsync(h.data(), ctx->fl_partials, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "copy");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  double t = 0.0;
+  for (double v : h) t += v;
+  *length = t;
+  return LBM_OK;
 }
 
 lbm_status lbm_use_graphs(lbm_ctx* ctx, int enable) {

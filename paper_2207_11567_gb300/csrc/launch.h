@@ -57,4 +57,14 @@ cudaError_t launch_initial_T_adjoint(const FDArgs<R>& fdf, const R* adj0, R* gra
 template <typename R>
 cudaError_t launch_fuel_objective(const FDArgs<R>& fdf, int fuel, R* Tbar, R* Ybar, double* partials, int nblocks,
                                   cudaStream_t st);
+// stats.cu: running statistics and flame length
+int stats_block();
+cudaError_t launch_stats_finalize(int N, int nf, const uint32_t* links, const float* mean, const float* m2,
+                                  long long n, double* out, cudaStream_t st);
+template <typename R>
+cudaError_t launch_stats(int N, int nf, const uint32_t* links, const R* u, int D, const R* ph, const R* T, long long n,
+                         float* mean, float* m2, cudaStream_t st);
+template <typename R>
+cudaError_t launch_flame_length(const Geo& g, const uint32_t* links, const R* T, double T_u, double T_b, double level,
+                                double* partials, cudaStream_t st);
 }  // namespace hlbm

@@ -188,6 +188,27 @@ class Solver:
             _check(self.ctx, L.lib.lbm_get_stencil_words(self.ctx, out.ctypes.data_as(C.c_void_p), 0))
         return out
 
+    # ----------------------------------------------------------------------- diagnostics
+    def stats_control(self, op, interval=1):
+        """0 reset, 1 sample every `interval` steps, 2 stop (lbm_stats_control)."""
+        _check(self.ctx, L.lib.lbm_stats_control(self.ctx, int(op), int(interval)))
+
+    def stats(self):
+        """(mean, rms, n): arrays [nf][N] for u components, P_h (and T), and the sample count."""
+        nf = self.dim + 1 + (1 if self.cfg.get("thermal") else 0)
+        buf = np.empty(2 * nf * self.N, dtype=np.float64)
+        n = C.c_longlong()
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_get_stats(self.ctx, buf.ctypes.data_as(C.c_void_p), 0, C.byref(n)))
+        return buf[: nf * self.N].reshape(nf, self.N), buf[nf * self.N:].reshape(nf, self.N), n.value
+
+    def flame_length(self, level, T_u, T_b):
+        """Length (cells) of the c = level iso-line of c = (T - T_u) / (T_b - T_u) (2-D)."""
+        out = C.c_double()
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_flame_length(self.ctx, float(level), float(T_u), float(T_b), C.byref(out)))
+        return out.value
+
     # ---------------------------------------------------------------------- checkpoints
     def state_bytes(self):
         return int(L.lib.lbm_state_bytes(self.ctx))

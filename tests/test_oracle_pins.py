@@ -436,3 +436,40 @@ def test_poiseuille_between_offset_walls(q):
             out.append(np.abs(mid - prof).max() / 0.01)
     assert errs[1] < 0.01 and errs[0] / errs[1] > 3.0, errs
     assert errs_hw[1] > 5.0 * errs[1], (errs, errs_hw)
+
+
+def test_running_stats_closed_form():
+    """x_k = a + b (-1)^k over an even number of samples: mean a, RMS |b| exactly."""
+    from oracle.stats import running_stats
+    a, b = np.array([1.5, -2.0, 300.0]), np.array([0.25, -3.0, 7.0])
+    samples = [a + b * (-1) ** k for k in range(10)]
+    mean, rms = running_stats(samples)
+    assert np.allclose(mean, a, rtol=0, atol=1e-12)
+    assert np.allclose(rms, np.abs(b), rtol=0, atol=1e-12)
+
+
+def test_flame_length_straight_line_and_circle():
+    """A linear field's iso-line is a straight segment: exact length within the square of corner
+    centres. A radial field's iso-line is a polygon inscribed in the circle: within 0.5% of 2 pi R
+    for R = 10 cells; and a 4-corner saddle gives the two short segments."""
+    from oracle.stats import flame_length
+    n = 40
+    yy, xx = np.mgrid[0:n, 0:n].astype(float)
+    fluid = np.ones((n, n), bool)
+    theta = 0.3
+    c = np.cos(theta) * (xx - 20.3) + np.sin(theta) * (yy - 17.1)
+    L = flame_length(c, fluid, 0.0)
+    # the line x cos + y sin = const crossing the square [0, n-1]^2 of centres
+    t = np.linspace(-100, 100, 400001)
+    px, py = 20.3 - np.sin(theta) * t, 17.1 + np.cos(theta) * t
+    inside = (px >= 0) & (px <= n - 1) & (py >= 0) & (py <= n - 1)
+    exact = (t[inside].max() - t[inside].min())
+    assert abs(L - exact) < 1e-3
+    r = np.hypot(xx - 19.6, yy - 20.2)
+    Lc = flame_length(r, fluid, 10.0)
+    assert abs(Lc - 2 * np.pi * 10.0) / (2 * np.pi * 10.0) < 5e-3
+    sad = np.array([[1.0, 0.0], [0.0, 1.0]])
+    # corners (0,0)=1 above, (1,0)=0, (1,1)=1, (0,1)=0 at level 0.6; centre 0.5 below: the two
+    # above-level corners are cut off, each by a segment between the edge midpoints at 0.4 / 0.6
+    Ls = flame_length(sad, np.ones((2, 2), bool), 0.6)
+    assert abs(Ls - 2 * np.hypot(0.4, 0.4)) < 1e-12
