@@ -117,6 +117,20 @@ void* dalloc(lbm_ctx* c, size_t bytes) {
   return p;
 }
 
+// A pointer the device can dereference for this host pointer: pinned (page-locked) host memory
+// through its device mapping, device or managed memory as it is; nullptr for pageable memory.
+const double* device_view(const double* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) return (const double*)a.devicePointer;
+  return nullptr;
+}
+
 void dfree_all(lbm_ctx* c) {
   for (void* p : c->allocs) {
     if (c->cfg.free) c->cfg.free(p, c->cfg.alloc_user);
@@ -536,25 +550,37 @@ lbm_status lbm_set_fields(lbm_ctx* ctx, const double* T, const double* Y, const 
   if (c.thermal && (!T || !Y)) return fail(ctx, LBM_ERR_ARG, "thermal run needs T and Y");
   CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
   const size_t N = ctx->N, K = ctx->K, D = ctx->D, Q = ctx->Q;
-  // stage all double inputs in one device buffer
+  // inputs the kernel can read in place (device memory, or pinned host memory through its device
+  // mapping) are used directly; the others are staged in one device buffer
   const size_t nT = c.thermal ? N : 0, nY = c.thermal ? K * N : 0, nG = g_pert ? Q * N : 0;
-  const size_t total = nT + nY + D * N + N + nG + 8;
+  const double* vT = on_device ? T : device_view(T);
+  const double* vY = on_device ? Y : device_view(Y);
+  const double* vu = on_device ? u : device_view(u);
+  const double* vP = on_device ? P_h : device_view(P_h);
+  const double* vG = on_device ? g_pert : device_view(g_pert);
+  const size_t total = (nT && !vT ? nT : 0) + (nY && !vY ? nY : 0) + (vu ? 0 : D * N) + (vP ? 0 : N) +
+                       (nG && !vG ? nG : 0) + 8;
   double* buf = (double*)dalloc(ctx, total * 8);
   if (!buf) return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
-  double *dT = buf, *dY = dT + nT, *du = dY + nY, *dP = du + D * N, *dG = dP + N, *dW = dG + nG;
-  const auto kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  double* next = buf;
   lbm_status st = LBM_OK;
-  auto cp = [&](double* dst, const double* src, size_t n) {
-    if (st == LBM_OK && n) {
-      cudaError_t e = cudaMemcpyAsync(dst, src, n * 8, kind, ctx->st);
+  auto stage = [&](const double* view, const double* src, size_t n) -> const double* {
+    if (!n || !src) return nullptr;
+    if (view) return view;
+    double* dst = next;
+    next += n;
+    if (st == LBM_OK) {
+      cudaError_t e = cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyHostToDevice, ctx->st);
       if (e != cudaSuccess) st = cuda_fail(ctx, e, "copy fields");
     }
+    return dst;
   };
-  cp(dT, T, nT);
-  cp(dY, Y, nY);
-  cp(du, u, D * N);
-  cp(dP, P_h, N);
-  cp(dG, g_pert, nG);
+  const double* dT = stage(vT, T, nT);
+  const double* dY = stage(vY, Y, nY);
+  const double* du = stage(vu, u, D * N);
+  const double* dP = stage(vP, P_h, N);
+  const double* dG = stage(vG, g_pert, nG);
+  double* dW = next;
   double invW[LBM_MAX_SPECIES] = {0};
   for (size_t k = 0; k < K; ++k) invW[k] = 1.0 / c.sp[k].W;
   if (st == LBM_OK) {
@@ -566,17 +592,17 @@ lbm_status lbm_set_fields(lbm_ctx* ctx, const double* T, const double* Y, const 
     cudaError_t e;
     const int cur = 0;
     if (ctx->f64)
-      e = launch_set_fields<double, double>(ctx->D, ctx->geo, dT, dY, (int)K, dW, du, dP, g_pert ? dG : nullptr,
+      e = launch_set_fields<double, double>(ctx->D, ctx->geo, dT, dY, (int)K, dW, du, dP, dG,
                                             p_fac, c.P_ref, c.thermal, (double*)ctx->g[cur], (double*)ctx->T[cur],
                                             (double*)ctx->Y[cur], (double*)ctx->u, (double*)ctx->rho,
                                             (double*)ctx->lam, (double*)ctx->ph, ctx->st);
     else if (c.storage == LBM_STORE_F16)
-      e = launch_set_fields<__half, float>(ctx->D, ctx->geo, dT, dY, (int)K, dW, du, dP, g_pert ? dG : nullptr,
+      e = launch_set_fields<__half, float>(ctx->D, ctx->geo, dT, dY, (int)K, dW, du, dP, dG,
                                            p_fac, c.P_ref, c.thermal, (__half*)ctx->g[cur], (float*)ctx->T[cur],
                                            (float*)ctx->Y[cur], (float*)ctx->u, (float*)ctx->rho,
                                            (float*)ctx->lam, (float*)ctx->ph, ctx->st);
     else
-      e = launch_set_fields<float, float>(ctx->D, ctx->geo, dT, dY, (int)K, dW, du, dP, g_pert ? dG : nullptr,
+      e = launch_set_fields<float, float>(ctx->D, ctx->geo, dT, dY, (int)K, dW, du, dP, dG,
                                           p_fac, c.P_ref, c.thermal, (float*)ctx->g[cur], (float*)ctx->T[cur],
                                           (float*)ctx->Y[cur], (float*)ctx->u, (float*)ctx->rho,
                                           (float*)ctx->lam, (float*)ctx->ph, ctx->st);
@@ -693,7 +719,11 @@ lbm_status lbm_get_fields(lbm_ctx* ctx, unsigned bits, double* dst, int dst_on_d
   const size_t n = fields_size(ctx, bits);
   if (n == 0) return LBM_OK;
   double* out = dst;
-  if (!dst_on_device) {
+  // pinned host memory is written in place through its device mapping; other host memory is
+  // filled from a device scratch buffer
+  double* view = dst_on_device ? dst : (double*)device_view(dst);
+  const bool staged = view == nullptr;
+  if (staged) {
     if (ctx->scratch_out_n < n) {
       double* p = (double*)dalloc(ctx, n * 8);
       if (!p) return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
@@ -701,6 +731,8 @@ lbm_status lbm_get_fields(lbm_ctx* ctx, unsigned bits, double* dst, int dst_on_d
       ctx->scratch_out_n = n;
     }
     out = ctx->scratch_out;
+  } else {
+    out = view;
   }
   const int cur = ctx->cur;
   cudaError_t e;
@@ -720,7 +752,7 @@ lbm_status lbm_get_fields(lbm_ctx* ctx, unsigned bits, double* dst, int dst_on_d
                                         (const float*)ctx->ph, (const float*)ctx->rho, (const float*)ctx->lam,
                                         ctx->pth, ctx->cfg.P_ref, out, ctx->st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "get_fields kernel");
-  if (!dst_on_device) CK(cudaMemcpyAsync(dst, out, n * 8, cudaMemcpyDeviceToHost, ctx->st), "copy out");
+  if (staged) CK(cudaMemcpyAsync(dst, out, n * 8, cudaMemcpyDeviceToHost, ctx->st), "copy out");
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, ctx->flag, 4, cudaMemcpyDeviceToHost, ctx->st), "copy flag");
   CK(cudaStreamSynchronize(ctx->st), "sync");

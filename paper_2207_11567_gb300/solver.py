@@ -145,13 +145,20 @@ class Solver:
         torch.cuda.current_stream(self.device).wait_stream(self.stream)
 
     # --------------------------------------------------------------------------- output
-    def fields(self, bits=L.F_T | L.F_Y | L.F_U | L.F_PH | L.F_RHO | L.F_LAM | L.F_G, device=False):
-        """Selected fields as float64 (numpy on the host, or a torch tensor on the device)."""
+    def fields(self, bits=L.F_T | L.F_Y | L.F_U | L.F_PH | L.F_RHO | L.F_LAM | L.F_G, device=False, out=None):
+        """Selected fields as float64 (numpy on the host, or a torch tensor on the device). out: an
+        optional host float64 array of lbm_fields_size(bits) values to fill (e.g. pinned memory)."""
         if not self.cfg.get("thermal"):
             bits &= ~(L.F_T | L.F_Y | L.F_RHO | L.F_LAM)
         n = L.lib.lbm_fields_size(self.ctx, bits)
         with torch.cuda.device(self.device):
-            if device:
+            if out is not None:
+                buf = np.asarray(out).reshape(-1)
+                if buf.dtype != np.float64 or buf.size < n or not buf.flags.c_contiguous:
+                    raise ValueError("out must be a contiguous float64 array of at least %d values" % n)
+                buf = buf[:n]
+                _check(self.ctx, L.lib.lbm_get_fields(self.ctx, bits, buf.ctypes.data_as(C.c_void_p), 0))
+            elif device:
                 out = torch.empty(n, dtype=torch.float64, device=self.device)
                 self._after_torch()
                 _check(self.ctx, L.lib.lbm_get_fields(self.ctx, bits, C.c_void_p(out.data_ptr()), 1))
