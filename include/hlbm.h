@@ -129,6 +129,12 @@ const char* lbm_last_error(const lbm_ctx* ctx);
  * Builds the per-cell link words (see lbm_get_links). */
 lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* mask, const double* inlet_u, int on_device);
 
+/* Replace the inlet-face velocities only (same layout as in lbm_set_geometry), between steps;
+ * fields, link words and captured graphs stay. on_device: 1 if inlet_u is device memory. Pinned
+ * host memory is read in place by the device: keep it unchanged until the stream has passed the
+ * call; pageable host memory may be reused on return. Requires lbm_set_geometry first. */
+lbm_status lbm_set_inlet(lbm_ctx* ctx, const double* inlet_u, int on_device);
+
 /* Initial fields: T [N] (K), Y [n_species][N], u [dim][N], P_h [N] (lattice), g_pert [Q][N]
  * (lattice, may be NULL). Populations are set to the equilibrium of Eq. 6 plus g_pert. T and Y
  * are ignored (may be NULL) when cfg.thermal == 0. Requires lbm_set_geometry first. */
@@ -200,6 +206,26 @@ lbm_status lbm_get_stats(lbm_ctx* ctx, double* dst, int dst_on_device, long long
  * level counts as above; saddles are split by the mean of the corners). 2-D thermal runs only;
  * synchronises the stream. */
 lbm_status lbm_flame_length(lbm_ctx* ctx, double level, double T_u, double T_b, double* length);
+
+/* Properties of a planar flame propagating along x (Section 3.1 takes the burnt state, adiabatic
+ * temperature and interface thickness from a 1-D freely propagating flame; Section 3.2.2 gives its
+ * speed S_L and thickness delta_L = (T_max - T_min) / max dT/dx). From the current state, with
+ * column means over the fluid cells of each x column (y, z):
+ *   props[0] S_c, consumption speed (m/s): sum over fluid cells of (-omega_F / F_loc) dx /
+ *            (rho_u Y_F,u A), A = ny nz cross-section cells, rho_u = P_th W_u / (R T_in) and
+ *            Y_F,u = Y_in[fuel] the inlet state, omega_F the fuel rate of the Arrhenius law the
+ *            update uses and F_loc its thickening factor (the flame sensor's value at the
+ *            current state when the sensor is on), so that thickening leaves S_c unchanged;
+ *   props[1] delta_L (m), (T_max - T_min) / max |centred difference of the column-mean T|
+ *            (0 when the profile is flat);
+ *   props[2] x_f (m), first crossing of (T_min + T_max) / 2 from low x, linear between column
+ *            centres at x dx (-1 when there is none);
+ *   props[3] T_min, props[4] T_max (K) of the column means;
+ *   props[5] T_b, props[6 .. 6+K) Y_b: column means of the last column holding fluid.
+ * props: host array of 6 + n_species doubles. profile: NULL or host array [2 + n_species][nx] that
+ * receives the column means of T, of -omega_F / F_loc (kg/(m^3 s)) and of each Y_k (0 where a column holds
+ * no fluid). Thermal runs with Y_in[fuel] > 0; synchronises the stream. */
+lbm_status lbm_flame_properties(lbm_ctx* ctx, int fuel_species, double* props, double* profile);
 
 /* Checkpoint: bytes of device memory needed, save into / load from caller-owned device memory. */
 size_t lbm_state_bytes(const lbm_ctx* ctx);

@@ -8,3 +8,4 @@ fails when the library has not been built: there is no CPU fallback.
 from . import _lib  # noqa: F401  (loads libhlbm.so or raises)
 from .solver import Solver, from_workload  # noqa: F401
 from .adjoint import AdjointProblem, HybridStepFn  # noqa: F401
+from .flame1d import FlameSolution, free_flame  # noqa: F401

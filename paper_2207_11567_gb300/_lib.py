@@ -88,6 +88,8 @@ def _load():
         "lbm_stats_control": (C.c_int, [P, C.c_int, C.c_int]),
         "lbm_get_stats": (C.c_int, [P, P, C.c_int, C.POINTER(C.c_longlong)]),
         "lbm_flame_length": (C.c_int, [P, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]),
+        "lbm_flame_properties": (C.c_int, [P, C.c_int, P, P]),
+        "lbm_set_inlet": (C.c_int, [P, P, C.c_int]),
         "lbm_pth_integral_noalloc": (C.c_int, [P, P, P, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_double,
                                                C.c_double, P, P, C.c_char_p, C.c_size_t]),
     }
@@ -105,7 +107,8 @@ EXPORTED = ("lbm_init", "lbm_destroy", "lbm_last_error", "lbm_set_geometry", "lb
             "lbm_save_state", "lbm_load_state", "lbm_profile", "lbm_kernel_times", "lbm_kernel_bytes",
             "lbm_use_graphs", "lbm_pth_integral_noalloc", "lbm_adjoint_step", "lbm_fuel_objective",
             "lbm_initial_T_adjoint", "lbm_adjoint_segment", "lbm_set_wall_fractions",
-            "lbm_set_wall_links", "lbm_stats_control", "lbm_get_stats", "lbm_flame_length")
+            "lbm_set_wall_links", "lbm_stats_control", "lbm_get_stats", "lbm_flame_length",
+            "lbm_flame_properties", "lbm_set_inlet")
 
 
 class HLBMError(RuntimeError):

@@ -79,6 +79,11 @@ struct lbm_ctx {
   long long st_n = 0;
   bool st_on = false;
   double* fl_partials = nullptr;
+  // planar-flame properties: column means [rows][nx] and the property vector
+  double* flame_col = nullptr;
+  double* flame_props = nullptr;
+  // staging of pageable inlet velocities (dim * ny * nz doubles)
+  double* inlet_stage = nullptr;
   // profiling
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -498,6 +503,32 @@ void lbm_destroy(lbm_ctx* ctx) {
 
 const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+namespace {
+// Inlet-face velocities ([dim][ny nz] doubles) converted to the field type on the device. Input
+// the device can read in place is converted directly; pageable host memory goes through a
+// staging buffer the context keeps (cudaMemcpyAsync has taken the data when it returns).
+lbm_status set_inlet_impl(lbm_ctx* ctx, const double* inlet_u, int on_device) {
+  const size_t n = (size_t)ctx->D * ctx->cfg.ny * ctx->cfg.nz;
+  const double* src = on_device ? inlet_u : device_view(inlet_u);
+  if (!src) {
+    if (!ctx->inlet_stage && !(ctx->inlet_stage = (double*)dalloc(ctx, n * 8)))
+      return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+    CK(cudaMemcpyAsync(ctx->inlet_stage, inlet_u, n * 8, cudaMemcpyHostToDevice, ctx->st), "copy inlet");
+    src = ctx->inlet_stage;
+  }
+  if (ctx->f64) CK(launch_to_field<double>(src, (double*)ctx->inlet_u, n, ctx->st), "inlet kernel");
+  else CK(launch_to_field<float>(src, (float*)ctx->inlet_u, n, ctx->st), "inlet kernel");
+  return LBM_OK;
+}
+}  // namespace
+
+lbm_status lbm_set_inlet(lbm_ctx* ctx, const double* inlet_u, int on_device) {
+  if (!ctx || !inlet_u) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->have_geo) return fail(ctx, LBM_ERR_STATE, "set_geometry must come first");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  return set_inlet_impl(ctx, inlet_u, on_device);
+}
+
 lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* mask, const double* inlet_u, int on_device) {
   if (!ctx || !mask) return fail(ctx, LBM_ERR_ARG, "null argument");
   if (ctx->allocs.empty()) return fail(ctx, LBM_ERR_STATE, "context not initialised");
@@ -507,26 +538,8 @@ lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* mask, const double* inl
   CK(cudaMemcpyAsync(ctx->mask, mask, N, kind, ctx->st), "copy mask");
   const size_t nf = (size_t)ctx->cfg.ny * ctx->cfg.nz;
   if (inlet_u) {
-    // convert the face velocities to the field type on the device
-    double* tmp = (double*)dalloc(ctx, ctx->D * nf * 8);
-    if (!tmp) return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
-    CK(cudaMemcpyAsync(tmp, inlet_u, ctx->D * nf * 8, kind, ctx->st), "copy inlet");
-    if (ctx->f64) {
-      CK(cudaMemcpyAsync(ctx->inlet_u, tmp, ctx->D * nf * 8, cudaMemcpyDeviceToDevice, ctx->st), "copy inlet");
-    } else {
-      std::vector<double> h(ctx->D * nf);
-      std::vector<float> hf(ctx->D * nf);
-      CK(cudaMemcpyAsync(h.data(), tmp, ctx->D * nf * 8, cudaMemcpyDeviceToHost, ctx->st), "copy inlet");
-      CK(cudaStreamSynchronize(ctx->st), "sync");
-      for (size_t i = 0; i < h.size(); ++i) hf[i] = (float)h[i];
-      CK(cudaMemcpyAsync(ctx->inlet_u, hf.data(), ctx->D * nf * 4, cudaMemcpyHostToDevice, ctx->st), "copy inlet");
-      CK(cudaStreamSynchronize(ctx->st), "sync");
-    }
-    CK(cudaStreamSynchronize(ctx->st), "sync");
-    // release the staging buffer
-    ctx->allocs.pop_back();
-    if (ctx->cfg.free) ctx->cfg.free(tmp, ctx->cfg.alloc_user);
-    else cudaFree(tmp);
+    lbm_status st = set_inlet_impl(ctx, inlet_u, on_device);
+    if (st != LBM_OK) return st;
   }
   CK(launch_links(ctx->D, ctx->geo, ctx->mask, ctx->links, ctx->st), "links kernel");
   CK(launch_stencil_words(ctx->D, ctx->geo, ctx->mask, ctx->sword, ctx->st), "stencil words kernel");
@@ -1286,6 +1299,39 @@ lbm_status lbm_flame_length(lbm_ctx* ctx, double level, double T_u, double T_b, 
   double t = 0.0;
   for (double v : h) t += v;
   *length = t;
+  return LBM_OK;
+}
+
+lbm_status lbm_flame_properties(lbm_ctx* ctx, int fuel_species, double* props, double* profile) {
+  if (!ctx || !props) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "set_fields must come first");
+  if (!ctx->cfg.thermal || fuel_species < 0 || fuel_species >= ctx->K)
+    return fail(ctx, LBM_ERR_ARG, "flame properties need a thermal run and a valid fuel index");
+  const double Y_Fu = ctx->cfg.Y_in[fuel_species];
+  if (!(Y_Fu > 0.0)) return fail(ctx, LBM_ERR_ARG, "the inlet mixture holds no fuel");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  const size_t nx = ctx->cfg.nx, rows = (size_t)flame_col_rows();
+  if (!ctx->flame_col && !(ctx->flame_col = (double*)dalloc(ctx, rows * nx * 8)))
+    return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+  if (!ctx->flame_props && !(ctx->flame_props = (double*)dalloc(ctx, (6 + LBM_MAX_SPECIES) * 8)))
+    return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+  const double rho_u_per_P = ctx->W_in / (R_GAS * ctx->cfg.T_in);
+  const double dx = ctx->cfg.dx;
+  if (ctx->f64)
+    CK(launch_flame_properties<double>(make_fd_args<double>(ctx, ctx->cur), fuel_species, rho_u_per_P, Y_Fu, dx,
+                                       ctx->flame_col, ctx->flame_props, ctx->st),
+       "flame properties");
+  else
+    CK(launch_flame_properties<float>(make_fd_args<float>(ctx, ctx->cur), fuel_species, rho_u_per_P, Y_Fu, dx,
+                                      ctx->flame_col, ctx->flame_props, ctx->st),
+       "flame properties");
+  CK(cudaMemcpyAsync(props, ctx->flame_props, (6 + ctx->K) * 8, cudaMemcpyDeviceToHost, ctx->st), "copy");
+  if (profile) {
+    // rows T, -omega_F, Y_k of the column means (the fluid-count row is not returned)
+    CK(cudaMemcpyAsync(profile, ctx->flame_col + nx, (2 + ctx->K) * nx * 8, cudaMemcpyDeviceToHost, ctx->st),
+       "copy");
+  }
+  CK(cudaStreamSynchronize(ctx->st), "sync");
   return LBM_OK;
 }
 

@@ -67,4 +67,10 @@ cudaError_t launch_stats(int N, int nf, const uint32_t* links, const R* u, int D
 template <typename R>
 cudaError_t launch_flame_length(const Geo& g, const uint32_t* links, const R* T, double T_u, double T_b, double level,
                                 double* partials, cudaStream_t st);
+// flame.cu: inlet conversion and planar-flame properties
+template <typename R> cudaError_t launch_to_field(const double* src, R* dst, size_t n, cudaStream_t st);
+int flame_col_rows();
+template <typename R>
+cudaError_t launch_flame_properties(const FDArgs<R>& a, int fuel, double rho_u_per_P, double Y_Fu, double dx,
+                                    double* col, double* props, cudaStream_t st);
 }  // namespace hlbm

@@ -91,6 +91,16 @@ class Solver:
             _check(self.ctx, L.lib.lbm_set_geometry(self.ctx, m.ctypes.data_as(C.c_void_p), ptr, 0))
         del keep
 
+    def set_inlet(self, inlet_u):
+        """Replace the inlet-face velocities [dim][ny nz] (lattice units) between steps
+        (lbm_set_inlet); fields and captured graphs stay."""
+        keep, ptr = _as_c_double(inlet_u)
+        if keep.size != self.N // self.cfg["nx"] * self.dim:
+            raise ValueError("inlet size")
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_set_inlet(self.ctx, ptr, 0))
+        del keep
+
     def set_wall_fractions(self, q):
         """Interpolated bounce-back: q [Q][N] wall fraction per bounce-back link (0.5 half-way),
         or None to clear (lbm_set_wall_fractions). Call after set_geometry."""
@@ -215,6 +225,25 @@ class Solver:
         with torch.cuda.device(self.device):
             _check(self.ctx, L.lib.lbm_flame_length(self.ctx, float(level), float(T_u), float(T_b), C.byref(out)))
         return out.value
+
+    def flame_properties(self, fuel=0, profile=False):
+        """Planar flame along x (lbm_flame_properties): dict with S_c (m/s), delta_L (m), x_f (m),
+        T_min, T_max, T_b and Y_b [K]; with profile=True also the column means T, w_F (fuel
+        consumption rate -omega_F, kg/(m^3 s)) and Y [K][nx]."""
+        K = len(self.cfg["species"])
+        nx = self.cfg["nx"]
+        props = np.zeros(6 + K)
+        prof = np.zeros((2 + K, nx)) if profile else None
+        with torch.cuda.device(self.device):
+            self._after_torch()
+            _check(self.ctx, L.lib.lbm_flame_properties(
+                self.ctx, int(fuel), props.ctypes.data_as(C.c_void_p),
+                prof.ctypes.data_as(C.c_void_p) if profile else None))
+        out = {"S_c": props[0], "delta_L": props[1], "x_f": props[2], "T_min": props[3], "T_max": props[4],
+               "T_b": props[5], "Y_b": props[6:].copy()}
+        if profile:
+            out.update({"T": prof[0].copy(), "w_F": prof[1].copy(), "Y": prof[2:].copy()})
+        return out
 
     # ---------------------------------------------------------------------- checkpoints
     def state_bytes(self):

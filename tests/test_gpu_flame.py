@@ -1,0 +1,118 @@
+"""Planar-flame properties (lbm_flame_properties) and the 1-D free-flame tool on the GPU.
+
+* Parity: the GPU's properties of its own run against the FP64 oracle's properties of the oracle
+  run (same seeded inputs): FP64 to round-off, including a one-cell-high channel and a channel
+  with a solid block; FP32 consumption speed within 1% of the FP64 oracle.
+* The tool (free_flame) against physics, properties that hold at any size: the burnt side
+  reaches the closed-form adiabatic temperature of complete combustion (unity Lewis numbers,
+  constant c_p), the lean flame burns all its fuel, mass flux is continuous across the steady
+  flame (rho_u S_L = rho_b u_b), and thickening by F keeps S_L while delta_L grows about F times.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.parity import oracle_run
+
+pytestmark = pytest.mark.gpu
+
+R_GAS = 8.314462618
+
+
+def _oracle_props(o, st, fuel=0):
+    from oracle.flame import flame_properties
+    return flame_properties(o.p, o.grid, st["T"].numpy(), st["Y"].numpy(), float(st["P_th"]), fuel)
+
+
+def _gpu_props(wl, steps, fuel=0):
+    from paper_2207_11567_gb300 import from_workload
+    s = from_workload(wl)
+    s.step(steps)
+    g = s.flame_properties(fuel, profile=True)
+    s.close()
+    return g
+
+
+def _rel(a, b, scale=None):
+    return abs(a - b) / (abs(b) if scale is None else scale)
+
+
+@pytest.mark.parametrize("ny,solid", [(1, False), (4, True), (8, False)])
+def test_flame_properties_f64_match_oracle(ny, solid):
+    wl = W.generate.flame_2d(nx=128, ny=ny, storage="f64", seed=2)
+    if solid:
+        m = wl.mask.reshape(ny, 128).copy()
+        m[1:3, 90:92] = 1  # a block in the burnt gas: column means over fluid cells only
+        wl.mask = m.reshape(-1)
+    o, st = oracle_run(wl, 300)
+    ref = _oracle_props(o, st)
+    g = _gpu_props(wl, 300)
+    dx = wl.cfg["dx"]
+    assert _rel(g["S_c"], ref["S_c"]) < 1e-10, (g["S_c"], ref["S_c"])
+    assert _rel(g["delta_L"], ref["delta_L"]) < 1e-10
+    assert abs(g["x_f"] - ref["x_f"]) < 1e-10 * dx
+    for k in ("T_min", "T_max", "T_b"):
+        assert _rel(g[k], ref[k]) < 1e-13, k
+    assert np.abs(g["Y_b"] - ref["Y_b"]).max() < 1e-13
+    assert np.abs(g["T"] - ref["T"]).max() < 1e-12 * ref["T"].max()
+    assert np.abs(g["Y"] - ref["Y"]).max() < 1e-13
+    assert np.abs(g["w_F"] - ref["w_F"]).max() < 1e-10 * np.abs(ref["w_F"]).max()
+
+
+def test_flame_speed_f32_within_one_percent_of_f64_oracle():
+    """The 256 x 8 planar flame after 600 steps in FP32 (populations and arithmetic) against the
+    FP64 oracle: consumption speed within 1%, thickness and position within 1%."""
+    wl64 = W.generate.flame_2d(nx=256, ny=8, storage="f64", seed=0)
+    o, st = oracle_run(wl64, 600)
+    ref = _oracle_props(o, st)
+    g = _gpu_props(W.generate.flame_2d(nx=256, ny=8, storage="f32", seed=0), 600)
+    assert _rel(g["S_c"], ref["S_c"]) < 1e-2, (g["S_c"], ref["S_c"])
+    assert _rel(g["delta_L"], ref["delta_L"]) < 1e-2
+    assert _rel(g["x_f"], ref["x_f"]) < 1e-2
+
+
+def _closed_form_T_ad(names, phi, T_u, cp):
+    """Complete lean combustion at constant pressure with constant c_p."""
+    thermo = W.configs._THERMO
+    Yu = W.mixture_phi(names, phi)
+    Yb = W.burnt_mixture(names, phi)
+    hf = [thermo[n][1] / thermo[n][0] for n in names]
+    return T_u + sum(h * (a - b) for h, a, b in zip(hf, Yu, Yb)) / cp
+
+
+def _free(F, storage="f64", nx=256, tol=2e-3):
+    from paper_2207_11567_gb300 import from_workload
+    from paper_2207_11567_gb300.flame1d import free_flame
+    wl = W.generate.flame_2d(nx=nx, ny=1, storage=storage, seed=0, width_cells=20.0 * F)
+    wl.cfg["thicken_F"] = F
+    s = from_workload(wl)
+    sol = free_flame(s, chunk=200, tol=tol, max_steps=300000)
+    u_b = s.fields()["u"][0].reshape(-1)[nx - 2]
+    s.close()
+    return wl, sol, u_b
+
+
+def test_free_flame_burnt_state_and_mass_flux():
+    wl, sol, u_b = _free(1.0)
+    assert sol.converged, sol.history[-5:]
+    names = W.SPECIES["4sp"]
+    T_ad = _closed_form_T_ad(names, 0.83, wl.cfg["T_in"], wl.cfg["cp"])
+    assert _rel(sol.T_b, T_ad) < 1e-3, (sol.T_b, T_ad)
+    assert sol.Y_b[0] < 1e-6 * wl.cfg["Y_in"][0]
+    # steady flame: rho_u S_L = rho_b u_b (ideal gas at P_th, molar masses of both states)
+    Wm = lambda Y: 1.0 / sum(y / s["W"] for y, s in zip(Y, wl.cfg["species"]))
+    ratio = (Wm(wl.cfg["Y_in"]) / wl.cfg["T_in"]) / (Wm(sol.Y_b) / sol.T_b)
+    S_lat = sol.S_L * wl.cfg["dt"] / wl.cfg["dx"]
+    assert _rel(u_b, S_lat * ratio) < 2e-2, (u_b, S_lat * ratio)
+
+
+def test_thickening_keeps_flame_speed():
+    """Thickened flame (Section 3.2.2 uses a factor 6): diffusion times F, rates divided by F, so S_L
+    stays and delta_L grows F times; checked for F = 4 against F = 1 on a grid where both are
+    resolved (the F = 1 flame spans only a few cells, so its discretisation error decides the
+    tolerance)."""
+    _, s1, _ = _free(1.0)
+    _, s4, _ = _free(4.0)
+    assert s1.converged and s4.converged
+    assert _rel(s4.S_L, s1.S_L) < 0.05, (s1.S_L, s4.S_L)
+    assert 3.0 < s4.delta_L / s1.delta_L < 5.0, (s1.delta_L, s4.delta_L)

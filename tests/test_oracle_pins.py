@@ -473,3 +473,72 @@ def test_flame_length_straight_line_and_circle():
     # above-level corners are cut off, each by a segment between the edge midpoints at 0.4 / 0.6
     Ls = flame_length(sad, np.ones((2, 2), bool), 0.6)
     assert abs(Ls - 2 * np.hypot(0.4, 0.4)) < 1e-12
+
+
+# ----------------------------------------------------------------------- planar flame
+def _flame_grid(nx, ny, mask=None):
+    cfg = W.generate._base_cfg(2, nx, ny, 1, "f64")
+    cfg["bc"] = {"x": ("inlet", "outlet"), "y": ("periodic", "periodic")}
+    return geo.Grid(cfg, np.zeros(nx * ny, np.uint8) if mask is None else mask)
+
+
+def test_flame_thickness_and_position_of_tanh_profile():
+    """T = T_u + dT (1 + tanh((x - x0) / w)) / 2 has max slope dT / (2 w), so delta_L -> 2 w with a
+    second-order error as dx -> 0 (centred differences). With x0 at the middle of the columns
+    (on a column centre for an odd count, midway between two for an even one) the sampled profile
+    is odd about x0, so the mid temperature of its end values is crossed exactly at x_f = x0;
+    T_min and T_max are the end columns. Solid cells, whatever their T, are left out of the
+    column means."""
+    from oracle.flame import column_means, profile_properties
+    Tu, dT, w = 300.0, 1600.0, 4.0e-4
+    errs = []
+    for nx in (40, 80, 160):
+        dx = 8.0 * w / nx
+        for ncol in (nx, nx + 1):
+            x0 = 0.5 * (ncol - 1) * dx
+            x = (np.arange(ncol * 3) % ncol) * dx
+            T = Tu + dT * 0.5 * (1.0 + np.tanh((x - x0) / w))
+            Tm, n = column_means(_flame_grid(ncol, 3), T)
+            delta, xf, Tmin, Tmax = profile_properties(Tm, n, dx)
+            assert abs(xf - x0) < 1e-12 * x0
+            assert Tmin == Tm[0] and Tmax == Tm[-1]
+        errs.append(abs(delta - 2 * w) / (2 * w))
+    assert errs[2] < 2e-3 and errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, errs
+    # a solid cell with a wild temperature in column 7 changes nothing
+    nx = 40
+    mask = np.zeros(nx * 3, np.uint8)
+    mask[7 + nx] = 1
+    x = (np.arange(nx * 3) % nx) * 1.0
+    T = 300.0 + 10.0 * x
+    T_bad = T.copy()
+    T_bad[7 + nx] = 1e6
+    a, na = column_means(_flame_grid(nx, 3), T)
+    b, nb_ = column_means(_flame_grid(nx, 3, mask), T_bad)
+    assert np.array_equal(a, b) and nb_[7] == 2 and na[7] == 3
+
+
+@pytest.mark.parametrize("F", [1.0, 4.0])
+def test_consumption_speed_is_the_fuel_source_of_the_update(F):
+    """Uniform fresh mixture at the inlet state (rho = rho_u), at rest in a periodic box: one
+    explicit update changes Y_F by dY = dt omega_F / (rho F) in every cell (no transport), so the
+    consumption speed of that state is S_c = -dY nx dx / (dt Y_F,u), whatever the thickening
+    factor F. Checks the dx, cross-section, rho_u, Y_F,u, sign and 1/F factors of S_c against
+    the update's own source term."""
+    from oracle.flame import flame_properties
+    names = W.SPECIES["6sp"]
+    nx, ny, dx, dt, T0 = 12, 3, 1e-4, 5e-8, 1500.0
+    Yu = W.mixture_phi(names, 0.83)
+    cfg = W.generate._base_cfg(2, nx, ny, 1, "f64")
+    cfg.update({"bc": {"x": ("periodic", "periodic"), "y": ("periodic", "periodic")}, "dx": dx, "dt": dt,
+                "nu_ref": 1.5e-5, "thermal": True, "species": W.configs.species(names),
+                "reactions": W.chemistry_2step(), "T_in": T0, "Y_in": Yu, "thicken_F": F})
+    p = Params(cfg)
+    grid = geo.Grid(cfg, np.zeros(nx * ny, np.uint8))
+    T = torch.full((nx * ny,), T0, dtype=f64)
+    Y = torch.tensor(Yu, dtype=f64)[:, None].repeat(1, nx * ny)
+    u = torch.zeros(2, nx * ny, dtype=f64)
+    _, Y1, _, _ = fdm.fd_update(p, grid, geo.FDNeighbours(grid), T, Y, u, u, p.P_th0, 0.0)
+    dY = (Y1[0] - Y[0]).numpy()
+    assert np.ptp(dY) <= 1e-14 * abs(dY).max() and dY[0] < 0
+    S = flame_properties(p, grid, T.numpy(), Y.numpy(), p.P_th0, 0)["S_c"]
+    assert abs(S - (-dY[0] * nx * dx / (dt * Yu[0]))) < 1e-12 * S
