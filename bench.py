@@ -339,6 +339,41 @@ def small_bench(args):
     print(json.dumps(line))
 
 
+def flame_tool_bench(args):
+    """The 1-D free-flame tool on the planar flame's mixture (one-step chemistry, 4 species,
+    phi = 0.83, 300 K): a 256 x 1 channel run until the consumption speed is steady, with the
+    thickening factors 1 and 4, FP32. Reports the time to the converged flame (device steps and
+    the tool's host control every 200 steps, wall clock) and the flame it finds."""
+    import torch
+    import workloads as W
+    from paper_2207_11567_gb300 import from_workload
+    from paper_2207_11567_gb300.flame1d import free_flame
+    torch.cuda.set_device(0)
+    runs = {}
+    for F in (1.0, 4.0):
+        wl = W.generate.flame_2d(nx=256, ny=1, storage="f32", seed=0, width_cells=20.0 * F)
+        wl.cfg["thicken_F"] = F
+        s = from_workload(wl)
+        s.step(max(3, args.warmup))
+        s.synchronize()
+        t0 = time.perf_counter()
+        sol = free_flame(s, chunk=200, max_steps=400000)
+        s.synchronize()
+        wall = time.perf_counter() - t0
+        s.close()
+        runs[f"F={F:g}"] = {"converged": sol.converged, "steps": sol.steps, "seconds": wall,
+                            "steps_per_s": sol.steps / wall, "S_L_m_s": sol.S_L, "delta_L_m": sol.delta_L,
+                            "T_b_K": sol.T_b, "Y_b": [float(v) for v in sol.Y_b]}
+    total = sum(r["seconds"] for r in runs.values())
+    line = {"metric": "1-D free flame: wall time to a converged flame (F = 1 and F = 4)", "value": total,
+            "unit": "s", "n_gpus": 1, "steps": sum(r["steps"] for r in runs.values()), "warmup": max(3, args.warmup),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "flame1d_tool", "grid": [256, 1], "chunk": 200,
+                       "mixture": "CH4/air phi 0.83, one-step chemistry, unity Lewis numbers"},
+            "runs": runs}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,7 +387,8 @@ def main():
                     help="time one storage variant only (profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=["c4_swirl_reactive_3d", "c3_swirl_cold_3d",
-                                                             "c2_chamber_2d", "c1_flame_2d", "c5_adjoint_2d"],
+                                                             "c2_chamber_2d", "c1_flame_2d", "c5_adjoint_2d",
+                                                             "flame1d_tool"],
                     help="benchmark configuration (default: the reactive swirl burner)")
     ap.add_argument("--no-fd-check", action="store_true", help="c5: skip the FP64 finite-difference check")
     ap.add_argument("--fd-dirs", type=int, default=16, help="c5: directions of the finite-difference check")
@@ -364,6 +400,9 @@ def main():
     args = ap.parse_args()
     if args.workload == "c5_adjoint_2d" and args.impl == "ours":
         adjoint_bench(args)
+        return
+    if args.workload == "flame1d_tool" and args.impl == "ours":
+        flame_tool_bench(args)
         return
     if args.workload in ("c1_flame_2d", "c2_chamber_2d") and args.impl == "ours" and not args.only:
         small_bench(args)

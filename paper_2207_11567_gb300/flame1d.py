@@ -9,13 +9,18 @@ gas entering at x = 0 with the inlet velocity, burnt gas leaving at the high-x o
 A free flame moves against the fresh gas at S_L; to keep it inside the channel the inlet
 velocity follows the measured consumption speed S_c (lbm_flame_properties), with a
 proportional correction that pulls the flame position x_f back to a target:
-    u_in = S_c - gain (x_f - x_target) / (chunk dt)        (velocities in m/s)
-applied every ``chunk`` steps (lbm_set_inlet). In the flame's frame the fresh gas then arrives
-at S_c, and the position error decays by the factor (1 - gain) per chunk. The run has converged
-when, over the last ``window`` chunks and at least one flame time delta_L / S_c, S_c varies by
-less than ``tol`` of its mean and x_f stays within one cell of the target (a transient that
-decays on the flame time then leaves an error of a few tol). Every step and every measurement runs in the library's kernels;
-this module only chooses the inlet velocity and keeps the history.
+    u_in = <S_c> - gain (x_f - x_target) / tau_f                (velocities in m/s)
+applied every ``chunk`` steps (lbm_set_inlet), with <S_c> the mean consumption speed over the
+last flame time tau_f = delta_L / S_c. With the fresh gas arriving at <S_c> the position error
+decays as exp(-gain t / tau_f): slow against the flame's own response (about one flame time),
+so that the loop does not ring, and blind to the small oscillation of S_c as a thin front
+crosses grid cells. The run has converged when the means of S_c over the last two windows of one
+flame time (at least ``window`` chunks each) differ by less than ``tol``, x_f has stayed within
+two cells of the target over both, and the gas burnt since the start has swept the channel behind
+the flame twice (burnt-gas velocity estimated as <S_c> T_max / T_min), so that the outlet holds
+the flame's own burnt state; S_L is the mean of the last window. Every step and every
+measurement runs in the library's kernels; this module only chooses the inlet velocity and
+keeps the history.
 """
 from dataclasses import dataclass, field
 
@@ -50,7 +55,7 @@ class FlameSolution:
         return T, Y
 
 
-def free_flame(solver, fuel=0, x_target=None, chunk=200, gain=0.5, tol=2e-3, window=5, max_steps=400000,
+def free_flame(solver, fuel=0, x_target=None, chunk=200, gain=0.2, tol=2e-3, window=5, max_steps=400000,
                u_max=None):
     """Run the planar flame held by ``solver`` (a ``Solver`` whose fields are already set: inlet at
     low x, outlet at high x, periodic across) until its consumption speed is steady.
@@ -73,6 +78,7 @@ def free_flame(solver, fuel=0, x_target=None, chunk=200, gain=0.5, tol=2e-3, win
     hist = []
     steps = 0
     converged = False
+    S_L = p["S_c"]
     while steps < max_steps:
         solver.step(chunk)
         steps += chunk
@@ -82,17 +88,24 @@ def free_flame(solver, fuel=0, x_target=None, chunk=200, gain=0.5, tol=2e-3, win
             raise RuntimeError(f"flame left the channel or went out after {steps} steps (x_f={xf}, S_c={S})")
         if S <= 0 or p["T_max"] - p["T_min"] < 1e-3 * p["T_min"]:
             raise RuntimeError(f"flame extinguished after {steps} steps")
-        u = float(np.clip(S - gain * (xf - x_target) / (chunk * dt), 0.0, u_max))
+        hist.append((steps, S, xf, 0.0))
+        tau = max(p["delta_L"], dx) / S
+        L = max(window, int(np.ceil(tau / (chunk * dt))))
+        S_bar = float(np.mean([h[1] for h in hist[-L:]]))
+        u = float(np.clip(S_bar - gain * (xf - x_target) / tau, 0.0, u_max))
+        hist[-1] = (steps, S, xf, u)
         solver.set_inlet(np.concatenate([np.full(n_face, u * lat), np.zeros((solver.dim - 1) * n_face)]))
-        hist.append((steps, S, xf, u))
-        span = max(window, int(np.ceil(p["delta_L"] / S / (chunk * dt))) + 1)
-        if len(hist) >= span:
-            last = np.array([h[1] for h in hist[-span:]])
-            pos = np.array([h[2] for h in hist[-span:]])
-            if np.ptp(last) <= tol * abs(last.mean()) and np.abs(pos - x_target).max() <= dx:
+        if len(hist) >= 2 * L:
+            a = np.mean([h[1] for h in hist[-L:]])
+            b = np.mean([h[1] for h in hist[-2 * L:-L]])
+            pos = np.array([h[2] for h in hist[-2 * L:]])
+            flushed = steps * dt * a * p["T_max"] / p["T_min"] >= 2.0 * ((nx - 1) * dx - xf)
+            if abs(a - b) <= tol * a and np.abs(pos - x_target).max() <= 2 * dx and flushed:
                 converged = True
+                S_L = float(a)
                 break
+        S_L = S_bar
     p = solver.flame_properties(fuel, profile=True)
-    return FlameSolution(S_L=p["S_c"], delta_L=p["delta_L"], T_b=p["T_b"], Y_b=p["Y_b"], T_u=cfg["T_in"],
+    return FlameSolution(S_L=S_L, delta_L=p["delta_L"], T_b=p["T_b"], Y_b=p["Y_b"], T_u=cfg["T_in"],
                          x_f=p["x_f"], x=np.arange(nx) * dx, T=p["T"], Y=p["Y"], w_F=p["w_F"], steps=steps,
                          converged=converged, history=hist)

@@ -47,8 +47,10 @@ def test_control_holds_the_flame_and_converges_to_its_speed():
     assert sol.converged
     # the scripted transient decays on about one flame time: a few tol of error remain
     assert abs(sol.S_L - f.S) < 3e-3 * f.S
-    assert abs(sol.x_f - 3e-3) <= f.cfg["dx"]
-    assert abs(f.u - f.S) < 2e-3 * f.S  # the fresh gas arrives at the flame speed
+    assert abs(sol.x_f - 3e-3) <= 2 * f.cfg["dx"]
+    # the fresh gas arrives at the flame speed, up to the correction of a position error of at
+    # most two cells (gain 0.2 over one flame time delta_L / S)
+    assert abs(f.u - f.S) <= 0.2 * 2 * f.cfg["dx"] / (4e-4 / f.S) + 3e-3 * f.S
     assert len(sol.history) == sol.steps // 100
 
 
