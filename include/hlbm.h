@@ -227,6 +227,32 @@ lbm_status lbm_flame_length(lbm_ctx* ctx, double level, double T_u, double T_b, 
  * no fluid). Thermal runs with Y_in[fuel] > 0; synchronises the stream. */
 lbm_status lbm_flame_properties(lbm_ctx* ctx, int fuel_species, double* props, double* profile);
 
+/* Probes (Section 3.2 finds the precessing vortex core from the pressure recorded at points and
+ * its spectrum). After every `interval`-th step the values u_x, u_y[, u_z], P_h[, T] (nf = dim + 1
+ * [+ 1 thermal]) of each probe cell are appended to a ring of `capacity` samples; when it is full
+ * the oldest sample is overwritten. cells: host array of n_probes fluid cell indices (LBM_ERR_ARG
+ * for a solid or out-of-range cell). n_probes = 0 stops recording. Recording steps launch directly
+ * (no graphs) and write P_h. Resets the sample count; synchronises the stream. */
+lbm_status lbm_set_probes(lbm_ctx* ctx, int n_probes, const int* cells, long long capacity, int interval);
+
+/* The recorded samples, oldest first: dst [n_samples][n_probes][nf] doubles (may be NULL to query
+ * the count); n_samples (may be NULL) receives min(samples taken, capacity). Synchronises the
+ * stream when dst is host memory. */
+lbm_status lbm_get_probes(lbm_ctx* ctx, double* dst, int dst_on_device, long long* n_samples);
+
+/* Welch estimate of the one-sided power spectral density of the device series x[i * stride],
+ * i < n, sampled every dt seconds: segments of seg_len samples (even, >= 4, <= n) advancing by
+ * seg_len / 2, each with its mean removed and the periodic Hann window (1 - cos(2 pi j / seg_len))/2
+ * applied; |DFT|^2 averaged over the segments, times dt / sum(window^2), doubled except at
+ * frequency 0 and seg_len / 2. psd: host array of seg_len / 2 + 1 doubles, bin f at frequency
+ * f / (seg_len dt) Hz, in units^2 / Hz. Synchronises the stream. */
+lbm_status lbm_welch_psd(lbm_ctx* ctx, const double* x, long long n, long long stride, double dt, int seg_len,
+                         double* psd);
+
+/* lbm_welch_psd of one probe's field (0 .. nf-1 in the order above) over the recorded samples,
+ * oldest first, dt = interval * cfg.dt. */
+lbm_status lbm_probe_spectrum(lbm_ctx* ctx, int probe, int field, int seg_len, double* psd);
+
 /* Checkpoint: bytes of device memory needed, save into / load from caller-owned device memory. */
 size_t lbm_state_bytes(const lbm_ctx* ctx);
 lbm_status lbm_save_state(lbm_ctx* ctx, void* dst_device);

@@ -9,7 +9,11 @@ Test infrastructure like the rest of the oracle.
   the crossing is placed by linear interpolation; two crossings make one segment; four (a
   saddle) make two, paired by the value at the square's centre (mean of the corners): centre
   above the level joins each crossing to the neighbouring crossing that keeps the above-level
-  corners connected.
+  corners connected;
+* probe spectra: Welch's estimate of the one-sided power spectral density of a sampled series
+  (segments of L samples advancing by L/2, mean removed, periodic Hann window
+  w_j = (1 - cos(2 pi j / L)) / 2, |DFT|^2 averaged over segments, times dt / sum w^2, doubled
+  except at 0 and L/2), with numpy's FFT for the DFT.
 """
 import math
 
@@ -58,3 +62,20 @@ def flame_length(c, fluid, level):
                     p, q = pts[(k - 1) % 4], pts[k]
                     total += math.hypot(p[0] - q[0], p[1] - q[1])
     return total
+
+
+def welch_psd(x, dt, L):
+    """One-sided PSD (units^2/Hz) at the frequencies f / (L dt), f = 0 .. L/2."""
+    x = np.asarray(x, dtype=np.float64)
+    hop = L // 2
+    nseg = (x.size - L) // hop + 1
+    j = np.arange(L)
+    w = 0.5 - 0.5 * np.cos(2.0 * np.pi * j / L)
+    acc = np.zeros(L // 2 + 1)
+    for s in range(nseg):
+        seg = x[s * hop: s * hop + L]
+        X = np.fft.rfft(w * (seg - seg.mean()))
+        acc += np.abs(X) ** 2
+    psd = acc / nseg * dt / (w * w).sum()
+    psd[1:-1] *= 2.0
+    return np.arange(L // 2 + 1) / (L * dt), psd

@@ -84,6 +84,16 @@ struct lbm_ctx {
   double* flame_props = nullptr;
   // staging of pageable inlet velocities (dim * ny * nz doubles)
   double* inlet_stage = nullptr;
+  // probes: cells, ring buffer [cap][n][nf] of doubles, samples taken so far
+  int* pr_cells = nullptr;
+  double* pr_ring = nullptr;
+  int pr_n = 0, pr_nf = 0, pr_interval = 1;
+  long long pr_cap = 0, pr_count = 0;
+  size_t pr_ring_words = 0;
+  bool pr_on = false;
+  // spectrum workspace: segment means, PSD, ordered series
+  double* psd_ws = nullptr;
+  size_t psd_ws_n = 0;
   // profiling
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -675,13 +685,29 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
   if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "set_fields must come first");
   if (n_steps == 0) return LBM_OK;
   CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
-  if (ctx->st_on) {
-    // statistics: direct launches; a sampled step also writes P_h, then the accumulators update
+  if (ctx->st_on || ctx->pr_on) {
+    // statistics and probes: direct launches; a sampled step also writes P_h, then the
+    // accumulators update and the probe values are copied into the ring
     for (int k = 0; k < n_steps; ++k) {
-      const bool sample = (ctx->steps + 1) % ctx->st_interval == 0;
-      CK(enqueue_step(ctx, ctx->cur, sample || k == n_steps - 1), "step launch");
+      const bool sample = ctx->st_on && (ctx->steps + 1) % ctx->st_interval == 0;
+      const bool probe = ctx->pr_on && (ctx->steps + 1) % ctx->pr_interval == 0;
+      CK(enqueue_step(ctx, ctx->cur, sample || probe || k == n_steps - 1), "step launch");
       ctx->cur ^= 1;
       ++ctx->steps;
+      if (probe) {
+        const size_t row = (size_t)ctx->pr_n * ctx->pr_nf;
+        double* dst = ctx->pr_ring + (size_t)(ctx->pr_count % ctx->pr_cap) * row;
+        const int cur = ctx->cur;
+        if (ctx->f64)
+          CK(launch_probes<double>(ctx->pr_cells, ctx->pr_n, ctx->pr_nf, ctx->D, (int)ctx->N, (const double*)ctx->u,
+                                   (const double*)ctx->ph, (const double*)ctx->T[cur], dst, ctx->st),
+             "probes");
+        else
+          CK(launch_probes<float>(ctx->pr_cells, ctx->pr_n, ctx->pr_nf, ctx->D, (int)ctx->N, (const float*)ctx->u,
+                                  (const float*)ctx->ph, (const float*)ctx->T[cur], dst, ctx->st),
+             "probes");
+        ++ctx->pr_count;
+      }
       if (sample) {
         ++ctx->st_n;
         const int cur = ctx->cur;
@@ -1333,6 +1359,118 @@ lbm_status lbm_flame_properties(lbm_ctx* ctx, int fuel_species, double* props, d
   }
   CK(cudaStreamSynchronize(ctx->st), "sync");
   return LBM_OK;
+}
+
+lbm_status lbm_set_probes(lbm_ctx* ctx, int n_probes, const int* cells, long long capacity, int interval) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (!ctx->have_geo) return fail(ctx, LBM_ERR_STATE, "set_geometry must come first");
+  if (n_probes < 0 || (n_probes > 0 && (!cells || capacity < 1 || interval < 1)))
+    return fail(ctx, LBM_ERR_ARG, "n_probes >= 0, cells, capacity >= 1 and interval >= 1 needed");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  ctx->pr_on = false;
+  ctx->pr_count = 0;
+  ctx->pr_n = 0;
+  if (n_probes == 0) return LBM_OK;
+  std::vector<uint8_t> hm(ctx->N);
+  CK(cudaMemcpyAsync(hm.data(), ctx->mask, ctx->N, cudaMemcpyDeviceToHost, ctx->st), "copy mask");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  for (int i = 0; i < n_probes; ++i)
+    if (cells[i] < 0 || (size_t)cells[i] >= ctx->N || hm[cells[i]])
+      return fail(ctx, LBM_ERR_ARG, "probe cell " + std::to_string(i) + " is outside the grid or solid");
+  const int nf = ctx->D + 1 + (ctx->cfg.thermal ? 1 : 0);
+  const size_t words = (size_t)capacity * n_probes * nf;
+  if (words > ctx->pr_ring_words) {
+    // grow: an older, smaller ring stays with the context's allocations until lbm_destroy
+    if (!(ctx->pr_ring = (double*)dalloc(ctx, words * 8))) return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+    ctx->pr_ring_words = words;
+  }
+  if (!(ctx->pr_cells = (int*)dalloc(ctx, (size_t)n_probes * sizeof(int))))
+    return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+  CK(cudaMemcpyAsync(ctx->pr_cells, cells, (size_t)n_probes * sizeof(int), cudaMemcpyHostToDevice, ctx->st),
+     "copy probes");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  ctx->pr_n = n_probes;
+  ctx->pr_nf = nf;
+  ctx->pr_cap = capacity;
+  ctx->pr_interval = interval;
+  ctx->pr_on = true;
+  return LBM_OK;
+}
+
+namespace {
+// device scratch of at least n doubles for the spectrum calls
+double* psd_scratch(lbm_ctx* ctx, size_t n) {
+  if (ctx->psd_ws_n < n) {
+    double* p = (double*)dalloc(ctx, n * 8);
+    if (!p) return nullptr;
+    ctx->psd_ws = p;
+    ctx->psd_ws_n = n;
+  }
+  return ctx->psd_ws;
+}
+}  // namespace
+
+lbm_status lbm_get_probes(lbm_ctx* ctx, double* dst, int dst_on_device, long long* n_samples) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (!ctx->pr_n) return fail(ctx, LBM_ERR_STATE, "no probes set");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  const long long count = ctx->pr_count < ctx->pr_cap ? ctx->pr_count : ctx->pr_cap;
+  const long long first = ctx->pr_count < ctx->pr_cap ? 0 : ctx->pr_count % ctx->pr_cap;
+  const long long row = (long long)ctx->pr_n * ctx->pr_nf;
+  if (n_samples) *n_samples = count;
+  if (!dst || count == 0) return LBM_OK;
+  double* view = dst_on_device ? dst : (double*)device_view(dst);
+  double* out = view;
+  if (!view && !(out = psd_scratch(ctx, (size_t)(count * row)))) return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+  CK(launch_ring_order(ctx->pr_ring, ctx->pr_cap, first, count, row, out, ctx->st), "probe order");
+  if (!view)
+    CK(cudaMemcpyAsync(dst, out, (size_t)(count * row) * 8, cudaMemcpyDeviceToHost, ctx->st), "copy probes");
+  if (!dst_on_device) CK(cudaStreamSynchronize(ctx->st), "sync");
+  return LBM_OK;
+}
+
+namespace {
+lbm_status welch_impl(lbm_ctx* ctx, const double* x, long long n, long long stride, double dt, int seg_len,
+                      double* psd, size_t ws_offset) {
+  const int nseg = (int)((n - seg_len) / (seg_len / 2) + 1);
+  double* ws = psd_scratch(ctx, ws_offset + (size_t)nseg + seg_len / 2 + 1);
+  if (!ws) return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+  double* mean = ws + ws_offset;
+  double* dpsd = mean + nseg;
+  CK(launch_welch(x, stride, n, seg_len, dt, mean, dpsd, ctx->st), "spectrum");
+  CK(cudaMemcpyAsync(psd, dpsd, (size_t)(seg_len / 2 + 1) * 8, cudaMemcpyDeviceToHost, ctx->st), "copy");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  return LBM_OK;
+}
+bool bad_segment(long long n, int seg_len) { return seg_len < 4 || seg_len % 2 != 0 || n < seg_len; }
+}  // namespace
+
+lbm_status lbm_welch_psd(lbm_ctx* ctx, const double* x, long long n, long long stride, double dt, int seg_len,
+                         double* psd) {
+  if (!ctx || !x || !psd) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (bad_segment(n, seg_len) || stride < 1 || !(dt > 0.0))
+    return fail(ctx, LBM_ERR_ARG, "seg_len even and >= 4, n >= seg_len, stride >= 1, dt > 0");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  return welch_impl(ctx, x, n, stride, dt, seg_len, psd, 0);
+}
+
+lbm_status lbm_probe_spectrum(lbm_ctx* ctx, int probe, int field, int seg_len, double* psd) {
+  if (!ctx || !psd) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (!ctx->pr_n) return fail(ctx, LBM_ERR_STATE, "no probes set");
+  if (probe < 0 || probe >= ctx->pr_n || field < 0 || field >= ctx->pr_nf)
+    return fail(ctx, LBM_ERR_ARG, "probe or field index out of range");
+  const long long count = ctx->pr_count < ctx->pr_cap ? ctx->pr_count : ctx->pr_cap;
+  if (bad_segment(count, seg_len)) return fail(ctx, LBM_ERR_ARG, "seg_len even, >= 4 and <= the samples recorded");
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  const long long first = ctx->pr_count < ctx->pr_cap ? 0 : ctx->pr_count % ctx->pr_cap;
+  const long long row = (long long)ctx->pr_n * ctx->pr_nf;
+  const size_t words = (size_t)(count * row);
+  const int nseg = (int)((count - seg_len) / (seg_len / 2) + 1);
+  double* ws = psd_scratch(ctx, words + (size_t)nseg + seg_len / 2 + 1);
+  if (!ws) return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+  CK(launch_ring_order(ctx->pr_ring, ctx->pr_cap, first, count, row, ws, ctx->st), "probe order");
+  return welch_impl(ctx, ws + (size_t)probe * ctx->pr_nf + field, count, row, ctx->pr_interval * ctx->cfg.dt,
+                    seg_len, psd, words);
 }
 
 lbm_status lbm_use_graphs(lbm_ctx* ctx, int enable) {

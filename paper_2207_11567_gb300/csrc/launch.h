@@ -73,4 +73,12 @@ int flame_col_rows();
 template <typename R>
 cudaError_t launch_flame_properties(const FDArgs<R>& a, int fuel, double rho_u_per_P, double Y_Fu, double dx,
                                     double* col, double* props, cudaStream_t st);
+// probes.cu: probe series and Welch spectra
+template <typename R>
+cudaError_t launch_probes(const int* cells, int n, int nf, int D, int N, const R* u, const R* ph, const R* T,
+                          double* row, cudaStream_t st);
+cudaError_t launch_ring_order(const double* ring, long long cap, long long first, long long count, long long row,
+                              double* dst, cudaStream_t st);
+cudaError_t launch_welch(const double* x, long long stride, long long n, int L, double dt, double* mean_ws,
+                         double* psd, cudaStream_t st);
 }  // namespace hlbm

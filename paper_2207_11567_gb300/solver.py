@@ -226,6 +226,50 @@ class Solver:
             _check(self.ctx, L.lib.lbm_flame_length(self.ctx, float(level), float(T_u), float(T_b), C.byref(out)))
         return out.value
 
+    def set_probes(self, cells, capacity=65536, interval=1):
+        """Record u, P_h (and T) at the given fluid cells after every `interval`-th step into a
+        ring of `capacity` samples (lbm_set_probes); an empty list stops recording."""
+        c = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1))
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_set_probes(self.ctx, int(c.size), c.ctypes.data_as(C.c_void_p),
+                                                  int(capacity), int(interval)))
+        self._probe_count, self._probe_interval = int(c.size), int(interval)
+
+    def probes(self):
+        """Recorded samples, oldest first: array [n_samples][n_probes][nf], fields u_x, u_y[, u_z],
+        P_h[, T]."""
+        n = C.c_longlong()
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_get_probes(self.ctx, None, 0, C.byref(n)))
+            nf = self.dim + 1 + (1 if self.cfg.get("thermal") else 0)
+            out = np.empty(n.value * nf * self._probe_count, dtype=np.float64)
+            if out.size:
+                self._after_torch()
+                _check(self.ctx, L.lib.lbm_get_probes(self.ctx, out.ctypes.data_as(C.c_void_p), 0, C.byref(n)))
+        return out.reshape(n.value, -1, nf) if out.size else out.reshape(0, 0, nf)
+
+    def welch_psd(self, x, dt, seg_len, stride=1):
+        """Welch power spectral density of a device tensor x (float64, 1-D; every `stride`-th
+        element), lbm_welch_psd; returns (frequencies in Hz, psd)."""
+        if x.dtype != torch.float64 or not x.is_cuda:
+            raise ValueError("x must be a float64 CUDA tensor")
+        n = (x.numel() + stride - 1) // stride
+        psd = np.empty(seg_len // 2 + 1)
+        with torch.cuda.device(self.device):
+            self._after_torch()
+            _check(self.ctx, L.lib.lbm_welch_psd(self.ctx, C.c_void_p(x.data_ptr()), n, stride, float(dt),
+                                                 int(seg_len), psd.ctypes.data_as(C.c_void_p)))
+        return np.arange(psd.size) / (seg_len * dt), psd
+
+    def probe_spectrum(self, probe, field, seg_len):
+        """Welch spectrum of one probe's field over the recorded samples (lbm_probe_spectrum);
+        returns (frequencies in Hz, psd)."""
+        psd = np.empty(seg_len // 2 + 1)
+        with torch.cuda.device(self.device):
+            _check(self.ctx, L.lib.lbm_probe_spectrum(self.ctx, int(probe), int(field), int(seg_len),
+                                                      psd.ctypes.data_as(C.c_void_p)))
+        return np.arange(psd.size) / (seg_len * self.cfg["dt"] * self._probe_interval), psd
+
     def flame_properties(self, fuel=0, profile=False):
         """Planar flame along x (lbm_flame_properties): dict with S_c (m/s), delta_L (m), x_f (m),
         T_min, T_max, T_b and Y_b [K]; with profile=True also the column means T, w_F (fuel

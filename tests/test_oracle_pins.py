@@ -542,3 +542,31 @@ def test_consumption_speed_is_the_fuel_source_of_the_update(F):
     assert np.ptp(dY) <= 1e-14 * abs(dY).max() and dY[0] < 0
     S = flame_properties(p, grid, T.numpy(), Y.numpy(), p.P_th0, 0)["S_c"]
     assert abs(S - (-dY[0] * nx * dx / (dt * Yu[0]))) < 1e-12 * S
+
+
+def test_welch_psd_against_scipy_and_a_sinusoid():
+    """The oracle's Welch estimate equals scipy.signal.welch with the same choices (Hann window,
+    half overlap, constant detrend, density scaling, one-sided) to round-off. A cosine of amplitude
+    A on bin k puts its power A^2 / 2 into bins k-1, k, k+1 in the ratio 1 : 4 : 1 (its Hann-windowed
+    DFT is A L / 4 at k and -A L / 8 at k +- 1, and the density divides by sum w^2 = 3 L / 8), and
+    nothing elsewhere; white noise of variance s^2 has the flat density 2 s^2 dt."""
+    scipy_signal = pytest.importorskip("scipy.signal")
+    from oracle.stats import welch_psd
+    rng = np.random.default_rng(11)
+    dt, L = 1e-3, 256
+    x = rng.standard_normal(5000) + 0.3 * np.sin(2 * np.pi * 37.0 * np.arange(5000) * dt)
+    f, p = welch_psd(x, dt, L)
+    fs, ps = scipy_signal.welch(x, fs=1.0 / dt, window="hann", nperseg=L, noverlap=L // 2, detrend="constant",
+                                scaling="density", return_onesided=True)
+    assert np.allclose(f, fs, rtol=0, atol=1e-12) and np.allclose(p, ps, rtol=1e-12, atol=0)
+    k0, A = 20, 2.0
+    t = np.arange(8 * L) * dt
+    f, p = welch_psd(A * np.cos(2 * np.pi * k0 / (L * dt) * t + 0.4), dt, L)
+    df = 1.0 / (L * dt)
+    assert int(np.argmax(p)) == k0
+    assert abs(p[k0 - 1: k0 + 2].sum() * df - A * A / 2) < 1e-12
+    assert abs(p[k0] * df - A * A / 3) < 1e-12 and abs(p[k0 + 1] * df - A * A / 12) < 1e-12
+    assert p[: k0 - 2].max() < 1e-20 and p[k0 + 3:].max() < 1e-20
+    noise = rng.standard_normal(200000) * 0.5
+    f, p = welch_psd(noise, dt, L)
+    assert abs(p[1:-1].mean() - 2 * 0.25 * dt) < 0.02 * 2 * 0.25 * dt
