@@ -115,12 +115,16 @@ def _timed_steps(solver, steps, torch):
     return e0.elapsed_time(e1)
 
 
-def run_variant(wl, storage, steps, warmup, torch, profile_steps, stats=0):
+def run_variant(wl, storage, steps, warmup, torch, profile_steps, stats=0, probes=0):
     from paper_2207_11567_gb300 import from_workload
     wl.cfg["storage"] = storage
     s = from_workload(wl)
     if stats:
         s.stats_control(1, stats)
+    if probes:
+        import numpy as np
+        fluid = np.nonzero(np.asarray(wl.mask).reshape(-1) == 0)[0]
+        s.set_probes(fluid[np.linspace(0, fluid.size - 1, probes).astype(np.int64)], capacity=steps + warmup + 16)
     s.step(warmup)
     s.synchronize()
     ms = _timed_steps(s, steps, torch)
@@ -395,6 +399,8 @@ def main():
     ap.add_argument("--adj-steps", type=int, default=0, help="c5: steps K (default: the workload's 2000)")
     ap.add_argument("--stats", type=int, default=0,
                     help="with --only: sample running statistics every N steps during the timed steps")
+    ap.add_argument("--probes", type=int, default=0,
+                    help="with --only: record N probe cells after every step during the timed steps")
     ap.add_argument("--curved", action="store_true",
                     help="c3/c4: interpolated bounce-back on the injector cylinders and the exhaust cone")
     args = ap.parse_args()
@@ -445,7 +451,8 @@ def main():
         return W.make(args.workload)
 
     if args.only:
-        r = run_variant(make(), args.only, args.steps, args.warmup, torch, profile_steps=2, stats=args.stats)
+        r = run_variant(make(), args.only, args.steps, args.warmup, torch, profile_steps=2, stats=args.stats,
+                        probes=args.probes)
         print(json.dumps({"case": args.case, "storage": args.only, "ms_per_step": r["ms"] / args.steps,
                           "kernels": r["kernels"]}))
         return
