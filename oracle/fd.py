@@ -24,6 +24,16 @@ Readings (the paper gives no formulas for these):
   * Lambda (Eq. 3) uses the non-advective right-hand side: Lambda = N_T / T + sum (W/W_k) N_k.
   * Thermodynamic pressure: rho = P_th W / (R T); the energy equation gains the pressure work
     dP_th/(rho c_p) of the previous step.
+  * Variable heat capacities (option; the paper couples a thermochemistry library that is not
+    available): c_p,k(T) a polynomial per species, h_k(T) = h_f,k + integral of c_p,k from T0,
+    c_p = sum Y_k c_p,k. The temperature equation becomes
+        N_T = [sum_faces lambda_face (T_n - T) + F mu/Pr sum_k (c_p,k - c_p)/Le_k grad Y_k . grad T]
+              / (rho c_p) + dt (-sum_k h_k omega_k) / (rho c_p F) + dP/(rho c_p)
+    with lambda = F mu c_p / Pr per cell (face value the arithmetic mean; a ghost neighbour's c_p
+    from its ghost T and Y), centred gradients (phi(r+e) - phi(r-e))/2 of the ghost-extended
+    fields, and the species-enthalpy flux written with the diffusion fluxes relative to the
+    mass-averaged velocity (c_p,k - c_p), so that equal species heat capacities give back the
+    constant-c_p update exactly.
 """
 import math
 
@@ -74,6 +84,23 @@ def species_rates(p, q):
                 acc = acc + p.W[k] * nu * q[j]
         om.append(acc)
     return om
+
+
+def cp_species(p, k, T):
+    """c_p,k(T) [J/(kg K)]."""
+    a = p.cp_poly[k]
+    return sum(a[m] * T ** m for m in range(len(a)))
+
+
+def h_species(p, k, T):
+    """h_k(T) = h_f,k + integral from T0 to T of c_p,k [J/kg]."""
+    a = p.cp_poly[k]
+    T0 = p.T0_thermo
+    return p.hf[k] + sum(a[m] * (T ** (m + 1) - T0 ** (m + 1)) / (m + 1) for m in range(len(a)))
+
+
+def cp_mixture(p, T, Y):
+    return sum(Y[k] * cp_species(p, k, T) for k in range(p.K))
 
 
 def thickening(p, T, Y):
@@ -128,7 +155,9 @@ def fd_update(p, grid, nb, T, Y, u, uin_r, P_th, dP_lag):
             Gp = Fp * p.nu_lat * (Tp / p.T_ref) ** p.mu_exp / (p.Pr * Le)
             dif = dif + 0.5 * (G + Gp) * (pp1 - phi) - 0.5 * (G + Gm) * (phi - pm1)
         dif = dif / rho
-        if f == 0:
+        if f == 0 and p.varcp:
+            dif, src = _energy_varcp(p, nb, T, Y, Floc, mu, rho, rho_phys, om, dP_lag)
+        elif f == 0:
             qdot = -sum(p.hf[k] * om[k] for k in range(p.K)) if p.K else torch.zeros_like(T)
             src = p.dt * qdot / (rho_phys * p.cp * Floc) + dP_lag / (rho_phys * p.cp)
         else:
@@ -139,6 +168,36 @@ def fd_update(p, grid, nb, T, Y, u, uin_r, P_th, dP_lag):
     Y1 = torch.stack([Y[k] - A_out[k + 1] + N_out[k + 1] for k in range(p.K)])
     lam = N_out[0] / T + sum((W / p.W[k]) * N_out[k + 1] for k in range(p.K))
     return T1, Y1, rho, lam
+
+
+def _energy_varcp(p, nb, T, Y, Floc, mu, rho, rho_phys, om, dP_lag):
+    """Diffusion and source parts of N_T with variable heat capacities (see the module notes)."""
+    cp = cp_mixture(p, T, Y)
+    lam_r = Floc * mu * cp / p.Pr
+    dif = torch.zeros_like(T)
+    flux = torch.zeros_like(T)  # sum_k (c_p,k - c_p)/Le_k grad Y_k . grad T
+    cpk = [cp_species(p, k, T) for k in range(p.K)]
+    for a in range(nb.grid.dim):
+        Tm = nb.value(T, p.T_in, a, -1, 1)
+        Tp = nb.value(T, p.T_in, a, +1, 1)
+        Ym = [nb.value(Y[k], p.Y_in[k], a, -1, 1) for k in range(p.K)]
+        Yp = [nb.value(Y[k], p.Y_in[k], a, +1, 1) for k in range(p.K)]
+        km, im = nb.kind1(a, -1), nb.index1(a, -1)
+        kp, ip = nb.kind1(a, +1), nb.index1(a, +1)
+        Fm = torch.where(km == 0, Floc[im], Floc)
+        Fp = torch.where(kp == 0, Floc[ip], Floc)
+        cpm = sum(Ym[k] * cp_species(p, k, Tm) for k in range(p.K))
+        cpp = sum(Yp[k] * cp_species(p, k, Tp) for k in range(p.K))
+        lam_m = Fm * p.nu_lat * (Tm / p.T_ref) ** p.mu_exp * cpm / p.Pr
+        lam_p = Fp * p.nu_lat * (Tp / p.T_ref) ** p.mu_exp * cpp / p.Pr
+        dif = dif + 0.5 * (lam_r + lam_p) * (Tp - T) - 0.5 * (lam_r + lam_m) * (T - Tm)
+        gT = 0.5 * (Tp - Tm)
+        for k in range(p.K):
+            flux = flux + (cpk[k] - cp) / p.Le[k] * 0.5 * (Yp[k] - Ym[k]) * gT
+    dif = (dif + Floc * mu / p.Pr * flux) / (rho * cp)
+    qdot = -sum(h_species(p, k, T) * om[k] for k in range(p.K))
+    src = p.dt * qdot / (rho_phys * cp * Floc) + dP_lag / (rho_phys * cp)
+    return dif, src
 
 
 def pth_integrand(p, T, Y):

@@ -42,6 +42,11 @@ class Params:
         self.Le = [s["Le"] for s in sp]
         self.hf = [s["hf"] for s in sp]
         self.reactions = cfg.get("reactions", [])
+        # variable heat capacities (NEXT-2 reading): c_p,k(T) = sum_m a_km T^m, J/(kg K); the
+        # formation enthalpies hf hold at T0_thermo
+        self.varcp = bool(cfg.get("variable_cp", False))
+        self.cp_poly = [list(s.get("cp_poly", [self.cp, 0.0, 0.0, 0.0, 0.0])) for s in sp]
+        self.T0_thermo = cfg.get("T0_thermo", 298.15)
         self.T_in = cfg.get("T_in", self.T_ref)
         self.Y_in = list(cfg.get("Y_in", [0.0] * self.K))
         self.weno_eps_T = 1e-6 * self.T_ref ** 2

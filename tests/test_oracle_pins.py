@@ -570,3 +570,133 @@ def test_welch_psd_against_scipy_and_a_sinusoid():
     noise = rng.standard_normal(200000) * 0.5
     f, p = welch_psd(noise, dt, L)
     assert abs(p[1:-1].mean() - 2 * 0.25 * dt) < 0.02 * 2 * 0.25 * dt
+
+
+# ------------------------------------------------------- variable heat capacities (NEXT-2)
+def test_variable_cp_with_equal_heat_capacities_is_the_constant_update():
+    """Equal, constant species heat capacities: the variable-c_p temperature update reduces to the
+    constant-c_p one (lambda / c_p = mu / Pr, h_k - h_f,k = c_p (T - T0) cancels in sum omega_k = 0,
+    the species-enthalpy flux vanishes), up to rounding."""
+    wl = W.generate.chamber_2d(nx=24, ny=12, inlet=True, dt=5e-7, seed=7, u_init=0.01)
+    p0 = Params(wl.cfg)
+    cfg = dict(wl.cfg)
+    cfg["species"] = [dict(s, cp_poly=[wl.cfg["cp"], 0.0, 0.0, 0.0, 0.0]) for s in wl.cfg["species"]]
+    cfg["variable_cp"] = True
+    p1 = Params(cfg)
+    grid = geo.Grid(wl.cfg, wl.mask)
+    nb = geo.FDNeighbours(grid)
+    T = torch.as_tensor(wl.T)
+    Y = torch.as_tensor(wl.Y)
+    Y = Y / Y.sum(0)
+    u = torch.as_tensor(wl.u)
+    uin = torch.zeros(2, grid.N, dtype=f64)
+    a = fdm.fd_update(p0, grid, nb, T, Y, u, uin, p0.P_th0, 3.0)
+    b = fdm.fd_update(p1, grid, nb, T, Y, u, uin, p1.P_th0, 3.0)
+    dT = (a[0] - T).abs().max()
+    assert (a[0] - b[0]).abs().max() < 1e-12 * dT
+    assert (a[3] - b[3]).abs().max() < 1e-12 * a[3].abs().max()
+
+
+def test_species_enthalpy_is_the_integral_of_cp():
+    """h_k(T0) = h_f,k, and h_k(T) - h_k(T0) equals Simpson's rule on c_p,k (exact for the cubic
+    a quartic c_p would need: checked with a full quartic)."""
+    cfg = W.generate._base_cfg(2, 2, 2, 1, "f64")
+    cfg.update({"dx": 1e-4, "dt": 1e-7, "nu_ref": 1.5e-5,
+                "species": [{"name": "A", "W": 0.03, "Le": 1.0, "hf": -1.5e6,
+                             "cp_poly": [900.0, 0.4, -1e-4, 3e-8, -2e-12]}], "variable_cp": True})
+    p = Params(cfg)
+    T0 = p.T0_thermo
+    assert fdm.h_species(p, 0, torch.tensor(T0, dtype=f64)).item() == -1.5e6
+    T1 = 1873.0
+    x = np.linspace(T0, T1, 2001)
+    c = fdm.cp_species(p, 0, torch.as_tensor(x)).numpy()
+    simpson = (x[1] - x[0]) / 3 * (c[0] + c[-1] + 4 * c[1:-1:2].sum() + 2 * c[2:-1:2].sum())
+    got = fdm.h_species(p, 0, torch.tensor(T1, dtype=f64)).item() + 1.5e6
+    assert abs(got - simpson) < 1e-9 * abs(simpson)
+
+
+def _T_ad_variable_cp(cfg, T_u, Yu, Yb):
+    """Root of sum_k Y_b,k h_k(T) = sum_k Y_u,k h_k(T_u) for linear c_p,k = a0 + a1 T (a quadratic)."""
+    T0 = cfg["T0_thermo"]
+    hf = [s["hf"] for s in cfg["species"]]
+    a0 = [s["cp_poly"][0] for s in cfg["species"]]
+    a1 = [s["cp_poly"][1] for s in cfg["species"]]
+
+    def h_mix(Y, T):
+        return sum(y * (h + c0 * (T - T0) + 0.5 * c1 * (T * T - T0 * T0)) for y, h, c0, c1 in zip(Y, hf, a0, a1))
+    A = sum(y * c0 for y, c0 in zip(Yb, a0))
+    B = 0.5 * sum(y * c1 for y, c1 in zip(Yb, a1))
+    C = h_mix(Yb, 0.0) - h_mix(Yu, T_u)  # h_mix(Yb, T) = C' + A T + B T^2 with C' = h_mix(Yb, 0)
+    return (-A + math.sqrt(A * A - 4 * B * C)) / (2 * B)
+
+
+def test_adiabatic_flame_temperature_variable_cp():
+    """Homogeneous constant-pressure combustion with c_p,k(T): the burnt temperature converges, as
+    dt -> 0, to the root of the enthalpy balance of complete combustion (closed form for linear
+    c_p,k), far from the constant-c_p value."""
+    names = W.SPECIES["4sp"]
+    rx = W.chemistry_1step()
+    T0, t_end = 1800.0, 2.0e-5
+    errs = []
+    for dt in (1e-7, 2.5e-8):
+        cfg = W.generate._base_cfg(2, 2, 2, 1, "f64")
+        cfg.update({"bc": {"x": ("periodic", "periodic"), "y": ("periodic", "periodic")}, "dx": 1e-3, "dt": dt,
+                    "nu_ref": 1.5e-5, "thermal": True, "species": W.configs.species(names, unity_lewis=True),
+                    "reactions": rx, "T_in": T0, "Y_in": W.mixture_phi(names, 0.83)})
+        W.configs.variable_cp(cfg)
+        p = Params(cfg)
+        grid = geo.Grid(cfg, np.zeros(4, np.uint8))
+        nb = geo.FDNeighbours(grid)
+        T = torch.full((4,), T0, dtype=f64)
+        Y = torch.tensor(cfg["Y_in"], dtype=f64)[:, None].repeat(1, 4)
+        u = torch.zeros(2, 4, dtype=f64)
+        for _ in range(int(round(t_end / dt))):
+            T, Y, _, _ = fdm.fd_update(p, grid, nb, T, Y, u, u, p.P_th0, 0.0)
+        from workloads.configs import burnt_mixture
+        T_ad = _T_ad_variable_cp(cfg, T0, cfg["Y_in"], burnt_mixture(names, 0.83))
+        errs.append(abs(T.mean().item() - T_ad) / T_ad)
+    T_const, _ = _closed_form_T_ad(names, 0.83, T0, 1400.0)
+    assert abs(T_ad - T_const) > 100.0
+    assert errs[1] < 2e-3 and errs[0] / errs[1] > 2.5, errs
+
+
+def test_variable_cp_temperature_operator_converges_to_the_pde():
+    """Periodic 1-D fields at rest, no chemistry, unequal Lewis numbers and heat capacities: one
+    update's N_T / dt converges at second order to the continuous right-hand side
+    [d/dx(lambda dT/dx) + F mu/Pr sum_k (c_p,k - c_p)/Le_k dY_k/dx dT/dx] / (rho c_p) evaluated
+    from the exact fields and their derivatives. A dropped or sign-flipped term changes the limit."""
+    sp = pytest.importorskip("sympy")
+    X = sp.symbols("x")
+    Lx = 2e-3
+    Texp = 900 + 300 * sp.sin(2 * sp.pi * X / Lx)
+    Y0 = 0.3 + 0.1 * sp.cos(2 * sp.pi * X / Lx)
+    Y1 = 1 - Y0
+    spc = [{"name": "A", "W": 0.028, "Le": 0.7, "hf": 0.0, "cp_poly": [1000.0, 0.3, 0.0, 0.0, 0.0]},
+           {"name": "B", "W": 0.044, "Le": 1.3, "hf": 0.0, "cp_poly": [700.0, 0.6, 0.0, 0.0, 0.0]}]
+    errs = []
+    for n in (32, 64, 128):
+        dx = Lx / n
+        cfg = W.generate._base_cfg(2, n, 1, 1, "f64")
+        cfg.update({"bc": {"x": ("periodic", "periodic"), "y": ("periodic", "periodic")}, "dx": dx, "dt": 1e-9,
+                    "nu_ref": 1.5e-5, "thermal": True, "species": spc, "reactions": [], "T_in": 300.0,
+                    "Y_in": [0.5, 0.5], "variable_cp": True, "T0_thermo": 298.15})
+        p = Params(cfg)
+        grid = geo.Grid(cfg, np.zeros(n, np.uint8))
+        nb = geo.FDNeighbours(grid)
+        xs = np.arange(n) * dx
+        f = lambda e: np.array([float(e.subs(X, v)) for v in xs])
+        T = torch.as_tensor(f(Texp))
+        Y = torch.as_tensor(np.stack([f(Y0), f(Y1)]))
+        u = torch.zeros(2, n, dtype=f64)
+        T1, _, rho, _ = fdm.fd_update(p, grid, nb, T, Y, u, u, p.P_th0, 0.0)
+        # continuous operator in lattice units (lengths in cells): mu as in the oracle
+        cpk = [c["cp_poly"][0] + c["cp_poly"][1] * Texp for c in spc]
+        cp = Y0 * cpk[0] + Y1 * cpk[1]
+        mu = p.nu_lat * (Texp / p.T_ref) ** p.mu_exp
+        d = lambda e: sp.diff(e, X) * dx  # derivative per cell
+        lam = mu * cp / p.Pr
+        flux = mu / p.Pr * sum((cpk[k] - cp) / spc[k]["Le"] * d([Y0, Y1][k]) * d(Texp) for k in range(2))
+        rhs = (d(lam * d(Texp)) + flux) / cp
+        exact = f(rhs) / rho.numpy()
+        errs.append(np.abs((T1 - T).numpy() - exact).max() / np.abs(exact).max())
+    assert errs[2] < 1e-3 and errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, errs

@@ -27,6 +27,24 @@ _THERMO["P"] = ((_THERMO["CO2"][0] + 2 * _THERMO["H2O"][0]) / 3.0, (-393.52e3 - 
 _LEWIS = {"CH4": 1.0, "O2": 1.1, "CO": 1.1, "CO2": 1.4, "H2O": 0.8, "N2": 1.0, "P": 1.0}
 
 
+# Heat capacities c_p,k(T) = a0 + a1 T (J/(kg K)) for the variable-thermodynamics option: SYNTHETIC
+# round values that follow the rise of each species' c_p between 300 and 1500 K, in the NASA
+# polynomial's place (the paper's thermochemistry library and its data are not available). The
+# lumped product P mixes CO2 and H2O by mass (44 : 36).
+_CP_LINEAR = {"CH4": (1590.0, 2.14), "O2": (863.0, 0.19), "CO": (985.0, 0.183), "CO2": (730.0, 0.4),
+              "H2O": (1685.0, 0.6), "N2": (990.0, 0.167), "P": (1160.0, 0.49)}
+
+
+def variable_cp(cfg):
+    """Switch a configuration to temperature-dependent species heat capacities (in place)."""
+    cfg["variable_cp"] = True
+    cfg["T0_thermo"] = 298.15
+    for s in cfg["species"]:
+        a0, a1 = _CP_LINEAR[s["name"]]
+        s["cp_poly"] = [a0, a1, 0.0, 0.0, 0.0]
+    return cfg
+
+
 def species(names, unity_lewis=False):
     out = []
     for n in names:
