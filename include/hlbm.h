@@ -135,6 +135,19 @@ lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* mask, const double* inl
  * call; pageable host memory may be reused on return. Requires lbm_set_geometry first. */
 lbm_status lbm_set_inlet(lbm_ctx* ctx, const double* inlet_u, int on_device);
 
+/* Variable heat capacities (Section 2.3 couples the solver to a thermochemistry library for the
+ * mixture properties; that library is not available, and this is the reading used in its place):
+ * cp: host array [n_species][5], c_p,k(T) = sum_m cp[k][m] T^m in J/(kg K); the species
+ * enthalpies are h_k(T) = hf_k + integral from T0 to T of c_p,k (T0 in K: the temperature at
+ * which the formation enthalpies hold). The temperature update then uses the mixture
+ * c_p = sum_k Y_k c_p,k(T), the conductivity lambda = F mu c_p / Pr per cell (face value the
+ * arithmetic mean), the heat release -sum_k h_k(T) omega_k and the species-enthalpy flux
+ * sum_k (c_p,k - c_p) rho D_k grad Y_k . grad T (centred gradients), all divided by rho c_p; the
+ * species equations are unchanged (constant Lewis numbers). cp = NULL returns to the constant
+ * cfg.cp. Thermal runs only; takes effect from the next step (captured graphs are rebuilt). The
+ * adjoint calls return LBM_ERR_UNSUPPORTED while it is on. */
+lbm_status lbm_set_thermo(lbm_ctx* ctx, const double* cp, double T0);
+
 /* Initial fields: T [N] (K), Y [n_species][N], u [dim][N], P_h [N] (lattice), g_pert [Q][N]
  * (lattice, may be NULL). Populations are set to the equilibrium of Eq. 6 plus g_pert. T and Y
  * are ignored (may be NULL) when cfg.thermal == 0. Requires lbm_set_geometry first. */

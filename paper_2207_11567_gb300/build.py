@@ -11,7 +11,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhlbm.so")
 SOURCES = ["api.cu", "aux_kernels.cu", "stats.cu", "fd_kernels.cu", "lb_d2q9.cu", "lb_d3q27_f64.cu",
            "lb_d3q27_f32.cu", "lb_d3q27_f16.cu", "noalloc.cu", "adjoint.cu",
-           "flame.cu", "probes.cu"]
+           "flame.cu", "probes.cu", "fd_kernels_vcp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -532,6 +532,52 @@ lbm_status set_inlet_impl(lbm_ctx* ctx, const double* inlet_u, int on_device) {
 }
 }  // namespace
 
+extern "C++" {
+namespace {
+// Heat-capacity polynomials into the FD constants of type R: c_p,k and W_k h_k with
+// h_k(T) = h_f,k + integral from T0 to T of c_p,k.
+template <typename R> void fill_thermo(FDConst<R>& f, const lbm_config& c, int K, const double* cp, double T0) {
+  f.varcp = cp ? 1 : 0;
+  for (int k = 0; k < MAX_SP; ++k) {
+    for (int m = 0; m < 5; ++m) f.cp_poly[k][m] = R(0);
+    for (int m = 0; m < 6; ++m) f.hW_poly[k][m] = R(0);
+  }
+  f.cp_in = (R)c.cp;
+  if (!cp) return;
+  double cp_in = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double* a = cp + 5 * k;
+    const double W = c.sp[k].W;
+    double h0 = c.sp[k].hf, Tp = T0, ck = 0.0, Tm = 1.0;
+    for (int m = 0; m < 5; ++m) {
+      h0 -= a[m] * Tp / (m + 1);  // minus the integral's value at T0
+      Tp *= T0;
+      f.cp_poly[k][m] = (R)a[m];
+      f.hW_poly[k][m + 1] = (R)(W * a[m] / (m + 1));
+      ck += a[m] * Tm;
+      Tm *= c.T_in;
+    }
+    f.hW_poly[k][0] = (R)(W * h0);
+    cp_in += c.Y_in[k] * ck;
+  }
+  f.cp_in = (R)cp_in;
+}
+}  // namespace
+}  // extern "C++"
+
+lbm_status lbm_set_thermo(lbm_ctx* ctx, const double* cp, double T0) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (cp && (!ctx->cfg.thermal || !(T0 > 0.0)))
+    return fail(ctx, LBM_ERR_ARG, "variable heat capacities need a thermal run and T0 > 0");
+  if (cp)
+    for (int i = 0; i < 5 * ctx->K; ++i)
+      if (!std::isfinite(cp[i])) return fail(ctx, LBM_ERR_ARG, "non-finite heat-capacity coefficient");
+  fill_thermo<float>(ctx->fdc_f, ctx->cfg, ctx->K, cp, T0);
+  fill_thermo<double>(ctx->fdc_d, ctx->cfg, ctx->K, cp, T0);
+  drop_graphs(ctx);  // the captured launches hold the old constants
+  return LBM_OK;
+}
+
 lbm_status lbm_set_inlet(lbm_ctx* ctx, const double* inlet_u, int on_device) {
   if (!ctx || !inlet_u) return fail(ctx, LBM_ERR_ARG, "null argument");
   if (!ctx->have_geo) return fail(ctx, LBM_ERR_STATE, "set_geometry must come first");
@@ -1168,10 +1214,10 @@ lbm_status adjoint_supported(lbm_ctx* ctx) {
   const lbm_config& c = ctx->cfg;
   const bool hi1 = c.omega_hi[0] == 1.0 && c.omega_hi[1] == 1.0;
   if (c.dim != 2 || c.storage == LBM_STORE_F16 || c.collision != LBM_COLL_CUMULANT || !hi1 || c.closed_domain ||
-      c.flame_sensor || ctx->n_wall > 0)
+      c.flame_sensor || ctx->n_wall > 0 || ctx->fdc_d.varcp)
     return fail(ctx, LBM_ERR_UNSUPPORTED,
                 "adjoint: 2-D, FP32/FP64 storage, cumulant collision with default higher-order rates, open domain, "
-                "no flame sensor, half-way walls");
+                "no flame sensor, half-way walls, constant heat capacity");
   return LBM_OK;
 }
 }  // namespace

@@ -80,6 +80,13 @@ template <typename R> struct FDConst {
   R heat[MAX_RX];
   R I_scale;              // integrand -> O(1) before the reduction
   R M_scale;              // mass flux -> O(1) before the reduction
+  // variable heat capacities (lbm_set_thermo; varcp = 0: the constant inv_cp above):
+  // c_p,k(T) = sum_m cp_poly[k][m] T^m (J/(kg K)); W_k h_k(T) = hW_poly[k][0] + T (hW_poly[k][1]
+  // + T (... hW_poly[k][5])) (J/mol); cp_in = c_p of the inlet state
+  int varcp;
+  R cp_poly[MAX_SP][5];
+  R hW_poly[MAX_SP][6];
+  R cp_in;
 };
 
 // ---------------------------------------------------------------------------- storage

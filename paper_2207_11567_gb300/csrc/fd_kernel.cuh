@@ -137,7 +137,21 @@ template <> struct FDShape<3> { static constexpr int X = 32, Y = 4, Z = 2; };
 // One fluid cell of the FD update. FAST: the whole radius-2 stencil is fluid and inside the grid
 // (no ghosts, no periodic wrap), so neighbour kinds are known at compile time and indices are
 // plain offsets; the arithmetic is the same as the general path.
-template <int D, typename R, int NK, int NR, bool FAST>
+// Polynomials of the variable heat capacities (Horner): c_p,k(T) and W_k h_k(T).
+template <typename R> __device__ __forceinline__ R poly5(const R (&a)[5], R T) {
+  return fma(fma(fma(fma(a[4], T, a[3]), T, a[2]), T, a[1]), T, a[0]);
+}
+template <typename R> __device__ __forceinline__ R poly6(const R (&a)[6], R T) {
+  return fma(fma(fma(fma(fma(a[5], T, a[4]), T, a[3]), T, a[2]), T, a[1]), T, a[0]);
+}
+
+// VCP: variable heat capacities. The temperature update becomes
+//   N_T = [sum_faces lambda_face (T_n - T) + F mu/Pr sum_k (c_p,k - c_p)/Le_k grad Y_k . grad T]
+//         / (rho c_p) + dt (-sum_k h_k omega_k) / (rho c_p F) + dP/(rho c_p),
+// lambda = F mu c_p / Pr per cell (face value the arithmetic mean, a ghost neighbour's c_p from its
+// ghost T and Y), centred gradients. The species fields run first so that the neighbours' c_p and
+// the species-enthalpy flux are summed before the temperature field.
+template <int D, typename R, int NK, int NR, bool FAST, bool VCP>
 __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z, int r, uint32_t sw, R& termI,
                                         R& termM) {
   const FDConst<R>& c = a.c;
@@ -200,11 +214,34 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
     reaction_rates<NR, R>(c, Tr, Yr, rho_phys, q);
     const R Fr = a.Floc ? ldg(a.Floc + r) : c.F;
     const R mur = c.nu_lat * powr<R>(Tr * c.T_ref_inv, c.mu_exp);
+    // variable heat capacities: mixture c_p and the heat of each reaction at T_r
+    R cp_r = R(0);
+    R heatT[VCP ? RMAX : 1];
+    if constexpr (VCP) {
+      R hW[KMAX];
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        if (NK > 0 || k < K) {
+          cp_r += Yr[k] * poly5<R>(c.cp_poly[k], Tr);
+          hW[k] = poly6<R>(c.hW_poly[k], Tr);
+        } else {
+          hW[k] = R(0);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) {
+        R h = R(0);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) h -= c.nu[j][k] * hW[k];
+        heatT[j] = h;
+      }
+    }
     R ur[3] = {ldg(a.u + r), ldg(a.u + N + r), D == 3 ? ldg(a.u + 2 * N + r) : R(0)};
     const int f = y + g.ny * z;
     const int nf = g.ny * g.nz;
     // face coefficients (F mu) and face velocities
     R FMf[3][2], uf[3][2];
+    R Tnb[VCP ? 3 : 1][2], FMn[VCP ? 3 : 1][2];  // VCP: neighbour T and F mu
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) {
 #pragma unroll
@@ -215,6 +252,10 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
         const R Fn = (a.Floc && kk == NB_FLUID) ? ldg(a.Floc + j) : Fr;
         const R mun = c.nu_lat * powr<R>(Tn * c.T_ref_inv, c.mu_exp);
         FMf[ax][sd] = R(0.5) * (Fr * mur + Fn * mun);
+        if constexpr (VCP) {
+          Tnb[ax][sd] = Tn;
+          FMn[ax][sd] = Fn * mun;
+        }
         R un;
         if (kk == NB_FLUID) un = ldg(a.u + ax * N + j);
         else if (kk == NB_INLET) un = ldg(a.inlet_u + ax * nf + f);
@@ -229,14 +270,30 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
     R qdot = R(0);
 #pragma unroll
     for (int j = 0; j < RMAX; ++j)
-      if (NR > 0 || j < nrx) qdot += c.heat[j] * q[j];
+      if (NR > 0 || j < nrx) qdot += (VCP ? heatT[j] : c.heat[j]) * q[j];
     const R fd_dT = sizeof(R) == 4 ? (R)a.pth->fd_dT : (R)a.pth->fd_dT_d;
     R lam = R(0);
     R sWn = R(0);
     R Tnew = Tr;
-    // fields: 0 = T, 1.. = Y_k
+    // VCP accumulators: neighbour c_p (sum over species of Y_k(n) c_p,k(T_n)) and, per axis,
+    // sum_k (c_p,k - c_p)/Le_k (Y_k(r+e) - Y_k(r-e))
+    R cpn[VCP ? 3 : 1][2], gYw[VCP ? 3 : 1];
+    if constexpr (VCP) {
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        cpn[ax][0] = cpn[ax][1] = R(0);
+        gYw[ax] = R(0);
+      }
+    }
+    R tflux = R(0);
+    // fields: 0 = T, 1.. = Y_k (VCP: the species first, T last)
 #pragma unroll 1
-    for (int fi = 0; fi <= K; ++fi) {
+    for (int it = 0; it <= K; ++it) {
+      const int fi = VCP ? (it == K ? 0 : it + 1) : it;
+      R ckr = R(0);
+      if constexpr (VCP) {
+        if (fi > 0) ckr = poly5<R>(c.cp_poly[fi - 1], Tr);
+      }
       const R* phi = fi == 0 ? a.T : a.Y + (size_t)(fi - 1) * N;
       const R phin = fi == 0 ? c.T_in : c.Y_in[fi - 1];
       const R eps = fi == 0 ? c.eps_T : c.eps_Y;
@@ -266,13 +323,31 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
         const R fp = bP + R(0.5) * fdiv<R>(tbcP * dabP + R(2) * tabP * dbcP, tbcP + R(2) * tabP);
         const R fm = bM + R(0.5) * fdiv<R>(tbcM * dabM + R(2) * tabM * dbcM, tbcM + R(2) * tabM);
         adv += ur[ax] * (fp - fm);
-        dif += FMf[ax][1] * dp1 - FMf[ax][0] * dm1;
+        if constexpr (VCP) {
+          if (fi > 0) {
+            cpn[ax][0] += m1 * poly5<R>(c.cp_poly[fi - 1], Tnb[ax][0]);
+            cpn[ax][1] += p1 * poly5<R>(c.cp_poly[fi - 1], Tnb[ax][1]);
+            gYw[ax] += (ckr - cp_r) * c.inv_Le[fi - 1] * (p1 - m1);
+            dif += FMf[ax][1] * dp1 - FMf[ax][0] * dm1;
+          } else {
+            const R Frm = Fr * mur * cp_r;
+            dif += R(0.5) * (Frm + FMn[ax][1] * cpn[ax][1]) * dp1 - R(0.5) * (Frm + FMn[ax][0] * cpn[ax][0]) * dm1;
+            tflux += gYw[ax] * (p1 - m1);
+          }
+        } else {
+          dif += FMf[ax][1] * dp1 - FMf[ax][0] * dm1;
+        }
       }
-      dif *= gfac * inv_rho;
       R src;
-      if (fi == 0) {
+      if (VCP && fi == 0) {
+        const R inv_cpr = R(1) / cp_r;
+        dif = (dif + R(0.25) * Fr * mur * tflux) * gfac * inv_rho * inv_cpr;
+        src = (dt * qdot * inv_rpF + fd_dT * inv_rho / c.inv_cp) * inv_cpr;
+      } else if (fi == 0) {
+        dif *= gfac * inv_rho;
         src = dt * qdot * inv_rpF * c.inv_cp + fd_dT * inv_rho;
       } else {
+        dif *= gfac * inv_rho;
         R om = R(0);
 #pragma unroll
         for (int j = 0; j < RMAX; ++j)
@@ -310,8 +385,9 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
 #ifndef HLBM_FD_MIN_BLOCKS
 #define HLBM_FD_MIN_BLOCKS 4  // FP32: resident blocks per SM the register budget is sized for
 #endif
-template <int D, typename R, int NK, int NR>
-__global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? HLBM_FD_MIN_BLOCKS : 1) fd_step_kernel(const FDArgs<R> a) {
+template <int D, typename R, int NK, int NR, bool VCP = false>
+__global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? (VCP ? 2 : HLBM_FD_MIN_BLOCKS) : 1)
+    fd_step_kernel(const FDArgs<R> a) {
   const FDConst<R>& c = a.c;
   const Geo& g = a.geo;
   const int x = blockIdx.x * FDShape<D>::X + threadIdx.x;
@@ -328,8 +404,8 @@ __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? HLBM_FD_MIN_BLOCKS 
     const uint32_t ghosts = sw & (D == 3 ? 0x00ffffffu : 0x0000ffffu);
     const bool fast = ghosts == 0u && x >= 2 && x < g.nx - 2 && y >= 2 && y < g.ny - 2 &&
                       (D == 2 || (z >= 2 && z < g.nz - 2));
-    if (fast) fd_cell<D, R, NK, NR, true>(a, x, y, z, r, sw, termI, termM);
-    else fd_cell<D, R, NK, NR, false>(a, x, y, z, r, sw, termI, termM);
+    if (fast) fd_cell<D, R, NK, NR, true, VCP>(a, x, y, z, r, sw, termI, termM);
+    else fd_cell<D, R, NK, NR, false, VCP>(a, x, y, z, r, sw, termI, termM);
   }
   if (!c.closed) return;  // uniform across the grid
   // block reduction of the two terms into this block's partial slot
@@ -378,8 +454,12 @@ template <int D> inline int fd_blocks(const Geo& g) {
   return (int)(b.x * b.y * b.z);
 }
 
+// variable heat capacities: fd_kernels_vcp.cu
+template <int D, typename R> cudaError_t launch_fd_vcp(const FDArgs<R>& a, cudaStream_t st);
+
 template <int D, typename R>
 cudaError_t launch_fd(const FDArgs<R>& a, cudaStream_t st, bool sensor_pass) {
+  if (!sensor_pass && a.c.varcp) return launch_fd_vcp<D, R>(a, st);
   if (sensor_pass) {
     const int grid = (a.geo.N + FD_BLOCK - 1) / FD_BLOCK;
     flame_sensor_kernel<D, R><<<grid, FD_BLOCK, 0, st>>>(a);

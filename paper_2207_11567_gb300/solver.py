@@ -68,6 +68,8 @@ class Solver:
         self.K = len(cfg.get("species", [])) if cfg.get("thermal") else 0
         nz = cfg.get("nz", 1) if self.dim == 3 else 1
         self.N = cfg["nx"] * cfg["ny"] * nz
+        if cfg.get("variable_cp"):
+            self.set_thermo([sp["cp_poly"] for sp in cfg["species"]], cfg.get("T0_thermo", 298.15))
         self.set_geometry(mask, inlet_u)
 
     def __del__(self):
@@ -89,6 +91,19 @@ class Solver:
             keep, ptr = _as_c_double(inlet_u)
         with torch.cuda.device(self.device):
             _check(self.ctx, L.lib.lbm_set_geometry(self.ctx, m.ctypes.data_as(C.c_void_p), ptr, 0))
+        del keep
+
+    def set_thermo(self, cp_poly, T0=298.15):
+        """Variable heat capacities (lbm_set_thermo): cp_poly [n_species][5] coefficients of
+        c_p,k(T) = sum_m a_m T^m in J/(kg K), formation enthalpies at T0; None for constant c_p."""
+        if cp_poly is None:
+            _check(self.ctx, L.lib.lbm_set_thermo(self.ctx, None, float(T0)))
+            return
+        a = np.zeros((len(self.cfg["species"]), 5))
+        for k, row in enumerate(cp_poly):
+            a[k, : len(row)] = row
+        keep, ptr = _as_c_double(a)
+        _check(self.ctx, L.lib.lbm_set_thermo(self.ctx, ptr, float(T0)))
         del keep
 
     def set_inlet(self, inlet_u):
