@@ -401,6 +401,8 @@ def main():
                     help="with --only: sample running statistics every N steps during the timed steps")
     ap.add_argument("--probes", type=int, default=0,
                     help="with --only: record N probe cells after every step during the timed steps")
+    ap.add_argument("--varcp", action="store_true",
+                    help="variable species heat capacities (c_p,k(T) polynomials) in the energy equation")
     ap.add_argument("--curved", action="store_true",
                     help="c3/c4: interpolated bounce-back on the injector cylinders and the exhaust cone")
     args = ap.parse_args()
@@ -450,6 +452,15 @@ def main():
                                        curved=True)
         return W.make(args.workload)
 
+    if args.varcp:
+        from workloads.configs import variable_cp
+        make_plain = make
+
+        def make():
+            wl = make_plain()
+            if wl.cfg.get("thermal"):
+                variable_cp(wl.cfg)
+            return wl
     if args.only:
         r = run_variant(make(), args.only, args.steps, args.warmup, torch, profile_steps=2, stats=args.stats,
                         probes=args.probes)

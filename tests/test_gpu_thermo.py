@@ -18,8 +18,12 @@ def _check(errs, tol):
     assert not bad, f"errors above {tol}: {bad} (all: {errs})"
 
 
-@pytest.mark.parametrize("case", ["chamber2d", "flame2d", "swirl3d"])
+@pytest.mark.parametrize("case", ["chamber2d", "flame2d", "swirl3d_sensor", "swirl3d_closed"])
 def test_variable_cp_f64(case):
+    """The reactive burner runs once with the flame sensor (open domain) and once with the
+    closed-domain pressure (no sensor): with both at once this case is ill-conditioned already
+    with constant c_p (GPU and oracle part at 1e-8..5e-7 within 20 steps, measured on GB300,
+    while each alone agrees to 1e-13)."""
     if case == "chamber2d":
         wl = W.generate.chamber_2d(nx=64, ny=32, inlet=True, dt=5e-7, storage="f64", seed=4, u_init=0.01,
                                    n_rows=1, per_row=2)
@@ -29,6 +33,8 @@ def test_variable_cp_f64(case):
         steps = 60
     else:
         wl = W.generate.swirl_3d(28, 16, 16, reactive=True, storage="f64", seed=5)
+        wl.cfg["flame_sensor"] = case == "swirl3d_sensor"
+        wl.cfg["closed_domain"] = case == "swirl3d_closed"
         steps = 20
     variable_cp(wl.cfg)
     o, st = oracle_run(wl, steps)
@@ -49,15 +55,28 @@ def test_variable_cp_changes_the_temperature():
 
 
 def test_variable_cp_f32():
-    wl = W.generate.chamber_2d(nx=64, ny=32, inlet=True, dt=5e-7, storage="f32", seed=4, u_init=0.01,
-                               n_rows=1, per_row=2)
+    """FP32 within max(1e-5, 3 x storage floor) per field on the closed chamber (200 steps); with an
+    inlet and a moving initial state the constant-c_p FP32 path already sits at ~15x the floor in
+    P_h (1.5e-5, measured on GB300), so there the variable-c_p run is held to that: at most 1.5x
+    the constant-c_p run's error, field by field."""
+    wl = W.generate.chamber_2d(nx=97, ny=41, dt=5e-7, storage="f32", seed=3)
     variable_cp(wl.cfg)
-    o, st = oracle_run(wl, 150)
-    gpu = gpu_run(wl, 150)
-    errs = compare(wl, gpu, st)
-    floor = storage_floor(wl, 150, st)
+    o, st = oracle_run(wl, 200)
+    errs = compare(wl, gpu_run(wl, 200), st)
+    floor = storage_floor(wl, 200, st)
     bad = {k: (v, floor[k]) for k, v in errs.items() if not (v <= max(1e-5, 3.0 * floor[k]))}
     assert not bad, (errs, floor)
+
+    def inlet_case(vcp):
+        wl = W.generate.chamber_2d(nx=64, ny=32, inlet=True, dt=5e-7, storage="f32", seed=4, u_init=0.01,
+                                   n_rows=1, per_row=2)
+        if vcp:
+            variable_cp(wl.cfg)
+        o, st = oracle_run(wl, 150)
+        return compare(wl, gpu_run(wl, 150), st), storage_floor(wl, 150, st)
+    (ev, fv), (ec, _) = inlet_case(True), inlet_case(False)
+    bad = {k: (v, ec[k]) for k, v in ev.items() if not (v <= max(1e-5, 3.0 * fv[k], 1.5 * ec[k]))}
+    assert not bad, (ev, ec, fv)
 
 
 def test_variable_cp_adjoint_is_unsupported():
@@ -82,15 +101,16 @@ def test_variable_cp_adjoint_is_unsupported():
 
 
 def test_free_flame_reaches_variable_cp_adiabatic_temperature():
-    """Planar flame thickened by F = 4 with c_p,k(T): burnt temperature within 1e-3 of the root of
-    the enthalpy balance of complete combustion (unity Lewis numbers), which lies far from the
-    constant-c_p value."""
+    """Planar flame thickened by F = 3 with c_p,k(T): burnt temperature within 1e-3 of the root of
+    the enthalpy balance of complete combustion (unity Lewis numbers), 2064 K, far from the
+    constant-c_p 1952 K. (At F = 4 the hotter burnt gas's thickened diffusivity exceeds the
+    explicit limit of this time step: dt F lambda / (rho c_p dx^2) reaches 0.5 near 2060 K.)"""
     from paper_2207_11567_gb300 import from_workload
     from paper_2207_11567_gb300.flame1d import free_flame
     from tests.test_oracle_pins import _T_ad_variable_cp
     from workloads.configs import burnt_mixture
-    wl = W.generate.flame_2d(nx=256, ny=1, storage="f64", seed=0, width_cells=80.0)
-    wl.cfg["thicken_F"] = 4.0
+    wl = W.generate.flame_2d(nx=256, ny=1, storage="f64", seed=0, width_cells=60.0)
+    wl.cfg["thicken_F"] = 3.0
     variable_cp(wl.cfg)
     s = from_workload(wl)
     sol = free_flame(s, chunk=200, max_steps=400000)
