@@ -537,7 +537,13 @@ namespace {
 // Heat-capacity polynomials into the FD constants of type R: c_p,k and W_k h_k with
 // h_k(T) = h_f,k + integral from T0 to T of c_p,k.
 template <typename R> void fill_thermo(FDConst<R>& f, const lbm_config& c, int K, const double* cp, double T0) {
-  f.varcp = cp ? 1 : 0;
+  f.varcp = 0;
+  if (cp) {
+    f.varcp = 1;  // degree of the kernel variant: 1 when every c_p,k is linear in T, else 4
+    for (int k = 0; k < K; ++k)
+      for (int m = 2; m < 5; ++m)
+        if (cp[5 * k + m] != 0.0) f.varcp = 4;
+  }
   for (int k = 0; k < MAX_SP; ++k) {
     for (int m = 0; m < 5; ++m) f.cp_poly[k][m] = R(0);
     for (int m = 0; m < 6; ++m) f.hW_poly[k][m] = R(0);

@@ -80,7 +80,8 @@ template <typename R> struct FDConst {
   R heat[MAX_RX];
   R I_scale;              // integrand -> O(1) before the reduction
   R M_scale;              // mass flux -> O(1) before the reduction
-  // variable heat capacities (lbm_set_thermo; varcp = 0: the constant inv_cp above):
+  // variable heat capacities (lbm_set_thermo; varcp = 0: the constant inv_cp above, 1: c_p linear
+  // in T, 4: higher powers present):
   // c_p,k(T) = sum_m cp_poly[k][m] T^m (J/(kg K)); W_k h_k(T) = hW_poly[k][0] + T (hW_poly[k][1]
   // + T (... hW_poly[k][5])) (J/mol); cp_in = c_p of the inlet state
   int varcp;

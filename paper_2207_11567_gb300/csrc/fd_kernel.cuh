@@ -137,26 +137,34 @@ template <> struct FDShape<3> { static constexpr int X = 32, Y = 4, Z = 2; };
 // One fluid cell of the FD update. FAST: the whole radius-2 stencil is fluid and inside the grid
 // (no ghosts, no periodic wrap), so neighbour kinds are known at compile time and indices are
 // plain offsets; the arithmetic is the same as the general path.
-// Polynomials of the variable heat capacities (Horner): c_p,k(T) and W_k h_k(T).
-template <typename R> __device__ __forceinline__ R poly5(const R (&a)[5], R T) {
-  return fma(fma(fma(fma(a[4], T, a[3]), T, a[2]), T, a[1]), T, a[0]);
+// Polynomials of the variable heat capacities (Horner, degree DEG of c_p known at compile time):
+// c_p,k(T) and W_k h_k(T) (one degree higher).
+template <int DEG, typename R> __device__ __forceinline__ R cp_eval(const R (&a)[5], R T) {
+  R v = a[DEG];
+#pragma unroll
+  for (int m = DEG - 1; m >= 0; --m) v = fma(v, T, a[m]);
+  return v;
 }
-template <typename R> __device__ __forceinline__ R poly6(const R (&a)[6], R T) {
-  return fma(fma(fma(fma(fma(a[5], T, a[4]), T, a[3]), T, a[2]), T, a[1]), T, a[0]);
+template <int DEG, typename R> __device__ __forceinline__ R hW_eval(const R (&a)[6], R T) {
+  R v = a[DEG + 1];
+#pragma unroll
+  for (int m = DEG; m >= 0; --m) v = fma(v, T, a[m]);
+  return v;
 }
 
-// VCP: variable heat capacities. The temperature update becomes
+// VDEG > 0: variable heat capacities, polynomials of degree VDEG. The temperature update becomes
 //   N_T = [sum_faces lambda_face (T_n - T) + F mu/Pr sum_k (c_p,k - c_p)/Le_k grad Y_k . grad T]
 //         / (rho c_p) + dt (-sum_k h_k omega_k) / (rho c_p F) + dP/(rho c_p),
 // lambda = F mu c_p / Pr per cell (face value the arithmetic mean, a ghost neighbour's c_p from its
 // ghost T and Y), centred gradients. The species fields run first so that the neighbours' c_p and
 // the species-enthalpy flux are summed before the temperature field.
-template <int D, typename R, int NK, int NR, bool FAST, bool VCP>
+template <int D, typename R, int NK, int NR, bool FAST, int VDEG>
 __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z, int r, uint32_t sw, R& termI,
                                         R& termM) {
   const FDConst<R>& c = a.c;
   const Geo& g = a.geo;
   const int N = g.N;
+  constexpr bool VCP = VDEG > 0;
   {
     const int pos[3] = {x, y, z};
     const int dims[3] = {g.nx, g.ny, g.nz};
@@ -222,8 +230,8 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
 #pragma unroll
       for (int k = 0; k < KMAX; ++k) {
         if (NK > 0 || k < K) {
-          cp_r += Yr[k] * poly5<R>(c.cp_poly[k], Tr);
-          hW[k] = poly6<R>(c.hW_poly[k], Tr);
+          cp_r += Yr[k] * cp_eval<VDEG, R>(c.cp_poly[k], Tr);
+          hW[k] = hW_eval<VDEG, R>(c.hW_poly[k], Tr);
         } else {
           hW[k] = R(0);
         }
@@ -292,7 +300,7 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
       const int fi = VCP ? (it == K ? 0 : it + 1) : it;
       R ckr = R(0);
       if constexpr (VCP) {
-        if (fi > 0) ckr = poly5<R>(c.cp_poly[fi - 1], Tr);
+        if (fi > 0) ckr = cp_eval<VDEG, R>(c.cp_poly[fi - 1], Tr);
       }
       const R* phi = fi == 0 ? a.T : a.Y + (size_t)(fi - 1) * N;
       const R phin = fi == 0 ? c.T_in : c.Y_in[fi - 1];
@@ -325,8 +333,8 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
         adv += ur[ax] * (fp - fm);
         if constexpr (VCP) {
           if (fi > 0) {
-            cpn[ax][0] += m1 * poly5<R>(c.cp_poly[fi - 1], Tnb[ax][0]);
-            cpn[ax][1] += p1 * poly5<R>(c.cp_poly[fi - 1], Tnb[ax][1]);
+            cpn[ax][0] += m1 * cp_eval<VDEG, R>(c.cp_poly[fi - 1], Tnb[ax][0]);
+            cpn[ax][1] += p1 * cp_eval<VDEG, R>(c.cp_poly[fi - 1], Tnb[ax][1]);
             gYw[ax] += (ckr - cp_r) * c.inv_Le[fi - 1] * (p1 - m1);
             dif += FMf[ax][1] * dp1 - FMf[ax][0] * dm1;
           } else {
@@ -385,8 +393,11 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
 #ifndef HLBM_FD_MIN_BLOCKS
 #define HLBM_FD_MIN_BLOCKS 4  // FP32: resident blocks per SM the register budget is sized for
 #endif
-template <int D, typename R, int NK, int NR, bool VCP = false>
-__global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? (VCP ? 2 : HLBM_FD_MIN_BLOCKS) : 1)
+#ifndef HLBM_FD_VCP_MIN_BLOCKS
+#define HLBM_FD_VCP_MIN_BLOCKS 4  // the same for the variable heat-capacity variant (measured: 2 blocks 2.24 ms, 3 blocks 1.72 ms, 4 blocks 1.60 ms per C4 launch)
+#endif
+template <int D, typename R, int NK, int NR, int VDEG = 0>
+__global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? (VDEG > 0 ? HLBM_FD_VCP_MIN_BLOCKS : HLBM_FD_MIN_BLOCKS) : 1)
     fd_step_kernel(const FDArgs<R> a) {
   const FDConst<R>& c = a.c;
   const Geo& g = a.geo;
@@ -404,8 +415,8 @@ __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? (VCP ? 2 : HLBM_FD_
     const uint32_t ghosts = sw & (D == 3 ? 0x00ffffffu : 0x0000ffffu);
     const bool fast = ghosts == 0u && x >= 2 && x < g.nx - 2 && y >= 2 && y < g.ny - 2 &&
                       (D == 2 || (z >= 2 && z < g.nz - 2));
-    if (fast) fd_cell<D, R, NK, NR, true, VCP>(a, x, y, z, r, sw, termI, termM);
-    else fd_cell<D, R, NK, NR, false, VCP>(a, x, y, z, r, sw, termI, termM);
+    if (fast) fd_cell<D, R, NK, NR, true, VDEG>(a, x, y, z, r, sw, termI, termM);
+    else fd_cell<D, R, NK, NR, false, VDEG>(a, x, y, z, r, sw, termI, termM);
   }
   if (!c.closed) return;  // uniform across the grid
   // block reduction of the two terms into this block's partial slot
