@@ -306,6 +306,18 @@ lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* state_n, void* adj, void* 
  * context's current state is left as it was. */
 lbm_status lbm_adjoint_segment(lbm_ctx* ctx, const void* checkpoint, int n_steps, void* adj, void* grad_inlet);
 
+/* Reverse sweep over a whole checkpointed run (same support as lbm_adjoint_step): checkpoints is a
+ * host array of n_segments device pointers, checkpoints[s] the state s * seg_len in the
+ * lbm_save_state layout; the run has n_steps steps, (n_segments - 1) seg_len < n_steps <=
+ * n_segments seg_len (the last segment may be shorter). adj: adjoint of state n_steps on entry,
+ * of state 0 on return; grad_inlet accumulated. Equivalent to lbm_adjoint_segment over the
+ * segments from the last to the first, with identical results: the same kernels in the same
+ * order on the context's stream, while the recompute of the next segment runs on a second stream
+ * of the library (the two overlap; at small grids each kernel fills a fraction of the GPU).
+ * Workspace: 2 seg_len segment slots (lbm_adjoint_segment's, grown). */
+lbm_status lbm_adjoint_sweep(lbm_ctx* ctx, const void* const* checkpoints, int n_segments, int seg_len, int n_steps,
+                             void* adj, void* grad_inlet);
+
 /* Objective J = sum over fluid cells of the fuel consumption rate -omega_F (kg/(m^3 s), lattice
  * cell volume 1) of the context's current state, written to *J (host), and its gradient with
  * respect to the state written to adj_out (device, lbm_save_state layout: T and Y parts filled,

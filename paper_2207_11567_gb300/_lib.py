@@ -91,6 +91,7 @@ def _load():
         "lbm_flame_properties": (C.c_int, [P, C.c_int, P, P]),
         "lbm_set_inlet": (C.c_int, [P, P, C.c_int]),
         "lbm_set_thermo": (C.c_int, [P, P, C.c_double]),
+        "lbm_adjoint_sweep": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, P, P]),
         "lbm_set_probes": (C.c_int, [P, C.c_int, P, C.c_longlong, C.c_int]),
         "lbm_get_probes": (C.c_int, [P, P, C.c_int, C.POINTER(C.c_longlong)]),
         "lbm_welch_psd": (C.c_int, [P, P, C.c_longlong, C.c_longlong, C.c_double, C.c_int, P]),
@@ -114,7 +115,7 @@ EXPORTED = ("lbm_init", "lbm_destroy", "lbm_last_error", "lbm_set_geometry", "lb
             "lbm_initial_T_adjoint", "lbm_adjoint_segment", "lbm_set_wall_fractions",
             "lbm_set_wall_links", "lbm_stats_control", "lbm_get_stats", "lbm_flame_length",
             "lbm_flame_properties", "lbm_set_inlet", "lbm_set_probes", "lbm_get_probes", "lbm_welch_psd",
-            "lbm_probe_spectrum", "lbm_set_thermo")
+            "lbm_probe_spectrum", "lbm_set_thermo", "lbm_adjoint_sweep")
 
 
 class HLBMError(RuntimeError):

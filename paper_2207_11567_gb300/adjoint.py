@@ -9,11 +9,12 @@ field T0 (which sets T^0 and, through rho = P_th W / (R T) of Eq. 13, the initia
 populations of Eq. 6).
 
 Forward: set the inlet and the initial fields, run K steps, saving the state every C steps.
-Backward: for each segment, last first, lbm_adjoint_segment reloads its checkpoint, recomputes
-and keeps the segment's states, then applies the adjoint step from the segment's last step down
-to its first, adding the inlet-velocity adjoint; lbm_initial_T_adjoint turns the adjoint of
-state 0 into dJ/dT0. Memory: K/C checkpoints of ``Solver.state_bytes()`` plus the library's
-segment workspace (C states with their rho and Lambda).
+Backward: lbm_adjoint_sweep takes the segments last first: for each, the library recomputes and
+keeps the segment's states from its checkpoint, then applies the adjoint step from the segment's
+last step down to its first, adding the inlet-velocity adjoint; the recompute of the next
+segment runs on a second stream while the current one is reversed. lbm_initial_T_adjoint turns
+the adjoint of state 0 into dJ/dT0. Memory: K/C checkpoints of ``Solver.state_bytes()`` plus the
+library's workspace of two segments (2 C states with their rho and Lambda).
 Every arithmetic step runs in the library's CUDA kernels; this module only orders the calls.
 """
 import numpy as np
@@ -69,10 +70,7 @@ class AdjointProblem:
         s = self.solver
         adj = self._adjK * scale
         gin = self._zeros(self.dim * self.ny)
-        for seg in reversed(range(len(self._ckpt))):
-            n0 = seg * self.C
-            n1 = min(n0 + self.C, self.n_steps)
-            s.adjoint_segment(self._ckpt[seg], n1 - n0, adj, gin)
+        s.adjoint_sweep(self._ckpt, self.C, self.n_steps, adj, gin)
         gT = self._zeros(s.N)
         s.initial_T_adjoint(self._ckpt[0], adj, gT)
         return gin.reshape(self.dim, self.ny), gT

@@ -71,6 +71,9 @@ struct lbm_ctx {
   void* adj_ws = nullptr;
   void* seg_ws = nullptr;
   int seg_cap = 0;
+  // second stream and events of the pipelined sweep (lbm_adjoint_sweep)
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t sw_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double* obj_partials = nullptr;
   // running statistics (lbm_stats_control) and flame length
   float* st_mean = nullptr;
@@ -506,6 +509,10 @@ void lbm_destroy(lbm_ctx* ctx) {
     cudaEventDestroy(e.second.second);
   }
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->st2) cudaStreamSynchronize(ctx->st2);
+  for (auto e : ctx->sw_ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->st2) cudaStreamDestroy(ctx->st2);
   dfree_all(ctx);
   if (ctx->own_stream) cudaStreamDestroy(ctx->st);
   delete ctx;
@@ -1033,32 +1040,28 @@ template <typename R> lbm_status adjoint_step_impl(lbm_ctx* ctx, const void* sta
   return LBM_OK;
 }
 
-// Reverse sweep over one checkpoint segment. Recompute: n steps from the checkpoint, state k + 1
-// written straight into slot k + 1 (the checkpoint itself serves as state 0), rho^k, Lambda^k
-// into the segment's rho/Lambda arrays; the last step needs its FD pass only. Reverse: the
-// adjoint step over the states n - 1 .. 0, read in place, alternating between adj and the
-// internal buffer. The context's current state is not touched.
+// Segment workspace: slot k holds state k (k >= 1; state 0 is the checkpoint) then rho^k,
+// Lambda^k. Grown to at least `slots` slots; the old block stays with the context's allocations
+// until lbm_destroy.
+template <typename R> lbm_status ensure_seg_ws(lbm_ctx* ctx, int slots, size_t slot_w) {
+  if (slots > ctx->seg_cap) {
+    if (!(ctx->seg_ws = dalloc(ctx, (size_t)slots * slot_w * sizeof(R))))
+      return fail(ctx, LBM_ERR_ALLOC, "adjoint segment workspace allocation failed");
+    ctx->seg_cap = slots;
+  }
+  return LBM_OK;
+}
+
+// Recompute of one segment on stream st: n steps from the checkpoint, state k + 1 written straight
+// into slot k + 1 of ws, rho^k, Lambda^k into slot k; the last step needs its FD pass only (its
+// state outputs go to the context's spare buffers, which nothing reads).
 template <typename R>
-lbm_status adjoint_segment_impl(lbm_ctx* ctx, const void* checkpoint, int n, void* adj, void* grad_inlet) {
+lbm_status seg_recompute(lbm_ctx* ctx, const void* checkpoint, int n, R* ws, cudaStream_t st) {
   const size_t N = ctx->N;
   const bool th = ctx->cfg.thermal != 0;
-  R *scratch, *buf;
-  lbm_status st = ensure_adj_ws<R>(ctx, &scratch, &buf);
-  if (st != LBM_OK) return st;
   const size_t sw = state_words(ctx), slot_w = sw + (th ? 2 * N : 0);
-  if (n > ctx->seg_cap) {
-    // grow: the old block stays with the context's allocations until lbm_destroy
-    if (!(ctx->seg_ws = dalloc(ctx, (size_t)n * slot_w * sizeof(R))))
-      return fail(ctx, LBM_ERR_ALLOC, "adjoint segment workspace allocation failed");
-    ctx->seg_cap = n;
-  }
-  R* ws = (R*)ctx->seg_ws;
-  // slot k: state k (k >= 1) then rho^k, Lambda^k; state 0 is the checkpoint
   auto state_of = [&](int k) -> R* { return k == 0 ? (R*)checkpoint : ws + (size_t)k * slot_w; };
   auto rho_of = [&](int k) -> R* { return ws + (size_t)k * slot_w + sw; };
-  // thermodynamic-pressure state of the checkpoint (constant in the supported open domain)
-  CK(cudaMemcpyAsync(ctx->pth, (const char*)checkpoint + sw * sizeof(R), sizeof(PthState),
-                     cudaMemcpyDeviceToDevice, ctx->st), "load P_th state");
   const int other = 1 - ctx->cur;
   const bool hi1 = ctx->cfg.omega_hi[0] == 1.0 && ctx->cfg.omega_hi[1] == 1.0 && ctx->cfg.omega_hi[2] == 1.0 &&
                    ctx->cfg.omega_hi[3] == 1.0;
@@ -1076,7 +1079,7 @@ lbm_status adjoint_segment_impl(lbm_ctx* ctx, const void* checkpoint, int n, voi
       fdf.Y_out = last ? (R*)ctx->Y[other] : sk1 + 12 * N;
       fdf.rho_out = rho_of(k);
       fdf.lam_out = rho_of(k) + N;
-      CK((launch_fd<2, R>(fdf, ctx->st, false)), "segment recompute (FD)");
+      CK((launch_fd<2, R>(fdf, st, false)), "segment recompute (FD)");
     }
     if (!last) {
       LBArgs<R> lbf = make_lb_args<R>(ctx, ctx->cur, false);
@@ -1090,15 +1093,27 @@ lbm_status adjoint_segment_impl(lbm_ctx* ctx, const void* checkpoint, int n, voi
         lbf.T = sk + 11 * N;
       } else {
         // isothermal: the step writes u at outlet cells only; carry the rest over
-        CK(cudaMemcpyAsync(sk1 + 9 * N, sk + 9 * N, 2 * N * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st),
+        CK(cudaMemcpyAsync(sk1 + 9 * N, sk + 9 * N, 2 * N * sizeof(R), cudaMemcpyDeviceToDevice, st),
            "segment recompute (u)");
       }
-      CK((launch_lb<2, R, R>(lbf, th ? 1 : 0, co, ctx->st)), "segment recompute (LB)");
+      CK((launch_lb<2, R, R>(lbf, th ? 1 : 0, co, st)), "segment recompute (LB)");
     }
   }
-  CK(launch_zero_solid_pops<R>(ctx->geo, ctx->links, (R*)adj, ctx->st), "zero solid adjoint");
-  const R* in = (const R*)adj;
-  R* out = buf;
+  return LBM_OK;
+}
+
+// Reverse of one recomputed segment on stream st: the adjoint step over the states n - 1 .. 0,
+// read in place, alternating between the two buffers pp[0], pp[1]; *which selects the one that
+// holds the incoming adjoint and, on return, the one that holds the adjoint of the segment's
+// first state.
+template <typename R>
+lbm_status seg_reverse(lbm_ctx* ctx, const void* checkpoint, int n, R* ws, R* scratch, R* const pp[2], int* which,
+                       void* grad_inlet, cudaStream_t st) {
+  const size_t N = ctx->N;
+  const bool th = ctx->cfg.thermal != 0;
+  const size_t sw = state_words(ctx), slot_w = sw + (th ? 2 * N : 0);
+  auto state_of = [&](int k) -> R* { return k == 0 ? (R*)checkpoint : ws + (size_t)k * slot_w; };
+  auto rho_of = [&](int k) -> R* { return ws + (size_t)k * slot_w + sw; };
   for (int k = n - 1; k >= 0; --k) {
     R* sk = state_of(k);
     LBArgs<R> lbf = make_lb_args<R>(ctx, ctx->cur, false);
@@ -1114,14 +1129,84 @@ lbm_status adjoint_segment_impl(lbm_ctx* ctx, const void* checkpoint, int n, voi
       fdf.T = sk + 11 * N;
       fdf.Y = sk + 12 * N;
     }
-    const AdjBuffers<R> b = adj_buffers<R>(ctx, scratch, in, out, grad_inlet);
-    CK(launch_adjoint_step2d<R>(b, lbf, fdf, th, ctx->st), "adjoint kernels");
-    R* done = out;
-    out = (R*)in;
-    in = done;
+    const AdjBuffers<R> b = adj_buffers<R>(ctx, scratch, pp[*which], pp[1 - *which], grad_inlet);
+    CK(launch_adjoint_step2d<R>(b, lbf, fdf, th, st), "adjoint kernels");
+    *which ^= 1;
   }
-  if (in != (const R*)adj)
-    CK(cudaMemcpyAsync(adj, in, sw * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
+  return LBM_OK;
+}
+
+// Reverse sweep over one checkpoint segment: recompute then reverse, on the context's stream.
+// The context's current state is not touched.
+template <typename R>
+lbm_status adjoint_segment_impl(lbm_ctx* ctx, const void* checkpoint, int n, void* adj, void* grad_inlet) {
+  const size_t N = ctx->N;
+  const bool th = ctx->cfg.thermal != 0;
+  R *scratch, *buf;
+  lbm_status st = ensure_adj_ws<R>(ctx, &scratch, &buf);
+  if (st != LBM_OK) return st;
+  const size_t sw = state_words(ctx), slot_w = sw + (th ? 2 * N : 0);
+  if ((st = ensure_seg_ws<R>(ctx, n, slot_w)) != LBM_OK) return st;
+  R* ws = (R*)ctx->seg_ws;
+  // thermodynamic-pressure state of the checkpoint (constant in the supported open domain)
+  CK(cudaMemcpyAsync(ctx->pth, (const char*)checkpoint + sw * sizeof(R), sizeof(PthState),
+                     cudaMemcpyDeviceToDevice, ctx->st), "load P_th state");
+  if ((st = seg_recompute<R>(ctx, checkpoint, n, ws, ctx->st)) != LBM_OK) return st;
+  CK(launch_zero_solid_pops<R>(ctx->geo, ctx->links, (R*)adj, ctx->st), "zero solid adjoint");
+  R* const pp[2] = {(R*)adj, buf};
+  int which = 0;
+  if ((st = seg_reverse<R>(ctx, checkpoint, n, ws, scratch, pp, &which, grad_inlet, ctx->st)) != LBM_OK) return st;
+  if (which != 0)
+    CK(cudaMemcpyAsync(adj, buf, sw * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
+  return LBM_OK;
+}
+
+// Whole-run sweep: segment s covers steps [s C, min((s + 1) C, K)). The recompute of segment s - 1
+// runs on a second stream into the other half of a two-segment workspace while segment s is
+// reversed on the context's stream; events order each half's reuse. Same kernels and arithmetic
+// as lbm_adjoint_segment segment by segment, so the results are identical.
+template <typename R>
+lbm_status adjoint_sweep_impl(lbm_ctx* ctx, const void* const* ckpt, int S, int C, int K, void* adj,
+                              void* grad_inlet) {
+  const size_t N = ctx->N;
+  const bool th = ctx->cfg.thermal != 0;
+  R *scratch, *buf;
+  lbm_status st = ensure_adj_ws<R>(ctx, &scratch, &buf);
+  if (st != LBM_OK) return st;
+  const size_t sw = state_words(ctx), slot_w = sw + (th ? 2 * N : 0);
+  if ((st = ensure_seg_ws<R>(ctx, 2 * C, slot_w)) != LBM_OK) return st;
+  if (!ctx->st2) CK(cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking), "cudaStreamCreate");
+  for (auto& e : ctx->sw_ev)
+    if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+  cudaEvent_t start = ctx->sw_ev[0], rec[2] = {ctx->sw_ev[1], ctx->sw_ev[2]}, rev[2] = {ctx->sw_ev[3], ctx->sw_ev[4]};
+  R* half[2] = {(R*)ctx->seg_ws, (R*)ctx->seg_ws + (size_t)C * slot_w};
+  auto len = [&](int s) { return (s + 1) * C <= K ? C : K - s * C; };
+  // P_th state (the same in every checkpoint of the supported open domain) and the solid-cell
+  // entries of the incoming adjoint, then the second stream joins
+  CK(cudaMemcpyAsync(ctx->pth, (const char*)ckpt[0] + sw * sizeof(R), sizeof(PthState), cudaMemcpyDeviceToDevice,
+                     ctx->st), "load P_th state");
+  CK(launch_zero_solid_pops<R>(ctx->geo, ctx->links, (R*)adj, ctx->st), "zero solid adjoint");
+  CK(cudaEventRecord(start, ctx->st), "event");
+  CK(cudaStreamWaitEvent(ctx->st2, start, 0), "event wait");
+  if ((st = seg_recompute<R>(ctx, ckpt[S - 1], len(S - 1), half[(S - 1) & 1], ctx->st2)) != LBM_OK) return st;
+  CK(cudaEventRecord(rec[(S - 1) & 1], ctx->st2), "event");
+  R* const pp[2] = {(R*)adj, buf};
+  int which = 0;
+  for (int s = S - 1; s >= 0; --s) {
+    if (s >= 1) {
+      // the half of segment s - 1 was last read by the reverse of segment s + 1
+      if (s + 1 <= S - 1) CK(cudaStreamWaitEvent(ctx->st2, rev[(s + 1) & 1], 0), "event wait");
+      if ((st = seg_recompute<R>(ctx, ckpt[s - 1], len(s - 1), half[(s - 1) & 1], ctx->st2)) != LBM_OK) return st;
+      CK(cudaEventRecord(rec[(s - 1) & 1], ctx->st2), "event");
+    }
+    CK(cudaStreamWaitEvent(ctx->st, rec[s & 1], 0), "event wait");
+    if ((st = seg_reverse<R>(ctx, ckpt[s], len(s), half[s & 1], scratch, pp, &which, grad_inlet, ctx->st)) !=
+        LBM_OK)
+      return st;
+    CK(cudaEventRecord(rev[s & 1], ctx->st), "event");
+  }
+  if (which != 0)
+    CK(cudaMemcpyAsync(adj, buf, sw * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
   return LBM_OK;
 }
 
@@ -1250,6 +1335,22 @@ lbm_status lbm_fuel_objective(lbm_ctx* ctx, int fuel_species, double* J, void* a
   CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
   return ctx->f64 ? fuel_objective_impl<double>(ctx, fuel_species, J, adj_out)
                   : fuel_objective_impl<float>(ctx, fuel_species, J, adj_out);
+}
+
+lbm_status lbm_adjoint_sweep(lbm_ctx* ctx, const void* const* checkpoints, int n_segments, int seg_len, int n_steps,
+                             void* adj, void* grad_inlet) {
+  if (!ctx || !checkpoints || !adj || !grad_inlet) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (n_segments < 1 || seg_len < 1 || n_steps <= (long long)(n_segments - 1) * seg_len ||
+      n_steps > (long long)n_segments * seg_len)
+    return fail(ctx, LBM_ERR_ARG, "need (n_segments - 1) * seg_len < n_steps <= n_segments * seg_len");
+  for (int s = 0; s < n_segments; ++s)
+    if (!checkpoints[s]) return fail(ctx, LBM_ERR_ARG, "null checkpoint");
+  if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "set_fields must come first");
+  lbm_status s = adjoint_supported(ctx);
+  if (s != LBM_OK) return s;
+  CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  return ctx->f64 ? adjoint_sweep_impl<double>(ctx, checkpoints, n_segments, seg_len, n_steps, adj, grad_inlet)
+                  : adjoint_sweep_impl<float>(ctx, checkpoints, n_segments, seg_len, n_steps, adj, grad_inlet);
 }
 
 lbm_status lbm_adjoint_segment(lbm_ctx* ctx, const void* checkpoint, int n_steps, void* adj, void* grad_inlet) {

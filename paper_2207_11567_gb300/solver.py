@@ -345,6 +345,18 @@ class Solver:
                                                        C.c_void_p(adj.data_ptr()), C.c_void_p(grad_inlet.data_ptr())))
             self._before_torch()
 
+    def adjoint_sweep(self, checkpoints, seg_len, n_steps, adj, grad_inlet):
+        """Reverse sweep over a whole run from its checkpoints (lbm_adjoint_sweep): checkpoints[s]
+        is the saved state s * seg_len; ``adj`` holds the adjoint of state n_steps and is
+        overwritten with that of state 0; the inlet adjoint is added into ``grad_inlet``. The
+        recompute of each segment overlaps the reverse of the one after it."""
+        ptrs = (C.c_void_p * len(checkpoints))(*[c.data_ptr() for c in checkpoints])
+        with torch.cuda.device(self.device):
+            self._after_torch()
+            _check(self.ctx, L.lib.lbm_adjoint_sweep(self.ctx, ptrs, len(checkpoints), int(seg_len), int(n_steps),
+                                                     C.c_void_p(adj.data_ptr()), C.c_void_p(grad_inlet.data_ptr())))
+            self._before_torch()
+
     def initial_T_adjoint(self, state0, adj0, grad_T0):
         """dJ/dT0 into ``grad_T0`` ([N], storage type) from the adjoint ``adj0`` of the state
         ``state0`` that set_fields produced (lbm_initial_T_adjoint)."""

@@ -245,3 +245,30 @@ def test_adjoint_segment_equals_single_steps(n):
     nw = (wl.Q + 2 + 1 + len(wl.cfg["species"])) * wl.N
     assert torch.equal(a1[:nw], a2[:nw])
     assert torch.equal(g1, g2)
+
+
+@pytest.mark.parametrize("K,C", [(11, 4), (12, 4), (5, 5), (7, 3)])
+def test_adjoint_sweep_equals_segments(K, C):
+    """lbm_adjoint_sweep (recompute of the next segment on a second stream, two-segment workspace)
+    gives the same bits as lbm_adjoint_segment over the segments from last to first, including
+    a shorter last segment and a single segment."""
+    from paper_2207_11567_gb300 import from_workload
+    wl = _case("f32")
+    s = from_workload(wl)
+    s.step(2)
+    ckpts = []
+    for n in range(K):
+        if n % C == 0:
+            ckpts.append(s.save_state())
+        s.step(1)
+    adjK = torch.zeros(s.state_bytes() // 4, dtype=torch.float32, device="cuda")
+    s.fuel_objective(FUEL, adjK)
+    a1, g1 = adjK.clone(), torch.zeros(2 * wl.cfg["ny"], dtype=torch.float32, device="cuda")
+    for seg in reversed(range(len(ckpts))):
+        s.adjoint_segment(ckpts[seg], min(C, K - seg * C), a1, g1)
+    a2, g2 = adjK.clone(), torch.zeros_like(g1)
+    s.adjoint_sweep(ckpts, C, K, a2, g2)
+    s.close()
+    nw = (wl.Q + 2 + 1 + len(wl.cfg["species"])) * wl.N
+    assert torch.equal(a1[:nw], a2[:nw])
+    assert torch.equal(g1, g2)
