@@ -56,10 +56,9 @@ class AdjointProblem:
         s.set_geometry(self.mask, np.asarray(inlet_u, dtype=np.float64).reshape(self.dim, self.ny))
         s.set_fields(T=np.asarray(T0, dtype=np.float64), Y=self.Y0, u=self.u0, P_h=self.P_h0, g_pert=self.g_pert)
         self._ckpt = []
-        for n in range(self.n_steps):
-            if n % self.C == 0:
-                self._ckpt.append(s.save_state())
-            s.step(1)
+        for n0 in range(0, self.n_steps, self.C):
+            self._ckpt.append(s.save_state())
+            s.step(min(self.C, self.n_steps - n0))
         self._adjK = self._zeros(self.n_words)
         return s.fuel_objective(self.fuel, self._adjK)
 
