@@ -18,7 +18,8 @@ Codes: 0 pull from ``src``, 1 bounce-back, 2 bounce-back plus inlet term, 3 outl
 anti-bounce-back. Inlets are allowed on the low-x face only, outlets on the high-x face only.
 
 Finite differences (Section 2.3): a stencil point that is not a fluid cell takes a ghost value.
-  * wall or solid: zero gradient (value of the last fluid cell on the line; velocity 0);
+  * wall or solid: zero gradient (value of the last fluid cell on the line; velocity 0), or, with
+    sub-cell wall positions, the ghost-point value of ``FDNeighbours``;
   * inlet: the inlet state (Dirichlet; velocity = inlet velocity of the face element next to r);
   * outlet: zero gradient (value and velocity of the last fluid cell).
 
@@ -181,9 +182,18 @@ def _classify(grid, axis, sigma, base):
 
 
 class FDNeighbours:
-    """Ghost resolution of the radius-2 line stencils, for each axis and side."""
+    """Ghost resolution of the radius-2 line stencils, for each axis and side.
 
-    def __init__(self, grid):
+    Walls with sub-cell positions (reading of the paper's curved-boundary treatment for the
+    finite differences: ghost points): where the distance-1 point along an axis is a wall or a
+    solid cell, the interpolated bounce-back data give the wall at the fraction q of the link, and
+    the point opposite is fluid, the ghost value is taken from the parabola through the cell and
+    its opposite neighbour whose derivative along the axis vanishes at the wall (adiabatic,
+    zero flux): ghost = phi_r + w (phi_opp - phi_r), w = (1 - 2q) / (1 + 2q). A distance-2 point
+    beyond such a ghost copies it; a distance-2 wall point seen past a fluid neighbour takes that
+    neighbour's ghost, phi_1 + w_1 (phi_r - phi_1). q = 1/2 (w = 0) is the zero-gradient ghost."""
+
+    def __init__(self, grid, wall=None, lat=None):
         self.grid = grid
         r = torch.arange(grid.N)
         self.lines = {}
@@ -197,12 +207,44 @@ class FDNeighbours:
                 i2 = torch.where(ghost1, r, i2)
                 # a zero-gradient ghost at distance 2 copies the fluid point at distance 1
                 self.lines[(axis, sigma)] = (k1, i1, k2, i2)
+        self.w1, self.w2 = None, None
+        if wall is not None:
+            self.w1, self.w2 = {}, {}
+            for axis in range(grid.dim):
+                for sigma in (-1, 1):
+                    c = [0, 0, 0]
+                    c[axis] = -sigma  # pull direction whose source is r + sigma e_axis
+                    i = sum((c[a] + 1) * 3 ** a for a in range(grid.dim))
+                    q = wall["q"][i]
+                    q = torch.where((q < 0.5) & (wall["far"][i] < 0), torch.full_like(q, 0.5), q)
+                    k1 = self.lines[(axis, sigma)][0]
+                    kopp = self.lines[(axis, -sigma)][0]
+                    use = (k1 == K_SOLID) & (kopp == K_FLUID) & grid.fluid
+                    self.w1[(axis, sigma)] = torch.where(use, (1 - 2 * q) / (1 + 2 * q), torch.zeros_like(q))
+            for axis in range(grid.dim):
+                for sigma in (-1, 1):
+                    k1, i1, k2, _ = self.lines[(axis, sigma)]
+                    beyond = (k1 == K_FLUID) & (k2 == K_SOLID)
+                    self.w2[(axis, sigma)] = torch.where(beyond, self.w1[(axis, sigma)][i1],
+                                                         torch.zeros(grid.N, dtype=torch.float64))
 
     def value(self, phi, phi_in, axis, sigma, dist):
-        """phi at r + dist*sigma*e_axis with ghosts (zero gradient or inlet Dirichlet)."""
+        """phi at r + dist*sigma*e_axis with ghosts (zero gradient or inlet Dirichlet, or the
+        ghost-point value at walls with sub-cell positions)."""
         k1, i1, k2, i2 = self.lines[(axis, sigma)]
         k, i = (k1, i1) if dist == 1 else (k2, i2)
-        return torch.where(k == K_INLET, torch.as_tensor(phi_in, dtype=phi.dtype), phi[i])
+        v = torch.where(k == K_INLET, torch.as_tensor(phi_in, dtype=phi.dtype), phi[i])
+        if self.w1 is None:
+            return v
+        w1 = self.w1[(axis, sigma)]
+        opp = phi[self.lines[(axis, -sigma)][1]]
+        g1 = phi + w1 * (opp - phi)  # ghost-point value; the zero-gradient one where w1 = 0
+        if dist == 1:
+            return torch.where(k1 == K_SOLID, g1, v)
+        v = torch.where(k1 == K_SOLID, g1, v)  # beyond a ghost: its copy
+        p1 = phi[i1]
+        w2 = self.w2[(axis, sigma)]
+        return torch.where(w2 != 0, p1 + w2 * (phi - p1), v)
 
     def velocity(self, u_axis, uin_axis_at_r, axis, sigma):
         """Velocity component at r + sigma e_axis: fluid value, 0 at walls, inlet value, or

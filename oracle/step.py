@@ -41,8 +41,8 @@ class Oracle:
         self.cs = CumulantSpace(self.lat)
         self.grid = geo.Grid(cfg, mask)
         self.code, self.src = geo.lb_links(self.lat, self.grid)
-        self.nb = geo.FDNeighbours(self.grid)
         self.wall = None if qwall is None else geo.wall_links(self.lat, self.grid, self.code, self.src, qwall)
+        self.nb = geo.FDNeighbours(self.grid, self.wall, self.lat)
         d = cfg["dim"]
         ny = cfg["ny"]
         nz = cfg["nz"] if d == 3 else 1

@@ -700,3 +700,54 @@ def test_variable_cp_temperature_operator_converges_to_the_pde():
         exact = f(rhs) / rho.numpy()
         errs.append(np.abs((T1 - T).numpy() - exact).max() / np.abs(exact).max())
     assert errs[2] < 1e-3 and errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, errs
+
+
+# ------------------------------------------------ ghost-point walls for the finite differences
+def _wall_conduction_rate(H, q, ghost):
+    """Decay rate per step of the slowest conduction mode between adiabatic walls at the fraction q
+    of the boundary links (walls at y = 0.5 - q and H - 0.5 + q, cell centres at j + 0.5), from
+    the oracle's FD update alone (fluid at rest, one inert species), and the exact rate
+    alpha (pi / width)^2 of the heat equation with zero-flux walls there."""
+    from oracle.lattice import Lattice
+    wl = W.generate.channel_2d(H=H, nx=4, q=q)
+    cfg = W.generate._base_cfg(2, 4, H, 1, "f64")
+    cfg.update({"bc": {"x": ("periodic", "periodic"), "y": ("wall", "wall")}, "dx": 1e-4, "dt": 1e-6,
+                "nu_ref": 1.5e-5, "thermal": True, "reactions": [], "T_in": 300.0, "Y_in": [1.0],
+                "species": [{"name": "A", "W": 0.029, "Le": 1.0, "hf": 0.0}]})
+    p = Params(cfg)
+    lat = Lattice(2)
+    grid = geo.Grid(cfg, np.zeros(4 * H, np.uint8))
+    code, src = geo.lb_links(lat, grid)
+    wall = geo.wall_links(lat, grid, code, src, wl.qwall) if ghost else None
+    nb = geo.FDNeighbours(grid, wall, lat)
+    lo, hi = 0.5 - q, H - 0.5 + q
+    yc = (np.arange(4 * H) // 4) + 0.5
+    T0, amp = 300.0, 0.01
+    T = torch.as_tensor(T0 + amp * np.cos(np.pi * (yc - lo) / (hi - lo)))
+    Y = torch.ones(1, 4 * H, dtype=f64)
+    u = torch.zeros(2, 4 * H, dtype=f64)
+    rho = p.P_th0 * 0.029 / (8.314462618 * T0 * p.rho_ref)
+    alpha = p.nu_lat * (T0 / p.T_ref) ** p.mu_exp / (p.Pr * rho)
+    A = []
+    for n in range(400):
+        if n in (100, 400 - 1):
+            A.append((T[:4].mean() - T[-4:].mean()).item())
+        T, Y, _, _ = fdm.fd_update(p, grid, nb, T, Y, u, u, p.P_th0, 0.0)
+    lam = np.log(A[0] / A[1]) / (400 - 1 - 100)
+    return lam, alpha * (np.pi / (hi - lo)) ** 2
+
+
+@pytest.mark.parametrize("q", [0.2, 0.8])
+def test_ghost_point_walls_conduct_heat_at_second_order(q):
+    """Slowest conduction mode between adiabatic walls at sub-cell positions: with the ghost-point
+    walls its decay rate converges to the exact one at second order (H = 8, 16, 32 cells); the
+    zero-gradient ghost (a wall on the cell face) misplaces the walls by 1/2 - q and stays an
+    order of magnitude off at H = 32."""
+    errs, errs0 = [], []
+    for H in (8, 16, 32):
+        lam, exact = _wall_conduction_rate(H, q, True)
+        errs.append(abs(lam / exact - 1))
+        lam0, _ = _wall_conduction_rate(H, q, False)
+        errs0.append(abs(lam0 / exact - 1))
+    assert errs[2] < 1e-3 and errs[0] / errs[1] > 2.5 and errs[1] / errs[2] > 3.3, errs
+    assert errs0[2] > 10 * errs[2], (errs, errs0)
