@@ -30,7 +30,8 @@ word 0.
 Packed stencil word of the finite-difference update: for axis a and side s (0: -, 1: +) the
 four bits at 4 (2a + s) hold the kind of the distance-1 point (bits 0-1: 0 fluid, 1 wall or
 solid, 2 inlet, 3 outlet) and of the distance-2 point (bits 2-3: 0 fluid, 1 zero-gradient copy
-of the distance-1 value, 2 inlet); bit 31 marks a fluid cell, a solid cell has word 0.
+of the distance-1 value, 2 inlet); bit 30 marks a cell with ghost-point wall weights; bit 31
+marks a fluid cell, a solid cell has word 0.
 """
 import torch
 
@@ -273,6 +274,12 @@ def pack_stencil_words(grid, nb):
             # distance-2 kind relative to the rule: fluid, zero-gradient copy, or inlet
             d2 = torch.where(k2 == K_FLUID, 0, torch.where(k2 == K_INLET, 2, 1))
             word |= (k1 | (d2 << 2)) << (4 * (2 * axis + side))
+    if nb.w1 is not None:
+        # bit 30: the cell has ghost-point wall weights on some side
+        flag = torch.zeros(grid.N, dtype=torch.bool)
+        for key in nb.w1:
+            flag |= (nb.w1[key] != 0) | (nb.w2[key] != 0)
+        word |= flag.to(torch.int64) << 30
     word |= grid.fluid.to(torch.int64) << 31
     word[~grid.fluid] = 0
     return word

@@ -43,6 +43,9 @@ struct lbm_ctx {
   int* wall_cells = nullptr;   // interpolated bounce-back list and table (lbm_set_wall_links)
   void* wall_q = nullptr;
   size_t wall_rows_cap = 0, n_wall = 0;
+  int* fd_row = nullptr;        // ghost-point wall weights of the FD update: row per flagged cell
+  void* fd_w = nullptr;         // [rows][2][2 D] in the field type
+  size_t fd_rows_cap = 0;
   uint32_t* sword = nullptr;
   uint8_t* mask = nullptr;
   void* inlet_u = nullptr;
@@ -314,6 +317,8 @@ template <typename R> FDArgs<R> make_fd_args(lbm_ctx* c, int cur) {
   a.lam_out = (R*)c->lam;
   a.partials = c->partials;
   a.pth = c->pth;
+  a.fd_row = c->fd_row;
+  a.fd_w = (const R*)c->fd_w;
   a.c = fdconst<R>(c);
   return a;
 }
@@ -1236,6 +1241,74 @@ template <typename R> lbm_status initial_T_adjoint_impl(lbm_ctx* ctx, const void
   return LBM_OK;
 }
 
+// Ghost-point weights of the FD update from the interpolated-wall rows (cells, Q fractions each,
+// the half-way fallback already applied): for a fluid cell whose distance-1 point along axis a on
+// side s is a wall or solid (stencil kind 1), whose opposite distance-1 point is fluid and whose
+// link toward that wall (pull direction c = -s e_a) has fraction q, w = (1 - 2q) / (1 + 2q); the
+// fluid cell on the opposite side gets the same weight for its distance-2 wall point. Flags the
+// stencil words of the cells with weights (SW_WALL) and uploads the rows.
+template <typename R> lbm_status set_fd_walls(lbm_ctx* ctx, const std::vector<int>& cells, const std::vector<R>& rows) {
+  const size_t N = ctx->N;
+  const int D = ctx->D, Q = ctx->Q;
+  const Geo& g = ctx->geo;
+  std::vector<uint32_t> sw(N);
+  CK(cudaMemcpyAsync(sw.data(), ctx->sword, N * 4, cudaMemcpyDeviceToHost, ctx->st), "copy stencil words");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  for (size_t r = 0; r < N; ++r) sw[r] &= ~SW_WALL;
+  std::vector<int> frow(N, -1);
+  std::vector<R> w;
+  const int W = 4 * D;
+  auto row_for = [&](int r) -> R* {
+    if (frow[r] < 0) {
+      frow[r] = (int)(w.size() / W);
+      w.insert(w.end(), W, R(0));
+    }
+    return w.data() + (size_t)frow[r] * W;
+  };
+  const int dims[3] = {g.nx, g.ny, g.nz};
+  const int strides[3] = {1, g.nx, g.nx * g.ny};
+  for (size_t k = 0; k < cells.size(); ++k) {
+    const int r = cells[k];
+    const uint32_t word = sw[r];
+    const int pos[3] = {r % g.nx, (r / g.nx) % g.ny, r / (g.nx * g.ny)};
+    for (int ax = 0; ax < D; ++ax)
+      for (int sd = 0; sd < 2; ++sd) {
+        const int k1 = (int)((word >> (4 * (2 * ax + sd))) & 3u);
+        const int ko = (int)((word >> (4 * (2 * ax + 1 - sd))) & 3u);
+        if (k1 != NB_SOLID || ko != NB_FLUID) continue;
+        int c[3] = {0, 0, 0};
+        c[ax] = sd ? -1 : 1;  // pull direction whose source is the wall point
+        const int i = (c[0] + 1) + 3 * (c[1] + 1) + (D == 3 ? 9 * (c[2] + 1) : 0);
+        const double q = (double)rows[k * Q + i];
+        if (q == 0.5) continue;
+        const R wv = (R)((1.0 - 2.0 * q) / (1.0 + 2.0 * q));
+        row_for(r)[2 * ax + sd] = wv;
+        // the opposite fluid point (periodic wrap as in the stencil) sees this wall at distance 2
+        int po = pos[ax] + (sd ? -1 : 1);
+        po = po < 0 ? po + dims[ax] : (po >= dims[ax] ? po - dims[ax] : po);
+        const int ro = r + (po - pos[ax]) * strides[ax];
+        const uint32_t wo = sw[ro];
+        if (((wo >> (4 * (2 * ax + sd))) & 15u) == (uint32_t)(NB_FLUID | (1 << 2))) row_for(ro)[2 * D + 2 * ax + sd] = wv;
+      }
+  }
+  const size_t nr = w.size() / W;
+  if (nr > 0) {
+    if (!ctx->fd_row && !(ctx->fd_row = (int*)dalloc(ctx, N * sizeof(int))))
+      return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+    if (nr > ctx->fd_rows_cap) {
+      if (!(ctx->fd_w = dalloc(ctx, nr * W * sizeof(R)))) return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+      ctx->fd_rows_cap = nr;
+    }
+    for (size_t r = 0; r < N; ++r)
+      if (frow[r] >= 0) sw[r] |= SW_WALL;
+    CK(cudaMemcpyAsync(ctx->fd_row, frow.data(), N * sizeof(int), cudaMemcpyHostToDevice, ctx->st), "copy rows");
+    CK(cudaMemcpyAsync(ctx->fd_w, w.data(), nr * W * sizeof(R), cudaMemcpyHostToDevice, ctx->st), "copy weights");
+  }
+  CK(cudaMemcpyAsync(ctx->sword, sw.data(), N * 4, cudaMemcpyHostToDevice, ctx->st), "copy stencil words");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  return LBM_OK;
+}
+
 // Build the interpolated-wall table from a list of links (cell, pull direction, fraction);
 // later entries for the same link replace earlier ones.
 template <typename R>
@@ -1293,6 +1366,10 @@ lbm_status set_wall_impl(lbm_ctx* ctx, long long n_links, const int* cell, const
     for (size_t k = 0; k < n; ++k) lw[cells[k]] |= LINK_WALL;
     CK(cudaMemcpyAsync(ctx->wall_cells, cells.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->st), "copy wall list");
     CK(cudaMemcpyAsync(ctx->wall_q, rows.data(), n * Q * sizeof(R), cudaMemcpyHostToDevice, ctx->st), "copy wall table");
+  }
+  {
+    lbm_status s2 = set_fd_walls<R>(ctx, cells, rows);
+    if (s2 != LBM_OK) return s2;
   }
   CK(cudaMemcpyAsync(ctx->links, lw.data(), N * 4, cudaMemcpyHostToDevice, ctx->st), "copy links");
   CK(cudaStreamSynchronize(ctx->st), "sync");

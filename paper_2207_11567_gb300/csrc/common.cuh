@@ -171,6 +171,8 @@ template <typename R> struct LBArgs {
 
 constexpr int FD_BLOCK = 256;
 enum { NB_FLUID = 0, NB_SOLID = 1, NB_INLET = 2, NB_OUTLET = 3 };
+// Stencil-word flag: the cell has ghost-point wall weights (fd_row / fd_w of FDArgs).
+constexpr uint32_t SW_WALL = 1u << 30;
 
 template <typename R> struct FDArgs {
   Geo geo;
@@ -187,6 +189,11 @@ template <typename R> struct FDArgs {
   R* lam_out;         // [N]
   void* partials;     // [grid][2] fixed-point int64 (float path) or double (double path)
   const PthState* pth;
+  // ghost-point walls: for a cell flagged SW_WALL, row fd_row[r] of fd_w holds, per axis side
+  // 2a + s, the weight w of the distance-1 wall ghost (phi_r + w (phi_opposite - phi_r)) and then
+  // that of the distance-2 wall ghost seen past the fluid neighbour (phi_1 + w (phi_r - phi_1))
+  const int* fd_row;
+  const R* fd_w;      // [rows][2][2 D]
   FDConst<R> c;
 };
 

@@ -196,6 +196,22 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
         }
       }
     }
+    // ghost-point wall weights (0: the zero-gradient ghost)
+    R wg1[3][2], wg2[3][2];
+    bool gw = false;
+    if constexpr (!FAST) {
+      gw = (sw & SW_WALL) != 0u;
+      if (gw) {
+        const R* wr = a.fd_w + (size_t)__ldg(a.fd_row + r) * (4 * D);
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax)
+#pragma unroll
+          for (int sd = 0; sd < 2; ++sd) {
+            wg1[ax][sd] = wr[2 * ax + sd];
+            wg2[ax][sd] = wr[2 * D + 2 * ax + sd];
+          }
+      }
+    }
     // local state
     constexpr int KMAX = NK > 0 ? NK : MAX_SP;
     constexpr int RMAX = NR > 0 ? NR : MAX_RX;
@@ -256,7 +272,8 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
       for (int sd = 0; sd < 2; ++sd) {
         const int kk = k1[ax][sd];
         const int j = i1[ax][sd];
-        const R Tn = kk == NB_FLUID ? ldg(a.T + j) : (kk == NB_INLET ? c.T_in : Tr);
+        R Tn = kk == NB_FLUID ? ldg(a.T + j) : (kk == NB_INLET ? c.T_in : Tr);
+        if (!FAST && gw && kk == NB_SOLID) Tn = Tr + wg1[ax][sd] * (ldg(a.T + i1[ax][1 - sd]) - Tr);
         const R Fn = (a.Floc && kk == NB_FLUID) ? ldg(a.Floc + j) : Fr;
         const R mun = c.nu_lat * powr<R>(Tn * c.T_ref_inv, c.mu_exp);
         FMf[ax][sd] = R(0.5) * (Fr * mur + Fn * mun);
@@ -311,10 +328,28 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
 #pragma unroll
       for (int ax = 0; ax < D; ++ax) {
         // m1 = phi(r - e), m2 = phi(r - 2e), p1 = phi(r + e), p2 = phi(r + 2e)
-        const R m1 = k1[ax][0] == NB_INLET ? phin : ldg(phi + i1[ax][0]);
-        const R m2 = k2[ax][0] == 2 ? phin : ldg(phi + i2[ax][0]);
-        const R p1 = k1[ax][1] == NB_INLET ? phin : ldg(phi + i1[ax][1]);
-        const R p2 = k2[ax][1] == 2 ? phin : ldg(phi + i2[ax][1]);
+        R m1 = k1[ax][0] == NB_INLET ? phin : ldg(phi + i1[ax][0]);
+        R m2 = k2[ax][0] == 2 ? phin : ldg(phi + i2[ax][0]);
+        R p1 = k1[ax][1] == NB_INLET ? phin : ldg(phi + i1[ax][1]);
+        R p2 = k2[ax][1] == 2 ? phin : ldg(phi + i2[ax][1]);
+        if (!FAST && gw) {
+          // ghost-point walls: a distance-1 wall ghost from the parabola through the cell and the
+          // opposite point with zero slope at the wall; a distance-2 point copies it, or past a
+          // fluid neighbour takes that neighbour's wall ghost
+          const R m1r = m1, p1r = p1;
+          if (k1[ax][0] == NB_SOLID) {
+            m1 = pr + wg1[ax][0] * (p1r - pr);
+            m2 = m1;
+          } else if (wg2[ax][0] != R(0)) {
+            m2 = m1r + wg2[ax][0] * (pr - m1r);
+          }
+          if (k1[ax][1] == NB_SOLID) {
+            p1 = pr + wg1[ax][1] * (m1r - pr);
+            p2 = p1;
+          } else if (wg2[ax][1] != R(0)) {
+            p2 = p1r + wg2[ax][1] * (pr - p1r);
+          }
+        }
         // WENO3 written with the one-sided differences around r, shared by both faces and the
         // diffusion flux: face = b + (t(d_bc) d_ab + 2 t(d_ab) d_bc) / (2 (t(d_bc) + 2 t(d_ab)))
         // with t(d) = (eps + d^2)^2 (b the upwind value, d_ab, d_bc its upwind-side differences)

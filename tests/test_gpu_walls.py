@@ -122,3 +122,67 @@ def test_swirl3d_curved_walls_f32():
     floor = compare(wl, {"u": st32["u"].numpy(), "P_h": st32["P_h"].numpy(), "g": st32["g"].numpy()}, st)
     bad = {k: (v, floor[k]) for k, v in errs.items() if not v <= max(3e-5, 3.0 * floor[k])}
     assert not bad, (errs, floor)
+
+
+def _thermal_walls(storage, seed=12):
+    """Reacting chamber with an inlet whose every bounce-back link (obstacles, top and bottom walls)
+    carries a seeded wall fraction in [0.1, 0.9]: interpolated bounce-back for the populations and
+    ghost-point walls for temperature and species."""
+    wl = W.generate.chamber_2d(nx=64, ny=32, inlet=True, dt=5e-7, storage=storage, seed=seed, u_init=0.01,
+                               n_rows=1, per_row=2)
+    rng = np.random.default_rng(seed)
+    q = rng.uniform(0.1, 0.9, (9, wl.N))
+    if storage != "f64":
+        q = q.astype(np.float32).astype(np.float64)
+    wl.qwall = q
+    return wl
+
+
+def test_thermal_ghost_point_walls_f64():
+    wl = _thermal_walls("f64")
+    o, st = _oracle(wl, 100)
+    gpu = gpu_run(wl, 100)
+    _links_match(o, gpu)
+    sw = o.stencil_words_packed().numpy()
+    assert ((sw >> 30) & 1).sum() > 50  # cells with ghost-point weights
+    assert np.array_equal(gpu["stencil_words"].astype(np.int64), sw)
+    errs = compare(wl, gpu, st)
+    assert max(errs.values()) < 1e-10, errs
+
+
+def test_thermal_ghost_point_walls_change_the_solution():
+    """The ghost-point weights are live: the same run with the walls at half-way differs in T."""
+    wl = _thermal_walls("f64")
+    a = gpu_run(wl, 100)
+    wl.qwall = None
+    b = gpu_run(wl, 100)
+    fluid = wl.mask == 0
+    assert np.abs(a["T"][fluid] - b["T"][fluid]).max() > 1e-3
+
+
+def test_thermal_ghost_point_walls_f32():
+    wl = _thermal_walls("f32")
+    o, st = _oracle(wl, 100)
+    gpu = gpu_run(wl, 100)
+    errs = compare(wl, gpu, st)
+    _, st32 = _oracle(wl, 100, store_round="f32")
+    floor = compare(wl, {k: st32[k].numpy() for k in ("u", "P_h", "g", "T", "Y", "rho", "lam")}, st)
+    bad = {k: (v, floor[k]) for k, v in errs.items() if not v <= max(3e-5, 3.0 * floor[k])}
+    assert not bad, (errs, floor)
+
+
+def test_swirl3d_reactive_curved_walls_f64():
+    """3-D reacting burner with the interpolated walls of the injector cylinders and the exhaust
+    cone (open domain, no sensor): populations and the ghost-point walls of T and Y in D3Q27."""
+    wl = W.generate.swirl_3d(32, 18, 18, reactive=True, curved=True, storage="f64", seed=6)
+    wl.cfg["flame_sensor"] = False
+    wl.cfg["closed_domain"] = False
+    c, d, q = wl.info["wall_links"]
+    dense = np.zeros((27, wl.N))
+    dense[d, c] = q
+    o, st = _oracle_q(wl, dense, 20)
+    gpu = gpu_run(wl, 20)
+    _links_match(o, gpu)
+    assert np.array_equal(gpu["stencil_words"].astype(np.int64), o.stencil_words_packed().numpy())
+    errs = compare(wl, gpu, st)
+    assert max(errs.values()) < 1e-10, errs
