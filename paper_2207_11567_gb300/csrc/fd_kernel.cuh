@@ -158,7 +158,7 @@ template <int DEG, typename R> __device__ __forceinline__ R hW_eval(const R (&a)
 // lambda = F mu c_p / Pr per cell (face value the arithmetic mean, a ghost neighbour's c_p from its
 // ghost T and Y), centred gradients. The species fields run first so that the neighbours' c_p and
 // the species-enthalpy flux are summed before the temperature field.
-template <int D, typename R, int NK, int NR, bool FAST, int VDEG>
+template <int D, typename R, int NK, int NR, bool FAST, int VDEG, bool GW = false>
 __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z, int r, uint32_t sw, R& termI,
                                         R& termM) {
   const FDConst<R>& c = a.c;
@@ -196,21 +196,18 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
         }
       }
     }
-    // ghost-point wall weights (0: the zero-gradient ghost)
-    R wg1[3][2], wg2[3][2];
-    bool gw = false;
-    if constexpr (!FAST) {
-      gw = (sw & SW_WALL) != 0u;
-      if (gw) {
-        const R* wr = a.fd_w + (size_t)__ldg(a.fd_row + r) * (4 * D);
+    // GW: ghost-point wall weights of this cell (0: the zero-gradient ghost); a separate copy of
+    // the update, so that the other cells carry none of its registers
+    R wg1[GW ? 3 : 1][2], wg2[GW ? 3 : 1][2];
+    if constexpr (GW) {
+      const R* wr = a.fd_w + (size_t)__ldg(a.fd_row + r) * (4 * D);
 #pragma unroll
-        for (int ax = 0; ax < D; ++ax)
+      for (int ax = 0; ax < D; ++ax)
 #pragma unroll
-          for (int sd = 0; sd < 2; ++sd) {
-            wg1[ax][sd] = wr[2 * ax + sd];
-            wg2[ax][sd] = wr[2 * D + 2 * ax + sd];
-          }
-      }
+        for (int sd = 0; sd < 2; ++sd) {
+          wg1[ax][sd] = wr[2 * ax + sd];
+          wg2[ax][sd] = wr[2 * D + 2 * ax + sd];
+        }
     }
     // local state
     constexpr int KMAX = NK > 0 ? NK : MAX_SP;
@@ -273,7 +270,9 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
         const int kk = k1[ax][sd];
         const int j = i1[ax][sd];
         R Tn = kk == NB_FLUID ? ldg(a.T + j) : (kk == NB_INLET ? c.T_in : Tr);
-        if (!FAST && gw && kk == NB_SOLID) Tn = Tr + wg1[ax][sd] * (ldg(a.T + i1[ax][1 - sd]) - Tr);
+        if constexpr (GW) {
+          if (kk == NB_SOLID) Tn = Tr + wg1[ax][sd] * (ldg(a.T + i1[ax][1 - sd]) - Tr);
+        }
         const R Fn = (a.Floc && kk == NB_FLUID) ? ldg(a.Floc + j) : Fr;
         const R mun = c.nu_lat * powr<R>(Tn * c.T_ref_inv, c.mu_exp);
         FMf[ax][sd] = R(0.5) * (Fr * mur + Fn * mun);
@@ -332,7 +331,7 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
         R m2 = k2[ax][0] == 2 ? phin : ldg(phi + i2[ax][0]);
         R p1 = k1[ax][1] == NB_INLET ? phin : ldg(phi + i1[ax][1]);
         R p2 = k2[ax][1] == 2 ? phin : ldg(phi + i2[ax][1]);
-        if (!FAST && gw) {
+        if constexpr (GW) {
           // ghost-point walls: a distance-1 wall ghost from the parabola through the cell and the
           // opposite point with zero slope at the wall; a distance-2 point copies it, or past a
           // fluid neighbour takes that neighbour's wall ghost
@@ -451,6 +450,7 @@ __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? (VDEG > 0 ? HLBM_FD
     const bool fast = ghosts == 0u && x >= 2 && x < g.nx - 2 && y >= 2 && y < g.ny - 2 &&
                       (D == 2 || (z >= 2 && z < g.nz - 2));
     if (fast) fd_cell<D, R, NK, NR, true, VDEG>(a, x, y, z, r, sw, termI, termM);
+    else if (sw & SW_WALL) fd_cell<D, R, NK, NR, false, VDEG, true>(a, x, y, z, r, sw, termI, termM);
     else fd_cell<D, R, NK, NR, false, VDEG>(a, x, y, z, r, sw, termI, termM);
   }
   if (!c.closed) return;  // uniform across the grid
