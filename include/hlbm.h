@@ -191,7 +191,12 @@ lbm_status lbm_get_stencil_words(lbm_ctx* ctx, uint32_t* dst, int dst_on_device)
  * entries are ignored, and q = 1/2 is half-way bounce-back (the default). A link with q < 1/2
  * whose node r + c_i is not fluid, and links of the inlet and outlet faces, stay half-way.
  * NULL clears the data. Must follow lbm_set_geometry (which clears it); synchronises the
- * stream. The finite-difference walls stay zero-gradient. */
+ * stream. The finite-difference update uses the same fractions for its walls (ghost points): where
+ * the distance-1 point along an axis is a wall or solid, the link toward it has fraction q and the
+ * opposite point is fluid, the ghost value is phi_r + w (phi_opposite - phi_r) with
+ * w = (1 - 2q) / (1 + 2q) (zero slope of the parabola through the two points at the wall); a
+ * distance-2 wall point copies that ghost, or past a fluid neighbour takes the neighbour's. Cells
+ * with such weights carry bit 30 of their stencil word (lbm_get_stencil_words). */
 lbm_status lbm_set_wall_fractions(lbm_ctx* ctx, const double* q);
 
 /* The same as a list of n_links links (host arrays): cell index r, pull direction i and the wall
