@@ -180,7 +180,8 @@ lbm_status lbm_get_links(lbm_ctx* ctx, uint32_t* dst, int dst_on_device);
 /* Per-cell stencil words of the finite-difference update (uint32, N): for axis a and side s
  * (0: minus, 1: plus) the four bits at 4*(2a+s) hold the kind of the distance-1 point (bits 0-1:
  * 0 fluid, 1 wall or solid, 2 inlet, 3 outlet) and of the distance-2 point (bits 2-3: 0 fluid,
- * 1 zero-gradient copy of the distance-1 value, 2 inlet); bit 31 marks a fluid cell, solid cells
+ * 1 zero-gradient copy of the distance-1 value, 2 inlet); bit 30 marks a cell with ghost-point
+ * wall weights (see lbm_set_wall_fractions); bit 31 marks a fluid cell, solid cells
  * hold 0. Integer output, comparable bit for bit. */
 lbm_status lbm_get_stencil_words(lbm_ctx* ctx, uint32_t* dst, int dst_on_device);
 
