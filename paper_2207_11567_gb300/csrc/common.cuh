@@ -140,9 +140,11 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
 
 // ---------------------------------------------------------------------------- kernel arguments
 constexpr int LB_BLOCK = 128;
-// resident blocks per SM the register allocation aims for (6: 80 registers, no spill)
+// resident blocks per SM the register allocation aims for (C4, D3Q27 thermal: 6 blocks 80
+// registers, LB 0.738 / 0.764 ms FP32 / FP16 storage; 7 blocks 0.736 / 0.737 ms; 8 blocks, 64
+// registers with spills, 0.767 / 0.807 ms)
 #ifndef LB_MIN_BLOCKS
-#define LB_MIN_BLOCKS 6
+#define LB_MIN_BLOCKS 7
 #endif
 
 // link word bit 30: the cell has interpolated bounce-back links (it is on the wall list)
