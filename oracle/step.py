@@ -89,20 +89,10 @@ class Oracle:
         return st
 
     def _integral(self, T, Y):
-        f = self.grid.fluid
-        return fdm.pth_integrand(self.p, T, Y)[f].sum().item()
+        return pth_integral(self.p, self.grid, T, Y)
 
     def _mass_flux(self, st, rho):
-        """Inlet minus outlet mass per step (lattice units), level n."""
-        p = self.p
-        m = 0.0
-        if self.at_inlet.any():
-            W_in = 1.0 / sum(p.Y_in[k] / p.W[k] for k in range(p.K))
-            rho_in = st["P_th"] * W_in / (R_GAS * p.T_in * p.rho_ref)
-            m += (rho_in * self.uin_r[0][self.at_inlet]).sum().item()
-        if self.at_outlet.any():
-            m -= (rho[self.at_outlet] * st["u"][0][self.at_outlet]).sum().item()
-        return m
+        return boundary_mass_flux(self.p, self.at_inlet, self.at_outlet, self.uin_r, st, rho)
 
     # ------------------------------------------------------------------ step
     def grad_rho(self, rho):
@@ -115,14 +105,18 @@ class Oracle:
             out.append(0.5 * (vals[1] - vals[0]))
         return torch.stack(out)
 
-    def step(self, st):
+    def step(self, st, P_next=None):
+        """One step. P_next: thermodynamic pressure after the step, given from outside (a patch
+        of a larger closed domain, whose integral the patch cannot form)."""
         p, lat, fluid = self.p, self.lat, self.grid.fluid
         N = self.grid.N
         new = dict(st)
         if p.thermal:
             T1, Y1, rho, lam_fd = fdm.fd_update(p, self.grid, self.nb, st["T"], st["Y"], st["u"],
                                                 self.uin_r, st["P_th"], st["dP_lag"])
-            if p.closed:
+            if P_next is not None:
+                M1, P1 = st["M"], P_next
+            elif p.closed:
                 M1 = st["M"] + self._mass_flux(st, rho)
                 I1 = self._integral(torch.where(fluid, T1, st["T"]), torch.where(fluid, Y1, st["Y"]))
                 P1 = M1 / I1
@@ -169,3 +163,45 @@ class Oracle:
         for _ in range(n):
             st = self.round_state(self.step(st))
         return st
+
+
+def pth_integral(p, grid, T, Y):
+    """I = sum over fluid cells of W / (R T rho_ref) (cell volume 1): P_th = M / I (reading c5)."""
+    return fdm.pth_integrand(p, T, Y)[grid.fluid].sum().item()
+
+
+def boundary_mass_flux(p, at_inlet, at_outlet, uin_r, st, rho):
+    """Inlet minus outlet mass per step (lattice units), level n."""
+    m = 0.0
+    if at_inlet.any():
+        W_in = 1.0 / sum(p.Y_in[k] / p.W[k] for k in range(p.K))
+        rho_in = st["P_th"] * W_in / (R_GAS * p.T_in * p.rho_ref)
+        m += (rho_in * uin_r[0][at_inlet]).sum().item()
+    if at_outlet.any():
+        m -= (rho[at_outlet] * st["u"][0][at_outlet]).sum().item()
+    return m
+
+
+def first_step_pressure(cfg, mask, inlet_u, T, Y, u):
+    """Thermodynamic pressure after the first step of a closed domain from the initial fields: the
+    finite-difference update over the whole grid and the mass balance, without the lattice
+    Boltzmann part (a full-size grid's populations would not fit the oracle's memory). Used with
+    Oracle.step(P_next=...) on patches of that grid."""
+    p = Params(cfg)
+    grid = geo.Grid(cfg, mask)
+    nb = geo.FDNeighbours(grid)
+    d = cfg["dim"]
+    nz = cfg["nz"] if d == 3 else 1
+    face = torch.as_tensor(inlet_u, dtype=torch.float64).reshape(d, cfg["ny"] * nz)
+    uin_r = face[:, grid.face_index()]
+    at_inlet = grid.fluid & (grid.coord[0] == 0) & torch.tensor(grid.bc[0][0] == geo.INLET)
+    at_outlet = grid.fluid & (grid.coord[0] == grid.shape[0] - 1) & torch.tensor(grid.bc[0][1] == geo.OUTLET)
+    T = torch.as_tensor(T, dtype=torch.float64)
+    Y = torch.as_tensor(Y, dtype=torch.float64)
+    u = torch.as_tensor(u, dtype=torch.float64).reshape(d, grid.N)
+    st = {"P_th": p.P_th0, "u": u}
+    M0 = p.P_th0 * pth_integral(p, grid, T, Y)
+    T1, Y1, rho, _ = fdm.fd_update(p, grid, nb, T, Y, u, uin_r, p.P_th0, 0.0)
+    M1 = M0 + boundary_mass_flux(p, at_inlet, at_outlet, uin_r, st, rho)
+    I1 = pth_integral(p, grid, torch.where(grid.fluid, T1, T), torch.where(grid.fluid, Y1, Y))
+    return M1 / I1
