@@ -7,8 +7,8 @@ the thermodynamic pressure after the step (finite-difference update over the who
 mass balance, oracle.step.first_step_pressure), and runs the whole step on a 7 x 7 x 7 patch
 around each sampled cell (radius 2 for the finite differences of the cell's neighbours, 1 for the
 pull of their populations) with that pressure. Samples: random fluid cells, cells on the inlet
-and outlet faces and cells next to walls. Bound per field: max(1e-5, 3 x the FP32 storage floor),
-the floor being the same patch step with the state rounded to FP32 storage before and after."""
+and outlet faces and cells next to walls. Bound per field: max(1e-5, 3 x the storage floor), the
+floor being the same patch step with the state rounded to the storage type before and after."""
 import copy
 
 import numpy as np
@@ -71,11 +71,15 @@ def _samples(wl, rng):
                            pick(flat(near), 24)])
 
 
-def test_c4_full_size_one_step_on_sampled_cells():
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_c4_full_size_one_step_on_sampled_cells(storage):
+    """FP32 arithmetic with FP32 or FP16 population storage (the benchmark's two variants); the
+    floor rounds the oracle's state to the same storage."""
     from oracle.step import first_step_pressure
     from paper_2207_11567_gb300 import from_workload
     wl = W.make("c4_swirl_reactive_3d")
     assert wl.cfg["storage"] == "f32" and wl.cfg["closed_domain"] and wl.cfg["flame_sensor"]
+    wl.cfg["storage"] = storage
     s = from_workload(wl)
     s.step(1)
     gpu = s.fields()
@@ -89,7 +93,7 @@ def test_c4_full_size_one_step_on_sampled_cells():
     got = {k: [] for k in FIELDS}
     for r in cells:
         a = _patch_step(wl, int(r), P1)
-        b = _patch_step(wl, int(r), P1, store_round="f32")
+        b = _patch_step(wl, int(r), P1, store_round=storage)
         for k in FIELDS:
             ref[k].append(a[k])
             rnd[k].append(b[k])
