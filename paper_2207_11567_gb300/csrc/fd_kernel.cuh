@@ -200,13 +200,16 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
     // the update, so that the other cells carry none of its registers
     R wg1[GW ? 3 : 1][2], wg2[GW ? 3 : 1][2];
     if constexpr (GW) {
-      const R* wr = a.fd_w + (size_t)__ldg(a.fd_row + r) * (4 * D);
+      // a cell without weights (in a warp that takes this copy for another lane) gets zeros,
+      // which reproduce the zero-gradient ghosts exactly
+      const bool has = (sw & SW_WALL) != 0u;
+      const R* wr = a.fd_w + (size_t)(has ? __ldg(a.fd_row + r) : 0) * (4 * D);
 #pragma unroll
       for (int ax = 0; ax < D; ++ax)
 #pragma unroll
         for (int sd = 0; sd < 2; ++sd) {
-          wg1[ax][sd] = wr[2 * ax + sd];
-          wg2[ax][sd] = wr[2 * D + 2 * ax + sd];
+          wg1[ax][sd] = has ? wr[2 * ax + sd] : R(0);
+          wg2[ax][sd] = has ? wr[2 * D + 2 * ax + sd] : R(0);
         }
     }
     // local state
@@ -444,13 +447,18 @@ __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? (VDEG > 0 ? HLBM_FD
   const bool active = (sw >> 31) != 0u;
   R termI = R(0), termM = R(0);  // P_th integrand and boundary mass flux of this cell
 
+  // interior fast path: stencil word without any non-fluid neighbour, cell 2 away from every face
+  const uint32_t ghosts = sw & (D == 3 ? 0x00ffffffu : 0x0000ffffu);
+  const bool fast = ghosts == 0u && x >= 2 && x < g.nx - 2 && y >= 2 && y < g.ny - 2 &&
+                    (D == 2 || (z >= 2 && z < g.nz - 2));
+  // one copy of the update per warp (a warp is a row of 32 cells along x): a warp whose cells
+  // would take different copies takes the most general one any of them needs, rather than
+  // issuing several in turn; the copies compute identical values
+  const bool warp_fast = __all_sync(0xffffffffu, !active || fast);
+  const bool warp_walls = __any_sync(0xffffffffu, active && (sw & SW_WALL) != 0u);
   if (active) {
-    // interior fast path: stencil word without any non-fluid neighbour, cell 2 away from every face
-    const uint32_t ghosts = sw & (D == 3 ? 0x00ffffffu : 0x0000ffffu);
-    const bool fast = ghosts == 0u && x >= 2 && x < g.nx - 2 && y >= 2 && y < g.ny - 2 &&
-                      (D == 2 || (z >= 2 && z < g.nz - 2));
-    if (fast) fd_cell<D, R, NK, NR, true, VDEG>(a, x, y, z, r, sw, termI, termM);
-    else if (sw & SW_WALL) fd_cell<D, R, NK, NR, false, VDEG, true>(a, x, y, z, r, sw, termI, termM);
+    if (warp_fast) fd_cell<D, R, NK, NR, true, VDEG>(a, x, y, z, r, sw, termI, termM);
+    else if (warp_walls) fd_cell<D, R, NK, NR, false, VDEG, true>(a, x, y, z, r, sw, termI, termM);
     else fd_cell<D, R, NK, NR, false, VDEG>(a, x, y, z, r, sw, termI, termM);
   }
   if (!c.closed) return;  // uniform across the grid
