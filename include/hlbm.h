@@ -281,7 +281,9 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* src_device);
  * kernel launch of lbm_step; lbm_kernel_times returns, per kernel kind, the summed device time
  * in ms and the launch count since the last reset:
  *   kind 0 finite-difference update, 1 flame sensor, 2 thermodynamic pressure, 3 lattice
- *   Boltzmann stream-collide. Synchronises the stream. */
+ *   Boltzmann stream-collide. The flame-sensor pass runs only for the first step after the state
+ *   was set from outside (lbm_set_fields, lbm_load_state); afterwards each finite-difference
+ *   update writes the sensor's F_loc of the state it produces. Synchronises the stream. */
 #define LBM_KERNEL_KINDS 4
 lbm_status lbm_profile(lbm_ctx* ctx, int enable);
 lbm_status lbm_kernel_times(lbm_ctx* ctx, double ms[LBM_KERNEL_KINDS], long long launches[LBM_KERNEL_KINDS]);

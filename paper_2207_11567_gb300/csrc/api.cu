@@ -38,7 +38,8 @@ struct lbm_ctx {
   void* rho = nullptr;
   void* lam = nullptr;
   void* ph = nullptr;
-  void* Floc = nullptr;
+  void* Floc[2] = {nullptr, nullptr};  // flame sensor F_loc of state cur / the next state
+  bool floc_ok = false;                 // Floc[cur] belongs to the current state
   uint32_t* links = nullptr;
   int* wall_cells = nullptr;   // interpolated bounce-back list and table (lbm_set_wall_links)
   void* wall_q = nullptr;
@@ -312,7 +313,8 @@ template <typename R> FDArgs<R> make_fd_args(lbm_ctx* c, int cur) {
   a.Y_out = (R*)c->Y[1 - cur];
   a.u = (const R*)c->u;
   a.inlet_u = (const R*)c->inlet_u;
-  a.Floc = c->cfg.flame_sensor ? (R*)c->Floc : nullptr;
+  a.Floc = c->cfg.flame_sensor ? (R*)c->Floc[cur] : nullptr;
+  a.Floc_out = c->cfg.flame_sensor ? (R*)c->Floc[1 - cur] : nullptr;
   a.rho_out = (R*)c->rho;
   a.lam_out = (R*)c->lam;
   a.partials = c->partials;
@@ -375,7 +377,11 @@ cudaError_t pth_thunk(lbm_ctx* c, int, int) {
 cudaError_t enqueue_step(lbm_ctx* c, int cur, bool want_out) {
   cudaError_t e;
   if (c->cfg.thermal) {
-    if (c->cfg.flame_sensor && (e = timed(c, KIND_SENSOR, fd_thunk, cur, 1)) != cudaSuccess) return e;
+    // the FD update writes F_loc of the state it produces; the sensor pass runs only when the
+    // state came from outside (lbm_step ensures it before any capture)
+    if (c->cfg.flame_sensor && !c->floc_ok && (e = timed(c, KIND_SENSOR, fd_thunk, cur, 1)) != cudaSuccess)
+      return e;
+    if (c->cfg.flame_sensor) c->floc_ok = true;
     if ((e = timed(c, KIND_FD, fd_thunk, cur, 0)) != cudaSuccess) return e;
     if (c->cfg.closed_domain && (e = timed(c, KIND_PTH, pth_thunk, cur, 0)) != cudaSuccess) return e;
   }
@@ -491,7 +497,8 @@ lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
       ok = ok && (ctx->T[b] = dalloc(ctx, N * ctx->F));
       ok = ok && (ctx->Y[b] = dalloc(ctx, (size_t)ctx->K * N * ctx->F));
     }
-    if (c.flame_sensor) ok = ok && (ctx->Floc = dalloc(ctx, N * ctx->F));
+    if (c.flame_sensor)
+      for (int b = 0; b < 2; ++b) ok = ok && (ctx->Floc[b] = dalloc(ctx, N * ctx->F));
   }
   if (!ok) {
     dfree_all(ctx);
@@ -499,7 +506,8 @@ lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
   }
   CK(cudaMemsetAsync(ctx->flag, 0, 16, ctx->st), "memset");
   CK(cudaMemsetAsync(ctx->inlet_u, 0, (size_t)ctx->D * c.ny * c.nz * ctx->F, ctx->st), "memset");
-  if (ctx->Floc) CK(cudaMemsetAsync(ctx->Floc, 0, N * ctx->F, ctx->st), "memset");
+  for (int b = 0; b < 2; ++b)
+    if (ctx->Floc[b]) CK(cudaMemsetAsync(ctx->Floc[b], 0, N * ctx->F, ctx->st), "memset");
   return LBM_OK;
 }
 
@@ -624,6 +632,7 @@ lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* mask, const double* inl
   for (size_t i = 0; i < N; ++i) nfl += hm[i] == 0;
   ctx->n_fluid = nfl;
   ctx->have_geo = true;
+  ctx->floc_ok = false;
   ctx->n_wall = 0;  // the rebuilt link words carry no interpolated walls
   drop_graphs(ctx);
   return LBM_OK;
@@ -739,6 +748,7 @@ lbm_status lbm_set_fields(lbm_ctx* ctx, const double* T, const double* Y, const 
   ctx->cur = 0;
   ctx->steps = 0;
   ctx->have_fields = true;
+  ctx->floc_ok = false;
   CK(cudaMemsetAsync(ctx->flag, 0, 16, ctx->st), "memset");
   return LBM_OK;
 }
@@ -749,6 +759,11 @@ lbm_status lbm_step(lbm_ctx* ctx, int n_steps) {
   if (!ctx->have_fields) return fail(ctx, LBM_ERR_STATE, "set_fields must come first");
   if (n_steps == 0) return LBM_OK;
   CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  if (ctx->cfg.thermal && ctx->cfg.flame_sensor && !ctx->floc_ok) {
+    // F_loc of a state set from outside, before any graph is captured or replayed
+    CK(timed(ctx, KIND_SENSOR, fd_thunk, ctx->cur, 1), "flame sensor");
+    ctx->floc_ok = true;
+  }
   if (ctx->st_on || ctx->pr_on) {
     // statistics and probes: direct launches; a sampled step also writes P_h, then the
     // accumulators update and the probe values are copied into the ring
@@ -909,6 +924,7 @@ size_t lbm_state_bytes(const lbm_ctx* ctx) {
 }
 
 static lbm_status copy_state(lbm_ctx* ctx, char* dev, bool save) {
+  if (!save) ctx->floc_ok = false;  // a new state: its F_loc is computed before the next step
   const size_t N = ctx->N;
   auto mv = [&](void* state, size_t bytes) -> cudaError_t {
     cudaError_t e = save ? cudaMemcpyAsync(dev, state, bytes, cudaMemcpyDeviceToDevice, ctx->st)
@@ -983,8 +999,9 @@ lbm_status lbm_kernel_bytes(const lbm_ctx* ctx, double bytes[LBM_KERNEL_KINDS]) 
   const double N = (double)ctx->N, Nf = (double)ctx->n_fluid, S = (double)ctx->S, F = (double)ctx->F;
   const double K = ctx->K, D = ctx->D, Q = ctx->Q;
   const bool th = ctx->cfg.thermal;
-  // FD: read T, Y, u; write T, Y, rho, Lambda; mask per cell; flame factor when the sensor is on
-  bytes[KIND_FD] = th ? Nf * ((2.0 * (1 + K) + D + 2.0 + (ctx->cfg.flame_sensor ? 1.0 : 0.0)) * F) + 4.0 * N : 0.0;
+  // FD: read T, Y, u; write T, Y, rho, Lambda; stencil word per cell; with the sensor, read F_loc
+  // of this state and write that of the next
+  bytes[KIND_FD] = th ? Nf * ((2.0 * (1 + K) + D + 2.0 + (ctx->cfg.flame_sensor ? 2.0 : 0.0)) * F) + 4.0 * N : 0.0;
   bytes[KIND_SENSOR] = (th && ctx->cfg.flame_sensor) ? Nf * 4.0 * F + N : 0.0;
   bytes[KIND_PTH] = (th && ctx->cfg.closed_domain) ? 16.0 * ctx->nblocks_fd : 0.0;
   // LB: populations read + written, link word, and (thermal) rho, Lambda, T read + u written

@@ -187,6 +187,7 @@ template <typename R> struct FDArgs {
   const R* u;         // [D][N]
   const R* inlet_u;   // [D][ny*nz]
   R* Floc;            // [N] flame sensor output (nullptr: F_loc = F)
+  R* Floc_out;        // [N] F_loc of the state this update produces (sensor on), else nullptr
   R* rho_out;         // [N]
   R* lam_out;         // [N]
   void* partials;     // [grid][2] fixed-point int64 (float path) or double (double path)

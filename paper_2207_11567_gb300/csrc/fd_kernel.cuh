@@ -113,7 +113,14 @@ template <typename R> __device__ __forceinline__ R nu_of(const FDConst<R>& c, in
 }
 
 // Flame sensor: F_loc = 1 + (F - 1) tanh(beta Omega / Omega_0) with
-// Omega = max(Y_F, 0) max(Y_O, 0) exp(-T_s / T), stored per fluid cell.
+// Omega = max(Y_F, 0) max(Y_O, 0) exp(-T_s / T), a function of the cell's own state.
+template <typename R> __device__ __forceinline__ R sensor_floc(const FDConst<R>& c, R T, R yf, R yo) {
+  const R om = fmax(yf, R(0)) * fmax(yo, R(0)) * exp(-c.sensor_Ta / T);
+  return R(1) + (c.F - R(1)) * tanh(c.sensor_beta * om * c.inv_wref);
+}
+
+// F_loc of the current state, per fluid cell: needed once after the state is set from outside
+// (fields, a checkpoint); each update then writes F_loc of the state it produces (Floc_out).
 template <int D, typename R>
 __global__ void __launch_bounds__(FD_BLOCK) flame_sensor_kernel(const FDArgs<R> a) {
   const int r = blockIdx.x * FD_BLOCK + threadIdx.x;
@@ -121,11 +128,8 @@ __global__ void __launch_bounds__(FD_BLOCK) flame_sensor_kernel(const FDArgs<R> 
   if (__ldg(a.mask + r)) return;
   const FDConst<R>& c = a.c;
   const size_t N = (size_t)a.geo.N;
-  const R T = ldg(a.T + r);
-  const R yf = fmax(ldg(a.Y + c.sensor_species * N + r), R(0));
-  const R yo = fmax(ldg(a.Y + c.sensor_oxidizer * N + r), R(0));
-  const R om = yf * yo * exp(-c.sensor_Ta / T);
-  a.Floc[r] = R(1) + (c.F - R(1)) * tanh(c.sensor_beta * om * c.inv_wref);
+  a.Floc[r] = sensor_floc<R>(c, ldg(a.T + r), ldg(a.Y + c.sensor_species * N + r),
+                             ldg(a.Y + c.sensor_oxidizer * N + r));
 }
 
 // Thread-block shape of the FD update: 32 x 4 x 2 cells in 3-D, 32 x 8 in 2-D (256 threads),
@@ -302,6 +306,7 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
     R lam = R(0);
     R sWn = R(0);
     R Tnew = Tr;
+    R yf_new = R(0), yo_new = R(0);  // sensor species of the new state
     // VCP accumulators: neighbour c_p (sum over species of Y_k(n) c_p,k(T_n)) and, per axis,
     // sum_k (c_p,k - c_p)/Le_k (Y_k(r+e) - Y_k(r-e))
     R cpn[VCP ? 3 : 1][2], gYw[VCP ? 3 : 1];
@@ -409,8 +414,12 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
         a.Y_out[(size_t)(fi - 1) * N + r] = pn;
         lam += W * c.inv_W[fi - 1] * NA;
         sWn += pn * c.inv_W[fi - 1];
+        if (fi - 1 == c.sensor_species) yf_new = pn;
+        if (fi - 1 == c.sensor_oxidizer) yo_new = pn;
       }
     }
+    // flame sensor of the new state (the separate sensor pass for the next step, fused)
+    if (a.Floc_out) a.Floc_out[r] = sensor_floc<R>(c, Tnew, yf_new, yo_new);
     a.rho_out[r] = rho;
     a.lam_out[r] = lam;
     if (c.closed) {

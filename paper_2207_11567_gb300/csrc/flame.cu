@@ -56,12 +56,9 @@ __global__ void __launch_bounds__(FL_BLOCK) flame_columns_kernel(FDArgs<R> a, in
     const R rho_phys = fdr / (sW * Tr) / c.inv_rho_ref;  // P_th W / (R T)
     R w = R(0);
     for (int jr = 0; jr < c.nrx; ++jr) w += c.nu[jr][fuel] * rate_of<R>(c, jr, Tr, a.Y, N, r, rho_phys);
-    R Floc = c.F;
-    if (c.sensor) {
-      const R yf = fmax(a.Y[(size_t)c.sensor_species * N + r], R(0));
-      const R yo = fmax(a.Y[(size_t)c.sensor_oxidizer * N + r], R(0));
-      Floc = R(1) + (c.F - R(1)) * tanh(c.sensor_beta * (yf * yo * exp(-c.sensor_Ta / Tr)) * c.inv_wref);
-    }
+    const R Floc = c.sensor ? sensor_floc<R>(c, Tr, a.Y[(size_t)c.sensor_species * N + r],
+                                             a.Y[(size_t)c.sensor_oxidizer * N + r])
+                            : c.F;
     acc[0] += 1.0;
     acc[1] += (double)Tr;
     acc[2] -= (double)(c.W[fuel] * w / Floc);
