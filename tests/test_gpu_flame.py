@@ -135,7 +135,8 @@ def test_thickening_keeps_flame_speed():
     """Thickened flame (Section 3.2.2 uses a factor 6): diffusion times F, rates divided by F, so S_L
     stays and delta_L grows about F times; F = 4 against F = 1. The F = 1 front spans only about
     6 cells: its own discretisation error (and an oscillation of its S_c by about 2%) sets the
-    tolerance."""
+    tolerance. F = 5 is out of reach at this time step: in the 1950 K burnt gas the thickened
+    diffusivity gives dt F lambda / (rho c_p dx^2) = 5 x 0.11 = 0.55, past the explicit limit 1/2."""
     _, s1, _ = _free(1.0)
     _, s4, _ = _free(4.0)
     assert s1.converged and s4.converged
