@@ -54,6 +54,8 @@ struct lbm_ctx {
   int nblocks_fd = 0;    // partial slots written by the FD kernel
   int nblocks_init = 0;  // partial slots written by the initial-integral kernel
   PthState* pth = nullptr;
+  void* pth_stage = nullptr;            // block sums of the P_th reduction
+  unsigned int* pth_counter = nullptr;  // blocks done in the P_th reduction (zero between launches)
   int* flag = nullptr;
   double* scratch_out = nullptr;  // staging for get_fields
   size_t scratch_out_n = 0;
@@ -370,7 +372,7 @@ cudaError_t timed(lbm_ctx* c, int kind, cudaError_t (*fn)(lbm_ctx*, int, int), i
 cudaError_t fd_thunk(lbm_ctx* c, int cur, int sensor) { return run_fd(c, cur, sensor != 0); }
 cudaError_t lb_thunk(lbm_ctx* c, int cur, int want) { return run_lb(c, cur, want != 0); }
 cudaError_t pth_thunk(lbm_ctx* c, int, int) {
-  return launch_pth_update(c->pu, c->partials, c->nblocks_fd, c->pth, 0, c->st);
+  return launch_pth_update(c->pu, c->partials, c->nblocks_fd, c->pth_stage, c->pth_counter, c->pth, 0, c->st);
 }
 
 // One full step from parity `cur`: FD (+ sensor) -> P_th -> LB.
@@ -492,6 +494,8 @@ lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
   ctx->nblocks_fd = fd_partial_blocks(ctx->D, ctx->geo);
   ctx->nblocks_init = (int)((N + AUX_BLOCK - 1) / AUX_BLOCK);
   ok = ok && (ctx->partials = dalloc(ctx, (size_t)std::max(ctx->nblocks_fd, ctx->nblocks_init) * 16));
+  ok = ok && (ctx->pth_stage = dalloc(ctx, (size_t)pth_stage_words() * 8));
+  ok = ok && (ctx->pth_counter = (unsigned int*)dalloc(ctx, 16));
   if (c.thermal) {
     for (int b = 0; b < 2; ++b) {
       ok = ok && (ctx->T[b] = dalloc(ctx, N * ctx->F));
@@ -505,6 +509,7 @@ lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
     return fail(ctx, LBM_ERR_ALLOC, "device allocation failed");
   }
   CK(cudaMemsetAsync(ctx->flag, 0, 16, ctx->st), "memset");
+  CK(cudaMemsetAsync(ctx->pth_counter, 0, 16, ctx->st), "memset");
   CK(cudaMemsetAsync(ctx->inlet_u, 0, (size_t)ctx->D * c.ny * c.nz * ctx->F, ctx->st), "memset");
   for (int b = 0; b < 2; ++b)
     if (ctx->Floc[b]) CK(cudaMemsetAsync(ctx->Floc[b], 0, N * ctx->F, ctx->st), "memset");
@@ -731,7 +736,9 @@ lbm_status lbm_set_fields(lbm_ctx* ctx, const double* T, const double* Y, const 
                                        ctx->fdc_d, ctx->partials, ctx->nblocks_init, ctx->st)
         : launch_init_integral<float>(ctx->geo, ctx->mask, (const float*)ctx->T[0], (const float*)ctx->Y[0],
                                       ctx->fdc_f, ctx->partials, ctx->nblocks_init, ctx->st);
-    if (e == cudaSuccess) e = launch_pth_update(ctx->pu, ctx->partials, ctx->nblocks_init, ctx->pth, 1, ctx->st);
+    if (e == cudaSuccess)
+      e = launch_pth_update(ctx->pu, ctx->partials, ctx->nblocks_init, ctx->pth_stage, ctx->pth_counter, ctx->pth, 1,
+                            ctx->st);
     if (e != cudaSuccess) st = cuda_fail(ctx, e, "initial integral");
   }
   cudaError_t e = cudaStreamSynchronize(ctx->st);

@@ -217,44 +217,74 @@ __global__ void init_integral_kernel(Geo g, const uint8_t* __restrict__ mask, co
 
 // One block: exact sum of the per-block partials, then the thermodynamic-pressure update
 // P^{n+1} = M^{n+1} / I^{n+1} in FP64.
-__global__ void pth_update_kernel(PthUpdate pu, const void* __restrict__ partials, int nblocks, PthState* pth,
-                                  int init) {
-  __shared__ long long sI[1024], sM[1024];
-  __shared__ double dI[1024], dM[1024];
+// Thermodynamic-pressure update: the per-block partial sums of the FD update (integral I and the
+// boundary mass flux) are reduced by PTH_BLOCKS blocks, each over a fixed contiguous range; the
+// block that finishes last (a counter in device memory) adds the block sums in block order and
+// updates the pressure state, then resets the counter. The partition and the order of every sum
+// are fixed, so the result does not depend on scheduling (the FP32 path's sums are exact integers
+// anyway).
+constexpr int PTH_BLOCKS = 152;
+constexpr int PTH_THREADS = 256;
+
+template <typename T> __device__ __forceinline__ void block_sum2(T& a, T& b, T* sa, T* sb) {
   const int t = threadIdx.x;
-  if (pu.fixed_point) {
-    const long long* p = (const long long*)partials;
-    long long a = 0, b = 0;
-    // unrolled so that several loads are in flight per thread (one block reads ~1 MB on C4)
-#pragma unroll 8
-    for (int i = t; i < nblocks; i += blockDim.x) { a += p[2 * i]; b += p[2 * i + 1]; }
-    sI[t] = a;
-    sM[t] = b;
-  } else {
-    const double* p = (const double*)partials;
-    double a = 0, b = 0;
-#pragma unroll 8
-    for (int i = t; i < nblocks; i += blockDim.x) { a += p[2 * i]; b += p[2 * i + 1]; }
-    dI[t] = a;
-    dM[t] = b;
-  }
+  sa[t] = a;
+  sb[t] = b;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+  for (int o = PTH_THREADS / 2; o > 0; o >>= 1) {
     if (t < o) {
-      if (pu.fixed_point) { sI[t] += sI[t + o]; sM[t] += sM[t + o]; }
-      else { dI[t] += dI[t + o]; dM[t] += dM[t + o]; }
+      sa[t] += sa[t + o];
+      sb[t] += sb[t + o];
     }
     __syncthreads();
   }
+  a = sa[0];
+  b = sb[0];
+}
+
+__global__ void __launch_bounds__(PTH_THREADS) pth_update_kernel(PthUpdate pu, const void* __restrict__ partials,
+                                                                 int nblocks, void* stage, unsigned int* counter,
+                                                                 PthState* pth, int init) {
+  __shared__ long long sI[PTH_THREADS], sM[PTH_THREADS];
+  __shared__ double dI[PTH_THREADS], dM[PTH_THREADS];
+  __shared__ bool last;
+  const int t = threadIdx.x, b = blockIdx.x, nb = gridDim.x;
+  const int chunk = (nblocks + nb - 1) / nb;
+  const int i0 = b * chunk, i1 = min(nblocks, i0 + chunk);
+  if (pu.fixed_point) {
+    const long long* p = (const long long*)partials;
+    long long a = 0, c = 0;
+    for (int i = i0 + t; i < i1; i += PTH_THREADS) { a += p[2 * i]; c += p[2 * i + 1]; }
+    block_sum2(a, c, sI, sM);
+    if (t == 0) { ((long long*)stage)[2 * b] = a; ((long long*)stage)[2 * b + 1] = c; }
+  } else {
+    const double* p = (const double*)partials;
+    double a = 0, c = 0;
+    for (int i = i0 + t; i < i1; i += PTH_THREADS) { a += p[2 * i]; c += p[2 * i + 1]; }
+    block_sum2(a, c, dI, dM);
+    if (t == 0) { ((double*)stage)[2 * b] = a; ((double*)stage)[2 * b + 1] = c; }
+  }
+  __threadfence();
+  __syncthreads();
+  if (t == 0) last = atomicAdd(counter, 1u) == (unsigned int)(nb - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double I, mflux;
+  if (pu.fixed_point) {
+    long long a = t < nb ? __ldcg((const long long*)stage + 2 * t) : 0;
+    long long c = t < nb ? __ldcg((const long long*)stage + 2 * t + 1) : 0;
+    block_sum2(a, c, sI, sM);
+    I = (double)a / (FIX_SCALE * pu.I_s);
+    mflux = (double)c / (FIX_SCALE * pu.M_s);
+  } else {
+    double a = t < nb ? __ldcg((const double*)stage + 2 * t) : 0.0;
+    double c = t < nb ? __ldcg((const double*)stage + 2 * t + 1) : 0.0;
+    block_sum2(a, c, dI, dM);
+    I = a / pu.I_s;
+    mflux = c / pu.M_s;
+  }
   if (t == 0) {
-    double I, mflux;
-    if (pu.fixed_point) {
-      I = (double)sI[0] / (FIX_SCALE * pu.I_s);
-      mflux = (double)sM[0] / (FIX_SCALE * pu.M_s);
-    } else {
-      I = dI[0] / pu.I_s;
-      mflux = dM[0] / pu.M_s;
-    }
     const double P_old = pth->P;
     // set-up: M = P_th0 I0 and nothing moves; step: P^{n+1} = M^{n+1} / I^{n+1}
     const double M_new = init ? P_old * I : pth->M + mflux;
@@ -271,6 +301,7 @@ __global__ void pth_update_kernel(PthUpdate pu, const void* __restrict__ partial
     pth->fd_rho = (float)pth->fd_rho_d;
     pth->fd_dT = (float)pth->fd_dT_d;
     pth->rho_in = (float)pth->rho_in_d;
+    *counter = 0u;  // ready for the next launch (stream order)
   }
 }
 }  // namespace
@@ -317,9 +348,12 @@ template cudaError_t launch_init_integral<float>(const Geo&, const uint8_t*, con
 template cudaError_t launch_init_integral<double>(const Geo&, const uint8_t*, const double*, const double*,
                                                   const FDConst<double>&, void*, int, cudaStream_t);
 
-cudaError_t launch_pth_update(const PthUpdate& pu, const void* partials, int nblocks, PthState* pth,
-                              int init, cudaStream_t st) {
-  pth_update_kernel<<<1, 1024, 0, st>>>(pu, partials, nblocks, pth, init);
+int pth_stage_words() { return 2 * PTH_BLOCKS; }
+
+cudaError_t launch_pth_update(const PthUpdate& pu, const void* partials, int nblocks, void* stage,
+                              unsigned int* counter, PthState* pth, int init, cudaStream_t st) {
+  const int nb = nblocks < PTH_BLOCKS ? (nblocks > 0 ? nblocks : 1) : PTH_BLOCKS;
+  pth_update_kernel<<<nb, PTH_THREADS, 0, st>>>(pu, partials, nblocks, stage, counter, pth, init);
   return cudaGetLastError();
 }
 

@@ -33,8 +33,10 @@ struct PthUpdate {
   double I_s, M_s, R_rho_ref, cp_rho_ref, rin_fac;  // rin_fac = W_in / (R T_in rho_ref)
   int fixed_point;                                  // partials are int64 fixed point
 };
-cudaError_t launch_pth_update(const PthUpdate& pu, const void* partials, int nblocks, PthState* pth,
-                              int init, cudaStream_t st);
+// stage: pth_stage_words() 8-byte words; counter: zero before the first launch (kept zero after)
+int pth_stage_words();
+cudaError_t launch_pth_update(const PthUpdate& pu, const void* partials, int nblocks, void* stage,
+                              unsigned int* counter, PthState* pth, int init, cudaStream_t st);
 constexpr int AUX_BLOCK = 256;
 
 // adjoint.cu: one adjoint step. in: adjoint of state n+1, out: adjoint of state n, both in the
