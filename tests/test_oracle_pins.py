@@ -751,3 +751,38 @@ def test_ghost_point_walls_conduct_heat_at_second_order(q):
         errs0.append(abs(lam0 / exact - 1))
     assert errs[2] < 1e-3 and errs[0] / errs[1] > 2.5 and errs[1] / errs[2] > 3.3, errs
     assert errs0[2] > 10 * errs[2], (errs, errs0)
+
+
+def test_closed_box_burns_at_constant_volume():
+    """Closed rigid box at rest (periodic, closed-domain pressure): the mass stays, so the
+    thermodynamic pressure follows P = M / I, and the pressure work dP/(rho c_p) in the energy
+    equation turns the constant-pressure heat balance into the constant-volume one. With the
+    one-step mechanism the moles, hence W, do not change (CH4 + 2 O2 -> 3 P), so complete
+    combustion reaches T0 + Q / (c_p - R / W) and P / P0 = T / T0. The pressure work is applied a
+    step late (reading c5), an O(dt) error: the burnt state converges to that closed form as
+    dt -> 0, far from the constant-pressure value T0 + Q / c_p."""
+    names = W.SPECIES["4sp"]
+    rx = W.chemistry_1step()
+    T0, t_end, cp = 1800.0, 2.0e-5, 1400.0
+    errs, perrs = [], []
+    for dt in (1e-7, 2.5e-8):
+        cfg = W.generate._base_cfg(2, 2, 2, 1, "f64")
+        cfg.update({"bc": {"x": ("periodic", "periodic"), "y": ("periodic", "periodic")}, "dx": 1e-3, "dt": dt,
+                    "nu_ref": 1.5e-5, "thermal": True, "species": W.configs.species(names, unity_lewis=True),
+                    "reactions": rx, "T_in": T0, "Y_in": W.mixture_phi(names, 0.83), "closed_domain": True,
+                    "cp": cp})
+        o = Oracle(cfg, np.zeros(4, np.uint8))
+        Y0 = np.array(cfg["Y_in"])[:, None].repeat(4, 1)
+        st = o.init_state(T=np.full(4, T0), Y=Y0, u=np.zeros((2, 4)))
+        st = o.run(st, int(round(t_end / dt)))
+        T_ad_p, Yb = _closed_form_T_ad(names, 0.83, T0, cp)
+        Wm = 1.0 / sum(y / s["W"] for y, s in zip(cfg["Y_in"], cfg["species"]))
+        T_ad_v = T0 + (T_ad_p - T0) * cp / (cp - 8.314462618 / Wm)
+        T = st["T"].mean().item()
+        errs.append(abs(T - T_ad_v) / T_ad_v)
+        perrs.append(abs(st["P_th"] / cfg["P_th0"] - T / T0))
+    assert T_ad_v - T_ad_p > 100.0
+    # measured: 4.5e-2 at dt = 1e-7 and 3.5e-3 at 2.5e-8 (3900 K), against the 11.5% gap to the
+    # constant-pressure 3452 K
+    assert errs[1] < 5e-3 and errs[0] / errs[1] > 2.5, errs
+    assert max(perrs) < 1e-9, perrs
