@@ -786,3 +786,28 @@ def test_closed_box_burns_at_constant_volume():
     # constant-pressure 3452 K
     assert errs[1] < 5e-3 and errs[0] / errs[1] > 2.5, errs
     assert max(perrs) < 1e-9, perrs
+
+
+def test_flame_sensor_limits():
+    """The thickening factor of the sensor reading stays in [1, F]: exactly 1 where the fuel or the
+    oxidizer is gone (burnt lean gas, pure air) or negative, F where the reaction-rate proxy is far
+    above its reference, and it grows with temperature at fixed composition."""
+    wl = W.generate.swirl_3d(20, 12, 12, reactive=True, seed=3)
+    p = Params(wl.cfg)
+    F = p.F
+    assert p.sensor and F > 1
+    n = 50
+    T = torch.linspace(300.0, 2500.0, n, dtype=f64)
+    Y = torch.tensor(wl.cfg["Y_in"], dtype=f64)[:, None].repeat(1, n)
+    fl = fdm.thickening(p, T, Y)
+    assert (fl >= 1).all() and (fl <= F).all()
+    assert (torch.diff(fl) >= 0).all() and fl[-1] > fl[0]
+    for k, v in ((p.sensor_species, 0.0), (p.sensor_oxidizer, 0.0), (p.sensor_species, -1e-3)):
+        Yz = Y.clone()
+        Yz[k] = v
+        assert (fdm.thickening(p, T, Yz) == 1.0).all()
+    Yh = Y.clone()
+    Yh[p.sensor_species] = 1.0
+    Yh[p.sensor_oxidizer] = 1.0
+    hot = fdm.thickening(p, torch.full((1,), 1e6, dtype=f64), Yh[:, :1])
+    assert abs(hot.item() - F) < 1e-12 * F
