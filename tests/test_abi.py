@@ -73,3 +73,15 @@ def test_invalid_configurations_are_rejected(L, mutate, msg):
 def test_null_arguments(L):
     assert L.lib.lbm_init(None, None) == L.LBM_ERR_ARG
     assert L.lib.lbm_step(None, 1) == L.LBM_ERR_ARG
+
+
+def test_package_without_the_library_fails_loudly(tmp_path):
+    """A copy of the package without libhlbm.so does not import (no CPU path to fall back to)."""
+    import shutil
+    import sys
+    src = os.path.join(ROOT, "paper_2207_11567_gb300")
+    dst = tmp_path / "paper_2207_11567_gb300"
+    shutil.copytree(src, dst, ignore=shutil.ignore_patterns("*.so", "_build", "__pycache__"))
+    r = subprocess.run([sys.executable, "-c", "import paper_2207_11567_gb300"], cwd=tmp_path,
+                       capture_output=True, text=True)
+    assert r.returncode != 0 and "libhlbm.so is missing" in r.stderr
