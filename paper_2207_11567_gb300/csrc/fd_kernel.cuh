@@ -8,7 +8,15 @@
 // face mean of G = F_loc mu(T) / (Pr Le), chemistry divided by F_loc, pressure work on T.
 // Lambda (Eq. 3) = N_T / T + sum_k (W / W_k) N_k, rho = P_th W / (R T).
 // Stencil points outside the fluid take ghost values: zero gradient (walls, solids, outlet) or
-// the inlet state (low-x inlet), velocity 0 at walls and solids, inlet velocity at the inlet.
+// the inlet state (low-x inlet), velocity 0 at walls and solids, inlet velocity at the inlet;
+// with sub-cell wall positions, ghost-point values from the wall fractions.
+//
+// Copies of the cell update (fd_cell): FAST for cells whose radius-2 stencil is all fluid and
+// inside the grid, the general one, and GW for cells with ghost-point wall weights; each warp
+// takes one copy for all its cells (the most general any of them needs). VDEG > 0 compiles the
+// variable heat-capacity form of the temperature equation (fd_kernels_vcp.cu). The update also
+// writes the flame sensor's F_loc of the state it produces, so the separate sensor pass is
+// needed only after the state was set from outside.
 #pragma once
 #include "common.cuh"
 
