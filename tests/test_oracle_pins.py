@@ -811,3 +811,30 @@ def test_flame_sensor_limits():
     Yh[p.sensor_oxidizer] = 1.0
     hot = fdm.thickening(p, torch.full((1,), 1e6, dtype=f64), Yh[:, :1])
     assert abs(hot.item() - F) < 1e-12 * F
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_smagorinsky_relaxation_solves_the_eddy_viscosity_relation(dim):
+    """Populations whose non-equilibrium second moment is a prescribed traceless-plus-trace Pi
+    (second-order Hermite term): the effective relaxation time satisfies the Smagorinsky relation
+    tau = tau0 + 3 nu_t, nu_t = (C_s dx)^2 |S|, |S| = sqrt(2 S:S), with the strain rate from the
+    deviatoric non-equilibrium stress S = -Pi_dev / (2 c_s^2 tau) (unit density, lattice units);
+    a trace in Pi does not change it, and C_s = 0 gives tau0."""
+    lat = Lattice(dim)
+    rng = np.random.default_rng(dim)
+    n = 7
+    A = rng.standard_normal((n, dim, dim)) * 1e-3
+    Pi = torch.as_tensor(A + A.transpose(0, 2, 1))  # symmetric, with a trace
+    u = torch.as_tensor(rng.standard_normal((dim, n)) * 0.02)
+    heq = lb.f_eq(lat, torch.ones(n, dtype=f64), u)
+    cc = lat.c[:, :, None] * lat.c[:, None, :] - CS2 * torch.eye(dim, dtype=f64)  # [Q, d, d]
+    h = heq + lat.w[:, None] / (2 * CS2 ** 2) * torch.einsum("qab,nab->qn", cc, Pi)
+    tau0 = torch.full((n,), 0.62, dtype=f64)
+    cs = 0.17
+    tau = lb.tau_smagorinsky(lat, h, u, tau0, cs)
+    Pd = Pi - torch.eye(dim, dtype=f64) * Pi.diagonal(dim1=1, dim2=2).sum(-1)[:, None, None] / dim
+    S = -Pd / (2 * CS2 * tau[:, None, None])
+    nu_t = cs ** 2 * torch.sqrt(2 * (S * S).sum((1, 2)))
+    assert torch.allclose(tau, tau0 + nu_t / CS2, rtol=1e-12, atol=0)
+    assert (tau > tau0).all()
+    assert torch.equal(lb.tau_smagorinsky(lat, h, u, tau0, 0.0), tau0)
