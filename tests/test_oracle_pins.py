@@ -838,3 +838,17 @@ def test_smagorinsky_relaxation_solves_the_eddy_viscosity_relation(dim):
     assert torch.allclose(tau, tau0 + nu_t / CS2, rtol=1e-12, atol=0)
     assert (tau > tau0).all()
     assert torch.equal(lb.tau_smagorinsky(lat, h, u, tau0, 0.0), tau0)
+
+
+def test_stencil_words_hand_derived():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "stencil_5x3.txt")) if l.strip() and l[0] != "#"]
+    for case, x, y, word, fluid in rows:
+        mask = np.zeros(15, np.uint8)
+        if case == "solid":
+            mask[3 + 5 * 1] = 1
+        cfg = {"dim": 2, "nx": 5, "ny": 3, "nz": 1, "bc": {"x": ("inlet", "outlet"), "y": ("wall", "wall")}}
+        g = geo.Grid(cfg, mask)
+        words = geo.pack_stencil_words(g, geo.FDNeighbours(g))
+        r = int(x) + 5 * int(y)
+        expect = (int(word) | (1 << 31)) if int(fluid) else 0
+        assert int(words[r]) == expect, (case, x, y, int(words[r]) & 0x7fffffff, int(word))
