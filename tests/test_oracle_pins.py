@@ -852,3 +852,31 @@ def test_stencil_words_hand_derived():
         r = int(x) + 5 * int(y)
         expect = (int(word) | (1 << 31)) if int(fluid) else 0
         assert int(words[r]) == expect, (case, x, y, int(words[r]) & 0x7fffffff, int(word))
+
+
+def test_dilatation_is_the_rate_of_density_change():
+    """Homogeneous burning gas at rest (open domain, constant P_th): the continuity equation gives
+    d(ln rho)/dt = -div u = -Lambda (Eq. 3), and rho = P W / (R T) follows from the updated T and Y.
+    One explicit update therefore changes ln rho by -Lambda up to O(Lambda^2): relative to Lambda
+    the mismatch falls in proportion to the step, while a wrong factor in Lambda (a dropped
+    W / W_k, the 1 / T of the temperature term, a sign) would leave it of order one."""
+    names = W.SPECIES["6sp"]
+    rx = W.chemistry_2step()
+    ratios = []
+    for dt in (4e-8, 2e-8, 1e-8):
+        cfg = W.generate._base_cfg(2, 2, 2, 1, "f64")
+        cfg.update({"bc": {"x": ("periodic", "periodic"), "y": ("periodic", "periodic")}, "dx": 1e-3, "dt": dt,
+                    "nu_ref": 1.5e-5, "thermal": True, "species": W.configs.species(names),
+                    "reactions": rx, "T_in": 1800.0, "Y_in": W.mixture_phi(names, 0.83)})
+        p = Params(cfg)
+        grid = geo.Grid(cfg, np.zeros(4, np.uint8))
+        T = torch.full((4,), 1800.0, dtype=f64)
+        Y = torch.tensor(cfg["Y_in"], dtype=f64)[:, None].repeat(1, 4)
+        Y[2] += 0.01  # some CO so that both reactions run
+        Y[5] -= 0.01
+        u = torch.zeros(2, 4, dtype=f64)
+        T1, Y1, rho0, lam = fdm.fd_update(p, grid, geo.FDNeighbours(grid), T, Y, u, u, p.P_th0, 0.0)
+        rho1 = p.P_th0 * fdm.mean_molar_mass(p, Y1) / (8.314462618 * T1 * p.rho_ref)
+        dlog = torch.log(rho1 / rho0)
+        ratios.append(((dlog + lam).abs().max() / lam.abs().max()).item())
+    assert ratios[0] < 5e-3 and ratios[0] / ratios[1] > 1.8 and ratios[1] / ratios[2] > 1.8, ratios
