@@ -108,7 +108,7 @@ class Oracle:
     def step(self, st, P_next=None):
         """One step. P_next: thermodynamic pressure after the step, given from outside (a patch
         of a larger closed domain, whose integral the patch cannot form)."""
-        p, lat, fluid = self.p, self.lat, self.grid.fluid
+        p, fluid = self.p, self.grid.fluid
         N = self.grid.N
         new = dict(st)
         if p.thermal:
@@ -136,15 +136,21 @@ class Oracle:
             lam = torch.zeros(N, dtype=torch.float64)
             grad = torch.zeros(p.dim, N, dtype=torch.float64)
             tau0 = torch.full((N,), p.nu_lat / CS2 + 0.5, dtype=torch.float64)
-        g = lb.stream(st["g"], self.code, self.src, lat, rho, self.uin_r, st["u"], self.cfg.get("P_ref", 0.0),
+        new["g"], new["u"], new["P_h"] = self.lb_update(st["g"], st["u"], st["P_h"], rho, lam, grad, tau0)
+        return new
+
+    def lb_update(self, g_post, u_prev, P_prev, rho, lam, grad, tau0):
+        """Step 3 of the module doc (Section 2.1-2.2) with the density rho, its gradient grad, the
+        dilatation lam and the relaxation time tau0 given per cell: returns (g*, u, P_h); non-fluid
+        cells keep g_post, u_prev and P_prev."""
+        lat, fluid = self.lat, self.grid.fluid
+        g = lb.stream(g_post, self.code, self.src, lat, rho, self.uin_r, u_prev, self.cfg.get("P_ref", 0.0),
                       self.wall)
         P_h, u = lb.moments(lat, g, rho, lam)
         xi = lb.source_xi(lat, rho, u, grad, lam)
-        gs = lb.collide(lat, self.cs, g, rho, u, xi, tau0, p.as_lb())
-        new["g"] = torch.where(fluid[None, :], gs, st["g"])
-        new["u"] = torch.where(fluid[None, :], u, st["u"])
-        new["P_h"] = torch.where(fluid, P_h, st["P_h"])
-        return new
+        gs = lb.collide(lat, self.cs, g, rho, u, xi, tau0, self.p.as_lb())
+        return (torch.where(fluid[None, :], gs, g_post), torch.where(fluid[None, :], u, u_prev),
+                torch.where(fluid, P_h, P_prev))
 
     def round_state(self, st):
         if self.store_round is None:
