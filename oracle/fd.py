@@ -34,6 +34,19 @@ Readings (the paper gives no formulas for these):
     fields, and the species-enthalpy flux written with the diffusion fluxes relative to the
     mass-averaged velocity (c_p,k - c_p), so that equal species heat capacities give back the
     constant-c_p update exactly.
+  * Mixture-averaged species diffusion (option; the paper's transport library is not available,
+    so binary diffusion data are given as pair Lewis numbers, rho D_kj = (mu / Pr) / Le_kj):
+    the Hirschfelder-Curtiss coefficient rho D_k = (1 - X_k) / sum_{j!=k} X_j / (rho D_kj), written
+    per cell as G_k = F_loc mu / (Pr Le_k^mix), Le_k^mix = sum_{j!=k} (X_j + d) Le_kj /
+    sum_{j!=k} (X_j + d) with the mole fractions X_j = Y_j W / W_j clipped at 0 and d = 1e-10
+    (a pure species keeps a finite coefficient), and the mass flux of the mole-fraction form with
+    a correction velocity, j_k = -rho D_k (W_k / W) grad X_k + rho Y_k V_c,
+    V_c = sum_j D_j (W_j / W) grad X_j. With (W_k / W) grad X_k = grad Y_k + Y_k grad(ln W), per
+    face (arithmetic means G_k,f and Y_k,f, differences dY_k, dlnW = (W_n - W_r) / mean W):
+        J_k,f = G_k,f (dY_k + Y_k,f dlnW) - Y_k,f sum_j G_j,f (dY_j + Y_j,f dlnW).
+    The J_k,f sum to zero over the species (sum_k Y_k = 1), and equal pair Lewis numbers give
+    J_k,f = G_f dY_k, the constant-Lewis flux, exactly. Ghost neighbours take their ghost T and
+    Y (and the fluid cell's F_loc) as in the constant-Lewis case.
 """
 import math
 
@@ -112,6 +125,45 @@ def thickening(p, T, Y):
     return 1.0 + (p.F - 1.0) * torch.tanh(p.sensor_beta * om / p.sensor_wref)
 
 
+def lewis_mixture(p, Y):
+    """Le_k^mix per cell for every species (mixture-averaged option, see the module notes)."""
+    W = mean_molar_mass(p, Y)
+    X = [torch.clamp(Y[j] * W / p.W[j], min=0.0) + 1e-10 for j in range(p.K)]
+    out = []
+    for k in range(p.K):
+        num = sum(X[j] * p.Le_pair[k][j] for j in range(p.K) if j != k)
+        den = sum(X[j] for j in range(p.K) if j != k)
+        out.append(num / den)
+    return out
+
+
+def _species_diffusion_mixavg(p, nb, T, Y, Floc, mu):
+    """sum over faces of J_k,f for every species (mixture-averaged option): list of [N]."""
+    W = mean_molar_mass(p, Y)
+    Lr = lewis_mixture(p, Y)
+    Gr = [Floc * mu / (p.Pr * Lr[k]) for k in range(p.K)]
+    dif = [torch.zeros_like(T) for _ in range(p.K)]
+    for a in range(nb.grid.dim):
+        for sigma in (-1, 1):
+            Tn = nb.value(T, p.T_in, a, sigma, 1)
+            Yn = torch.stack([nb.value(Y[k], p.Y_in[k], a, sigma, 1) for k in range(p.K)])
+            kn, i_n = nb.kind1(a, sigma), nb.index1(a, sigma)
+            Fn = torch.where(kn == 0, Floc[i_n], Floc)
+            mun = p.nu_lat * (Tn / p.T_ref) ** p.mu_exp
+            Ln = lewis_mixture(p, Yn)
+            Wn = mean_molar_mass(p, Yn)
+            dlnW = (Wn - W) / (0.5 * (Wn + W))
+            Gf = [0.5 * (Gr[k] + Fn * mun / (p.Pr * Ln[k])) for k in range(p.K)]
+            Yf = [0.5 * (Y[k] + Yn[k]) for k in range(p.K)]
+            dY = [Yn[k] - Y[k] for k in range(p.K)]
+            corr = sum(Gf[j] * (dY[j] + Yf[j] * dlnW) for j in range(p.K))
+            for k in range(p.K):
+                J = Gf[k] * (dY[k] + Yf[k] * dlnW) - Yf[k] * corr
+                # with differences neighbour minus cell, both faces of an axis enter with + sign
+                dif[k] = dif[k] + J
+    return dif
+
+
 def fd_update(p, grid, nb, T, Y, u, uin_r, P_th, dP_lag):
     """One explicit Euler step of T and Y. Returns (T1, Y1, rho_lat, lam_fd)."""
     W = mean_molar_mass(p, Y)
@@ -154,6 +206,10 @@ def fd_update(p, grid, nb, T, Y, u, uin_r, P_th, dP_lag):
             Gm = Fm * p.nu_lat * (Tm / p.T_ref) ** p.mu_exp / (p.Pr * Le)
             Gp = Fp * p.nu_lat * (Tp / p.T_ref) ** p.mu_exp / (p.Pr * Le)
             dif = dif + 0.5 * (G + Gp) * (pp1 - phi) - 0.5 * (G + Gm) * (phi - pm1)
+        if f > 0 and p.mixavg:
+            if f == 1:
+                dif_mix = _species_diffusion_mixavg(p, nb, T, Y, Floc, mu)
+            dif = dif_mix[f - 1]
         dif = dif / rho
         if f == 0 and p.varcp:
             dif, src = _energy_varcp(p, nb, T, Y, Floc, mu, rho, rho_phys, om, dP_lag)

@@ -47,6 +47,11 @@ class Params:
         self.varcp = bool(cfg.get("variable_cp", False))
         self.cp_poly = [list(s.get("cp_poly", [self.cp, 0.0, 0.0, 0.0, 0.0])) for s in sp]
         self.T0_thermo = cfg.get("T0_thermo", 298.15)
+        # mixture-averaged species diffusion (option): pair Lewis numbers Le_kj, rho D_kj = mu/(Pr Le_kj)
+        self.mixavg = bool(cfg.get("mixture_averaged", False))
+        self.Le_pair = cfg.get("Le_pair")
+        if self.mixavg and (self.Le_pair is None or len(self.Le_pair) != self.K):
+            raise ValueError("mixture-averaged diffusion needs Le_pair [K][K]")
         self.T_in = cfg.get("T_in", self.T_ref)
         self.Y_in = list(cfg.get("Y_in", [0.0] * self.K))
         self.weno_eps_T = 1e-6 * self.T_ref ** 2

@@ -985,3 +985,85 @@ def test_dilatation_drives_a_linear_outflow():
     x = o.grid.coord[0].double()
     err = (u[0] - L * (x + 0.5)).abs().max().item() / (L * nx)
     assert err < 1e-4 and u[1].abs().max().item() < 1e-15, err
+
+
+# ------------------------------------------------------ mixture-averaged species diffusion (NEXT-2)
+def _chamber_with_inlet():
+    wl = W.generate.chamber_2d(nx=24, ny=12, inlet=True, dt=5e-7, seed=7, u_init=0.01)
+    grid = geo.Grid(wl.cfg, wl.mask)
+    nb = geo.FDNeighbours(grid)
+    T = torch.as_tensor(wl.T)
+    Y = torch.as_tensor(wl.Y)
+    Y = Y / Y.sum(0)
+    return wl, grid, nb, T, Y, torch.as_tensor(wl.u), torch.zeros(2, grid.N, dtype=f64)
+
+
+def test_mixture_averaged_with_equal_pair_lewis_is_the_constant_lewis_update():
+    """All pair Lewis numbers equal to Le (and every species' constant Lewis number Le): the
+    Hirschfelder-Curtiss coefficient is the same for every species and the correction velocity
+    cancels the mole-fraction-gradient terms, so the update is the constant-Lewis one (Fick's law
+    in mass fractions) up to rounding, on a chamber with walls, obstacles, an inlet and an outlet.
+    Weighting the mixing rule with mass instead of mole fractions, or dropping either grad(ln W)
+    term or the correction velocity, leaves differences of the order of the diffusion term."""
+    wl, grid, nb, T, Y, u, uin = _chamber_with_inlet()
+    cfg0 = dict(wl.cfg)
+    cfg0["species"] = [dict(s, Le=1.3) for s in wl.cfg["species"]]
+    cfg1 = dict(cfg0, mixture_averaged=True, Le_pair=[[1.3] * len(cfg0["species"])] * len(cfg0["species"]))
+    p0, p1 = Params(cfg0), Params(cfg1)
+    a = fdm.fd_update(p0, grid, nb, T, Y, u, uin, p0.P_th0, 0.0)
+    b = fdm.fd_update(p1, grid, nb, T, Y, u, uin, p1.P_th0, 0.0)
+    dY = (a[1] - Y).abs().max()
+    assert (a[1] - b[1]).abs().max() < 1e-12 * dY
+    assert (a[0] - b[0]).abs().max() == 0.0
+    assert (a[3] - b[3]).abs().max() < 1e-12 * a[3].abs().max()
+
+
+def test_mixture_averaged_fluxes_sum_to_zero():
+    """Unequal pair Lewis numbers: the species diffusion fluxes of every face sum to zero over the
+    species (the correction velocity), so diffusion conserves sum_k Y_k = 1 cell by cell."""
+    from workloads.configs import mixture_averaged
+    wl, grid, nb, T, Y, u, uin = _chamber_with_inlet()
+    cfg = mixture_averaged(dict(wl.cfg))
+    p = Params(cfg)
+    Floc = fdm.thickening(p, T, Y)
+    mu = p.nu_lat * (T / p.T_ref) ** p.mu_exp
+    dif = fdm._species_diffusion_mixavg(p, nb, T, Y, Floc, mu)
+    tot = sum(dif)
+    scale = max(d.abs().max() for d in dif)
+    assert tot[grid.fluid].abs().max() < 1e-14 * scale * len(dif), (tot.abs().max(), scale)
+
+
+def test_trace_species_diffuses_with_the_bath_average_of_its_pair_coefficients():
+    """A trace of CO2 (Y = eps (1 + sin k x), eps = 1e-5) in a uniform O2/N2 bath, periodic, at rest:
+    its sine mode decays by the discrete Laplacian times rho D_CO2 / rho, with rho D_CO2 =
+    (mu / Pr) / Le^mix and Le^mix = (X_O2 Le_CO2,O2 + X_N2 Le_CO2,N2) / (X_O2 + X_N2) (Blanc's law: the
+    resistances 1/D add with mole-fraction weights). Mass-fraction weights would put the ratio off
+    by ~1e-3; the tolerance is 1e-4 (the trace's own O(eps) effects are far below)."""
+    names = ["CO2", "O2", "N2"]
+    nx = 64
+    cfg = W.generate._base_cfg(2, nx, 1, 1, "f64")
+    cfg.update({"bc": {"x": ("periodic", "periodic"), "y": ("periodic", "periodic")}, "dx": 1e-4, "dt": 5e-7,
+                "nu_ref": 1.5e-5, "thermal": True, "species": W.configs.species(names), "reactions": [],
+                "T_in": 900.0, "Y_in": [0.0, 0.21, 0.79]})
+    from workloads.configs import mixture_averaged
+    mixture_averaged(cfg)
+    p = Params(cfg)
+    grid = geo.Grid(cfg, np.zeros(nx, np.uint8))
+    nb = geo.FDNeighbours(grid)
+    x = torch.arange(nx, dtype=f64)
+    k = 2 * math.pi / nx
+    eps = 1e-5
+    Y = torch.zeros(3, nx, dtype=f64)
+    Y[0] = eps * (1 + torch.sin(k * x))
+    Y[1] = 0.21
+    Y[2] = 1.0 - Y[0] - Y[1]
+    T = torch.full((nx,), 900.0, dtype=f64)
+    u = torch.zeros(2, nx, dtype=f64)
+    T1, Y1, rho, _ = fdm.fd_update(p, grid, nb, T, Y, u, u, p.P_th0, 0.0)
+    mode = ((Y1[0] - Y[0]) * torch.sin(k * x)).sum() / (eps * (torch.sin(k * x) ** 2).sum())
+    Wb = 1.0 / (0.21 / p.W[1] + 0.79 / p.W[2])
+    X_o2, X_n2 = 0.21 * Wb / p.W[1], 0.79 * Wb / p.W[2]
+    Le_mix = (X_o2 * p.Le_pair[0][1] + X_n2 * p.Le_pair[0][2]) / (X_o2 + X_n2)
+    mu = p.nu_lat * (900.0 / p.T_ref) ** p.mu_exp
+    expect = -(mu / (p.Pr * Le_mix)) / rho.mean() * (2 - 2 * math.cos(k))
+    assert abs(mode / expect - 1) < 1e-4, (mode.item(), expect.item())

@@ -45,6 +45,19 @@ def variable_cp(cfg):
     return cfg
 
 
+def mixture_averaged(cfg):
+    """Switch a configuration to mixture-averaged species diffusion (in place) with synthetic pair
+    Lewis numbers Le_kj = sqrt(m_kj / m_N2N2), m_kj = W_k W_j / (W_k + W_j) the reduced molar mass
+    (binary diffusivities of kinetic theory scale as m_kj^-1/2 at fixed collision diameter), so that
+    the N2-N2 pair has Le = 1; e.g. CH4-N2 0.85, H2O-N2 0.89, O2-N2 1.03, CO2-N2 1.11."""
+    Ws = [s["W"] for s in cfg["species"]]
+    W_n2 = _molar_mass("N2")
+    m_ref = W_n2 * W_n2 / (2.0 * W_n2)
+    cfg["mixture_averaged"] = True
+    cfg["Le_pair"] = [[(Wk * Wj / (Wk + Wj) / m_ref) ** 0.5 for Wj in Ws] for Wk in Ws]
+    return cfg
+
+
 def species(names, unity_lewis=False):
     out = []
     for n in names:
