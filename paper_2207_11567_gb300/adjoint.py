@@ -15,6 +15,12 @@ last step down to its first, adding the inlet-velocity adjoint; the recompute of
 segment runs on a second stream while the current one is reversed. lbm_initial_T_adjoint turns
 the adjoint of state 0 into dJ/dT0. Memory: K/C checkpoints of ``Solver.state_bytes()`` plus the
 library's workspace of two segments (2 C states with their rho and Lambda).
+
+Each forward call returns J and keeps a tape of its own (inlet velocity, checkpoints, adjoint of
+the last state), so that several forward calls may be reversed later in any order: the backward
+of a tape sets that forward's inlet velocity again before its recompute. The backward leaves the
+solver in an unspecified state (its recompute and lbm_initial_T_adjoint load checkpoints): call
+forward again before stepping the solver for another purpose.
 Every arithmetic step runs in the library's CUDA kernels; this module only orders the calls.
 """
 import numpy as np
@@ -42,7 +48,7 @@ class AdjointProblem:
         esize = 8 if self.dtype == torch.float64 else 4
         self.n_words = (self.solver.state_bytes() + esize - 1) // esize
         self.dim, self.ny = cfg["dim"], cfg["ny"]
-        self._ckpt = []
+        self.tape = None  # the last forward call's tape
 
     def close(self):
         self.solver.close()
@@ -51,27 +57,34 @@ class AdjointProblem:
         return torch.zeros(n, dtype=self.dtype, device=self.solver.device)
 
     def forward(self, inlet_u, T0):
-        """Run the K steps from (inlet_u [dim][ny], T0 [N]); returns J and keeps checkpoints."""
+        """Run the K steps from (inlet_u [dim][ny], T0 [N]); returns J. The call's tape
+        (``self.tape``) holds what its backward needs."""
         s = self.solver
-        s.set_geometry(self.mask, np.asarray(inlet_u, dtype=np.float64).reshape(self.dim, self.ny))
+        inlet = np.array(inlet_u, dtype=np.float64).reshape(self.dim, self.ny)
+        s.set_geometry(self.mask, inlet)
         s.set_fields(T=np.asarray(T0, dtype=np.float64), Y=self.Y0, u=self.u0, P_h=self.P_h0, g_pert=self.g_pert)
-        self._ckpt = []
+        ckpt = []
         for n0 in range(0, self.n_steps, self.C):
-            self._ckpt.append(s.save_state())
+            ckpt.append(s.save_state())
             s.step(min(self.C, self.n_steps - n0))
-        self._adjK = self._zeros(self.n_words)
-        return s.fuel_objective(self.fuel, self._adjK)
+        adjK = self._zeros(self.n_words)
+        J = s.fuel_objective(self.fuel, adjK)
+        self.tape = {"inlet": inlet, "ckpt": ckpt, "adjK": adjK}
+        return J
 
-    def backward(self, scale=1.0):
-        """dJ/d(inlet_u) [dim][ny] and dJ/dT0 [N] for the last forward call (storage type)."""
-        if not self._ckpt:
+    def backward(self, scale=1.0, tape=None):
+        """dJ/d(inlet_u) [dim][ny] and dJ/dT0 [N] (storage type) of the forward call that made
+        ``tape`` (default: the last one)."""
+        tape = self.tape if tape is None else tape
+        if tape is None:
             raise RuntimeError("backward needs a forward call first")
         s = self.solver
-        adj = self._adjK * scale
+        s.set_inlet(tape["inlet"])
+        adj = tape["adjK"] * scale
         gin = self._zeros(self.dim * self.ny)
-        s.adjoint_sweep(self._ckpt, self.C, self.n_steps, adj, gin)
+        s.adjoint_sweep(tape["ckpt"], self.C, self.n_steps, adj, gin)
         gT = self._zeros(s.N)
-        s.initial_T_adjoint(self._ckpt[0], adj, gT)
+        s.initial_T_adjoint(tape["ckpt"][0], adj, gT)
         return gin.reshape(self.dim, self.ny), gT
 
 
@@ -84,10 +97,11 @@ class HybridStepFn(torch.autograd.Function):
         ctx.problem = problem
         ctx.meta = (inlet_u.dtype, inlet_u.device, T0.dtype, T0.device)
         J = problem.forward(inlet_u.detach().cpu().numpy(), T0.detach().cpu().numpy())
+        ctx.tape = problem.tape  # this call's own checkpoints: later forward calls do not touch them
         return torch.tensor(J, dtype=torch.float64, device=inlet_u.device)
 
     @staticmethod
     def backward(ctx, gJ):
-        gin, gT = ctx.problem.backward(float(gJ))
+        gin, gT = ctx.problem.backward(float(gJ), tape=ctx.tape)
         idt, idev, tdt, tdev = ctx.meta
         return gin.to(dtype=idt, device=idev), gT.to(dtype=tdt, device=tdev), None

@@ -210,6 +210,33 @@ def test_autograd_function():
     assert _rel(T0.grad.numpy(), 2.0 * gT_ref) < 1e-9
 
 
+def test_autograd_two_graphs_reversed_in_any_order():
+    """Two forward calls on the same problem with different inlet velocities and initial
+    temperatures, each through HybridStepFn; the backward of the first graph, taken after the
+    second forward, must still give the first call's gradient (oracle reverse mode)."""
+    from paper_2207_11567_gb300 import HybridStepFn
+    wl = _case("f64")
+    pb = _problem(wl, 6, C=4)
+    inlet0 = np.asarray(wl.inlet_u, dtype=np.float64).reshape(2, -1)
+    T00 = np.asarray(wl.T, dtype=np.float64).reshape(-1)
+    fluid = np.asarray(wl.mask).reshape(-1) == 0
+    ia = torch.tensor(inlet0, requires_grad=True)
+    ta = torch.tensor(T00, requires_grad=True)
+    ib = torch.tensor(1.1 * inlet0, requires_grad=True)
+    tb = torch.tensor(np.where(fluid, T00 + 5.0, T00), requires_grad=True)
+    Ja = HybridStepFn.apply(ia, ta, pb)
+    Jb = HybridStepFn.apply(ib, tb, pb)
+    Ja.backward()
+    Jb.backward()
+    pb.close()
+    ref_a = oracle_fuel_gradient(wl, 6, FUEL)
+    ref_b = oracle_fuel_gradient(wl, 6, FUEL, inlet_u=1.1 * inlet0, T0=np.where(fluid, T00 + 5.0, T00))
+    for J, gi, gt, (J_ref, gin_ref, gT_ref) in ((Ja, ia.grad, ta.grad, ref_a), (Jb, ib.grad, tb.grad, ref_b)):
+        assert abs(J.item() - J_ref) <= 1e-11 * abs(J_ref)
+        assert _rel(gi.numpy(), gin_ref) < 1e-9
+        assert _rel(gt.numpy(), gT_ref) < 1e-9
+
+
 def test_adjoint_rejects_unsupported_configs():
     from paper_2207_11567_gb300 import _lib as L, from_workload
     wl = W.generate.swirl_3d(nx=16, ny=12, nz=12, reactive=False, storage="f32", seed=1)
