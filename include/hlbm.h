@@ -26,8 +26,10 @@
  *   - Masks: uint8 per cell, 0 = fluid, anything else = solid (never updated).
  *   - Boundaries per face: LBM_BC_PERIODIC, LBM_BC_WALL (halfway bounce-back, zero-gradient
  *     scalars), LBM_BC_INLET (low-x face only: bounce-back from a wall moving with the inlet
- *     velocity, Dirichlet T_in / Y_in), LBM_BC_OUTLET (high-x face only: zero-gradient copy of
- *     the populations and scalars).
+ *     velocity, Dirichlet T_in / Y_in), LBM_BC_OUTLET (high-x face only: anti-bounce-back
+ *     pressure outlet at the half-way face, g_i = -g*_opp + 2 w_i (P_ref + rho (1.5 (c_i.u)^2
+ *     - 0.5 u^2)) with u of the outlet cell from the previous step, i.e. twice the even part of
+ *     the Eq. 6 equilibrium at the outlet pressure P_ref; zero-gradient T and Y).
  *   - Ownership: the caller owns every pointer it passes; the library copies inputs during the
  *     call and owns its internal device buffers (allocated through cfg.alloc/cfg.free when given,
  *     else cudaMalloc/cudaFree).
@@ -55,7 +57,9 @@ typedef enum {
   LBM_ERR_CUDA = 3,        /* a CUDA runtime call failed                               */
   LBM_ERR_STATE = 4,       /* call out of order (e.g. step before set_fields)          */
   LBM_ERR_NONFINITE = 5,   /* a non-finite velocity was produced by a step             */
-  LBM_ERR_UNSUPPORTED = 6  /* valid request this build does not implement              */
+  LBM_ERR_UNSUPPORTED = 6, /* valid request this build does not implement              */
+  LBM_ERR_TIMEOUT = 7      /* a bounded wait inside a kernel ran out (a data tile of the
+                              tiled FD update did not arrive); the kernel returned early */
 } lbm_status;
 
 enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_INLET = 2, LBM_BC_OUTLET = 3 };
@@ -148,13 +152,35 @@ lbm_status lbm_set_inlet(lbm_ctx* ctx, const double* inlet_u, int on_device);
  * adjoint calls return LBM_ERR_UNSUPPORTED while it is on. */
 lbm_status lbm_set_thermo(lbm_ctx* ctx, const double* cp, double T0);
 
+/* Mixture-averaged species diffusion (Section 2.3: the paper evaluates its transport properties
+ * with mixture-averaged approximations). Le_pair: host array [n_species][n_species] of pair Lewis
+ * numbers, rho D_kj = mu / (Pr Le_kj) (binary diffusion data expressed against the conductivity;
+ * the diagonal is not used); NULL returns to the constant Lewis numbers of cfg. Per cell the
+ * Hirschfelder-Curtiss coefficient rho D_k = (mu / Pr) / Le_k^mix with
+ * Le_k^mix = sum_{j!=k} (X_j + 1e-10) Le_kj / sum_{j!=k} (X_j + 1e-10), X_j = max(Y_j W / W_j, 0);
+ * per face the mass flux is that of the mole-fraction gradient with a correction velocity,
+ * J_k = G_k,f (dY_k + Y_k,f dlnW) - Y_k,f sum_j G_j,f (dY_j + Y_j,f dlnW) (arithmetic face means,
+ * dlnW = (W_n - W) / mean W), so that the fluxes sum to zero and equal Le_kj give the constant-Lewis
+ * update. The temperature equation is unchanged (constant c_p). The library allocates one
+ * [(n_species + 1)][N] coefficient array on the first call. LBM_ERR_UNSUPPORTED together with
+ * variable heat capacities or interpolated walls; the adjoint calls return LBM_ERR_UNSUPPORTED
+ * while it is on. */
+lbm_status lbm_set_transport(lbm_ctx* ctx, const double* Le_pair);
+
 /* Initial fields: T [N] (K), Y [n_species][N], u [dim][N], P_h [N] (lattice), g_pert [Q][N]
  * (lattice, may be NULL). Populations are set to the equilibrium of Eq. 6 plus g_pert. T and Y
  * are ignored (may be NULL) when cfg.thermal == 0. Requires lbm_set_geometry first. */
 lbm_status lbm_set_fields(lbm_ctx* ctx, const double* T, const double* Y, const double* u,
                           const double* P_h, const double* g_pert, int on_device);
 
-/* Advance n_steps full steps, asynchronously on the context's stream. */
+/* Advance n_steps full steps of the hybrid scheme (Section 2), asynchronously on the context's
+ * stream. Each step, in this order: the finite-difference update of T and Y_k (Section 2.3) with
+ * the Arrhenius sources, the thickened-flame factor and the flame sensor, which also gives rho
+ * and Lambda (Eq. 3) at the current level; in a closed domain the thermodynamic-pressure update
+ * (P = M / I, a reduction over all fluid cells); the lattice Boltzmann stream and collide
+ * (Eq. 1, 2, 7, 13, 9-12, 8) with that rho and Lambda. n_steps >= 0; LBM_ERR_STATE before
+ * lbm_set_fields. Failures inside a kernel are reported by the next lbm_get_fields
+ * (LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT). */
 lbm_status lbm_step(lbm_ctx* ctx, int n_steps);
 
 /* Field selection bits for lbm_get_fields. Output is FP64, concatenated in bit order:
@@ -165,7 +191,8 @@ enum { LBM_F_T = 1, LBM_F_Y = 2, LBM_F_U = 4, LBM_F_PH = 8, LBM_F_RHO = 16, LBM_
        LBM_F_G = 64 };
 /* Number of doubles lbm_get_fields writes for these bits. */
 size_t lbm_fields_size(const lbm_ctx* ctx, unsigned bits);
-/* Reports LBM_ERR_NONFINITE if any step since the last check produced a non-finite velocity. */
+/* Reports LBM_ERR_NONFINITE if any step since the last check produced a non-finite velocity, and
+ * LBM_ERR_TIMEOUT if a kernel's bounded wait for its data ran out (the fields are then invalid). */
 lbm_status lbm_get_fields(lbm_ctx* ctx, unsigned bits, double* dst, int dst_on_device);
 
 /* Thermodynamic pressure state: out[0] = P_th (Pa), out[1] = last increment of P_th (Pa per
@@ -351,14 +378,19 @@ lbm_status lbm_use_graphs(lbm_ctx* ctx, int enable);
  * with the kernel and exact fixed-point partial sums that lbm_step uses every step, and writes
  * it to I_out. T [n_cells] and Y [n_species][n_cells] are FP32, mask [n_cells] uint8, I_out one
  * double: all device pointers. W: n_species molar masses (kg/mol) in host memory. Work is
- * enqueued on `stream` (NULL = legacy default stream); the call returns before it completes.
+ * enqueued on `stream` (NULL = legacy default stream of the current device) and runs on the
+ * stream's device, which the call makes current while it enqueues and then restores; the call
+ * returns before the work completes. Per cell the term T_ref W / (max_k W_k T) is formed in FP32
+ * and summed exactly in 64-bit fixed point (resolution 2^-32); if any cell's term is non-finite
+ * or 2^30 and above (e.g. T = 0 in a fluid cell), I_out receives NaN (the status cannot report
+ * it, since the call does not wait for the GPU).
  * It calls no allocator: per-block partial sums go to a static device array of 1 MiB that every
  * GPU loading this library holds until the process exits, which limits n_cells to 16777216
  * (larger sizes return LBM_ERR_ARG). The first call on a device resolves that array's device
  * address (cudaGetSymbolAddress) and should therefore come before any stream capture on that
  * device. All calls on a device share the array, so calls that overlap on the GPU (on
- * different streams) race; nothing in the array needs to start at zero, since each call
- * overwrites every slot it reads. err (may be NULL) receives a one-line message. */
+ * different streams) race; each call overwrites every slot it reads and clears its counter of
+ * out-of-range cells before use. err (may be NULL) receives a one-line message. */
 lbm_status lbm_pth_integral_noalloc(const float* T, const float* Y, const uint8_t* mask, int n_cells,
                                    int n_species, const double* W, double T_ref, double rho_ref,
                                    double* I_out, void* stream, char* err, size_t err_len);

@@ -14,9 +14,9 @@ MAX_REACTIONS = 4
 KERNEL_KINDS = 4
 KERNEL_NAMES = ("fd_update", "flame_sensor", "pth_update", "lb_stream_collide")
 
-LBM_OK, LBM_ERR_ARG, LBM_ERR_ALLOC, LBM_ERR_CUDA, LBM_ERR_STATE, LBM_ERR_NONFINITE, LBM_ERR_UNSUPPORTED = range(7)
+LBM_OK, LBM_ERR_ARG, LBM_ERR_ALLOC, LBM_ERR_CUDA, LBM_ERR_STATE, LBM_ERR_NONFINITE, LBM_ERR_UNSUPPORTED, LBM_ERR_TIMEOUT = range(8)
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_ALLOC", 3: "ERR_CUDA", 4: "ERR_STATE", 5: "ERR_NONFINITE",
-                6: "ERR_UNSUPPORTED"}
+                6: "ERR_UNSUPPORTED", 7: "ERR_TIMEOUT"}
 BC = {"periodic": 0, "wall": 1, "inlet": 2, "outlet": 3}
 STORAGE = {"f64": 0, "f32": 1, "f16": 2}
 COLLISION = {"bgk": 0, "cumulant": 1}
@@ -91,6 +91,7 @@ def _load():
         "lbm_flame_properties": (C.c_int, [P, C.c_int, P, P]),
         "lbm_set_inlet": (C.c_int, [P, P, C.c_int]),
         "lbm_set_thermo": (C.c_int, [P, P, C.c_double]),
+        "lbm_set_transport": (C.c_int, [P, P]),
         "lbm_adjoint_sweep": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, P, P]),
         "lbm_set_probes": (C.c_int, [P, C.c_int, P, C.c_longlong, C.c_int]),
         "lbm_get_probes": (C.c_int, [P, P, C.c_int, C.POINTER(C.c_longlong)]),
@@ -115,7 +116,7 @@ EXPORTED = ("lbm_init", "lbm_destroy", "lbm_last_error", "lbm_set_geometry", "lb
             "lbm_initial_T_adjoint", "lbm_adjoint_segment", "lbm_set_wall_fractions",
             "lbm_set_wall_links", "lbm_stats_control", "lbm_get_stats", "lbm_flame_length",
             "lbm_flame_properties", "lbm_set_inlet", "lbm_set_probes", "lbm_get_probes", "lbm_welch_psd",
-            "lbm_probe_spectrum", "lbm_set_thermo", "lbm_adjoint_sweep")
+            "lbm_probe_spectrum", "lbm_set_thermo", "lbm_adjoint_sweep", "lbm_set_transport")
 
 
 class HLBMError(RuntimeError):

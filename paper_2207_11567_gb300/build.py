@@ -9,9 +9,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhlbm.so")
-SOURCES = ["api.cu", "aux_kernels.cu", "stats.cu", "fd_kernels.cu", "lb_d2q9.cu", "lb_d3q27_f64.cu",
+SOURCES = ["api.cu", "aux_kernels.cu", "stats.cu", "fd_kernels.cu", "fd_tiled.cu", "lb_d2q9.cu", "lb_d3q27_f64.cu",
            "lb_d3q27_f32.cu", "lb_d3q27_f16.cu", "noalloc.cu", "adjoint.cu",
-           "flame.cu", "probes.cu", "fd_kernels_vcp.cu"]
+           "flame.cu", "probes.cu", "fd_kernels_vcp.cu", "fd_kernels_mix.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -51,7 +51,11 @@ struct lbm_ctx {
   uint8_t* mask = nullptr;
   void* inlet_u = nullptr;
   void* partials = nullptr;
-  int nblocks_fd = 0;    // partial slots written by the FD kernel
+  int nblocks_fd = 0;    // partial slots written by fd_step_kernel over the whole grid
+  FDTiledMaps* tiled = nullptr;  // tiled FD update (3-D FP32), nullptr where it does not apply
+  int nblocks_tiled = 0;         // partial slots written by the tiled update
+  size_t n_fd_wall_rows = 0;     // cells with ghost-point wall weights (fd_step_kernel, walls only)
+  void* mix = nullptr;           // mixture-averaged diffusion: per-cell G_k and W [(K + 1)][N]
   int nblocks_init = 0;  // partial slots written by the initial-integral kernel
   PthState* pth = nullptr;
   void* pth_stage = nullptr;            // block sums of the P_th reduction
@@ -266,6 +270,7 @@ template <typename R> void fill_fdconst(FDConst<R>& f, const lbm_config& c, int 
   f.dt_phys = (R)c.dt;
   f.inv_cp = (R)(1.0 / c.cp);
   f.inv_rho_ref = (R)(1.0 / c.rho_ref);
+  f.rho_ref_f = (R)c.rho_ref;
   f.F = (R)c.thicken_F;
   f.sensor_beta = (R)c.sensor_beta;
   f.inv_wref = (R)(c.sensor_wref > 0 ? 1.0 / c.sensor_wref : 0.0);
@@ -323,6 +328,10 @@ template <typename R> FDArgs<R> make_fd_args(lbm_ctx* c, int cur) {
   a.pth = c->pth;
   a.fd_row = c->fd_row;
   a.fd_w = (const R*)c->fd_w;
+  a.flag = c->flag;
+  a.mix = (const R*)c->mix;
+  a.walls_only = 0;
+  a.part_offset = 0;
   a.c = fdconst<R>(c);
   return a;
 }
@@ -343,12 +352,29 @@ cudaError_t run_lb(lbm_ctx* c, int cur, bool want_out) {
   return c->D == 2 ? launch_lb<2, float, float>(a, th, co, c->st) : launch_lb<3, float, float>(a, th, co, c->st);
 }
 
+// the tiled update applies (3-D FP32, constant heat capacity, grid and chemistry it supports)
+bool use_tiled(const lbm_ctx* c) { return c->tiled && !c->fdc_f.varcp && !c->fdc_f.mixavg; }
+
+// partial slots of the P_th reduction written by one FD update
+int fd_slots(const lbm_ctx* c) {
+  if (!use_tiled(c)) return c->nblocks_fd;
+  return c->nblocks_tiled + (c->n_fd_wall_rows ? c->nblocks_fd : 0);
+}
+
 cudaError_t run_fd(lbm_ctx* c, int cur, bool sensor_pass) {
   if (c->f64) {
     auto a = make_fd_args<double>(c, cur);
     return c->D == 2 ? launch_fd<2, double>(a, c->st, sensor_pass) : launch_fd<3, double>(a, c->st, sensor_pass);
   }
   auto a = make_fd_args<float>(c, cur);
+  if (!sensor_pass && use_tiled(c)) {
+    cudaError_t e = launch_fd_tiled(a, *c->tiled, cur, c->st);
+    if (e != cudaSuccess || !c->n_fd_wall_rows) return e;
+    // cells with ghost-point wall weights: the general kernel, partial slots after the tiled ones
+    a.walls_only = 1;
+    a.part_offset = c->nblocks_tiled;
+    return launch_fd<3, float>(a, c->st, false);
+  }
   return c->D == 2 ? launch_fd<2, float>(a, c->st, sensor_pass) : launch_fd<3, float>(a, c->st, sensor_pass);
 }
 
@@ -372,7 +398,7 @@ cudaError_t timed(lbm_ctx* c, int kind, cudaError_t (*fn)(lbm_ctx*, int, int), i
 cudaError_t fd_thunk(lbm_ctx* c, int cur, int sensor) { return run_fd(c, cur, sensor != 0); }
 cudaError_t lb_thunk(lbm_ctx* c, int cur, int want) { return run_lb(c, cur, want != 0); }
 cudaError_t pth_thunk(lbm_ctx* c, int, int) {
-  return launch_pth_update(c->pu, c->partials, c->nblocks_fd, c->pth_stage, c->pth_counter, c->pth, 0, c->st);
+  return launch_pth_update(c->pu, c->partials, fd_slots(c), c->pth_stage, c->pth_counter, c->pth, 0, c->st);
 }
 
 // One full step from parity `cur`: FD (+ sensor) -> P_th -> LB.
@@ -493,7 +519,12 @@ lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
   ok = ok && (ctx->flag = (int*)dalloc(ctx, 16));
   ctx->nblocks_fd = fd_partial_blocks(ctx->D, ctx->geo);
   ctx->nblocks_init = (int)((N + AUX_BLOCK - 1) / AUX_BLOCK);
-  ok = ok && (ctx->partials = dalloc(ctx, (size_t)std::max(ctx->nblocks_fd, ctx->nblocks_init) * 16));
+  if (c.thermal && fd_tiled_eligible(ctx->geo, ctx->D, ctx->f64, 0, ctx->K, c.n_reactions)) {
+    ctx->tiled = fd_tiled_create();
+    if (!ctx->tiled) ok = false;
+  }
+  ok = ok && (ctx->partials = dalloc(ctx, (size_t)std::max(ctx->nblocks_fd * (ctx->tiled ? 2 : 1),
+                                                           ctx->nblocks_init) * 16));
   ok = ok && (ctx->pth_stage = dalloc(ctx, (size_t)pth_stage_words() * 8));
   ok = ok && (ctx->pth_counter = (unsigned int*)dalloc(ctx, 16));
   if (c.thermal) {
@@ -511,6 +542,14 @@ lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
   CK(cudaMemsetAsync(ctx->flag, 0, 16, ctx->st), "memset");
   CK(cudaMemsetAsync(ctx->pth_counter, 0, 16, ctx->st), "memset");
   CK(cudaMemsetAsync(ctx->inlet_u, 0, (size_t)ctx->D * c.ny * c.nz * ctx->F, ctx->st), "memset");
+  if (ctx->tiled) {
+    int n_sm = 0;
+    CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->dev), "device attribute");
+    CK(fd_tiled_setup(*ctx->tiled, ctx->geo, ctx->K, ctx->T, ctx->Y, ctx->Floc, ctx->u, ctx->sword, n_sm),
+       "tensor maps of the tiled FD update");
+    ctx->nblocks_tiled = fd_tiled_blocks(*ctx->tiled);
+    if (ctx->nblocks_tiled > ctx->nblocks_fd) return fail(ctx, LBM_ERR_ARG, "tiled FD grid too large");
+  }
   for (int b = 0; b < 2; ++b)
     if (ctx->Floc[b]) CK(cudaMemsetAsync(ctx->Floc[b], 0, N * ctx->F, ctx->st), "memset");
   return LBM_OK;
@@ -532,6 +571,7 @@ void lbm_destroy(lbm_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   if (ctx->st2) cudaStreamDestroy(ctx->st2);
   dfree_all(ctx);
+  fd_tiled_destroy(ctx->tiled);
   if (ctx->own_stream) cudaStreamDestroy(ctx->st);
   delete ctx;
 }
@@ -598,6 +638,8 @@ template <typename R> void fill_thermo(FDConst<R>& f, const lbm_config& c, int K
 
 lbm_status lbm_set_thermo(lbm_ctx* ctx, const double* cp, double T0) {
   if (!ctx) return LBM_ERR_ARG;
+  if (cp && ctx->fdc_d.mixavg)
+    return fail(ctx, LBM_ERR_UNSUPPORTED, "variable heat capacities with mixture-averaged diffusion");
   if (cp && (!ctx->cfg.thermal || !(T0 > 0.0)))
     return fail(ctx, LBM_ERR_ARG, "variable heat capacities need a thermal run and T0 > 0");
   if (cp)
@@ -605,6 +647,54 @@ lbm_status lbm_set_thermo(lbm_ctx* ctx, const double* cp, double T0) {
       if (!std::isfinite(cp[i])) return fail(ctx, LBM_ERR_ARG, "non-finite heat-capacity coefficient");
   fill_thermo<float>(ctx->fdc_f, ctx->cfg, ctx->K, cp, T0);
   fill_thermo<double>(ctx->fdc_d, ctx->cfg, ctx->K, cp, T0);
+  drop_graphs(ctx);  // the captured launches hold the old constants
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename R> void fill_transport(FDConst<R>& f, const lbm_config& c, int K, const double* Le, double W_in) {
+  f.mixavg = Le ? 1 : 0;
+  f.W_in = (R)W_in;
+  for (int k = 0; k < MAX_SP; ++k) {
+    f.inv_Lemix_in[k] = R(0);
+    for (int j = 0; j < MAX_SP; ++j) f.Le_pair[k][j] = (k < K && j < K && Le) ? (R)Le[k * K + j] : R(1);
+  }
+  if (!Le) return;
+  // 1 / Le_k^mix of the inlet state (the inlet ghost's coefficient), same rule as mix_coeff_kernel
+  double X[MAX_SP];
+  for (int k = 0; k < K; ++k) X[k] = std::max(c.Y_in[k] * W_in / c.sp[k].W, 0.0) + 1e-10;
+  for (int k = 0; k < K; ++k) {
+    double num = 0.0, den = 0.0;
+    for (int j = 0; j < K; ++j)
+      if (j != k) {
+        num += X[j] * Le[k * K + j];
+        den += X[j];
+      }
+    f.inv_Lemix_in[k] = (R)(den / num);
+  }
+}
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_set_transport(lbm_ctx* ctx, const double* Le_pair) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (Le_pair) {
+    if (!ctx->cfg.thermal || ctx->K < 2) return fail(ctx, LBM_ERR_ARG, "mixture-averaged diffusion needs species");
+    for (int i = 0; i < ctx->K * ctx->K; ++i)
+      if (!std::isfinite(Le_pair[i]) || !(Le_pair[i] > 0.0))
+        return fail(ctx, LBM_ERR_ARG, "pair Lewis numbers must be finite and > 0");
+    if (ctx->fdc_d.varcp)
+      return fail(ctx, LBM_ERR_UNSUPPORTED, "mixture-averaged diffusion with variable heat capacities");
+    if (ctx->n_fd_wall_rows)
+      return fail(ctx, LBM_ERR_UNSUPPORTED, "mixture-averaged diffusion with ghost-point (curved) walls");
+    if (!ctx->mix && !(ctx->mix = dalloc(ctx, (size_t)(ctx->K + 1) * ctx->N * ctx->F)))
+      return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+  }
+  fill_transport<float>(ctx->fdc_f, ctx->cfg, ctx->K, Le_pair, ctx->W_in);
+  fill_transport<double>(ctx->fdc_d, ctx->cfg, ctx->K, Le_pair, ctx->W_in);
   drop_graphs(ctx);  // the captured launches hold the old constants
   return LBM_OK;
 }
@@ -883,6 +973,7 @@ lbm_status lbm_get_fields(lbm_ctx* ctx, unsigned bits, double* dst, int dst_on_d
   CK(cudaStreamSynchronize(ctx->st), "sync");
   if (flag) {
     CK(cudaMemsetAsync(ctx->flag, 0, 4, ctx->st), "memset");
+    if (flag & 4) return fail(ctx, LBM_ERR_TIMEOUT, "a plane load of the FD update did not arrive in time");
     return fail(ctx, LBM_ERR_NONFINITE, "a step produced a non-finite velocity");
   }
   return LBM_OK;
@@ -1010,7 +1101,7 @@ lbm_status lbm_kernel_bytes(const lbm_ctx* ctx, double bytes[LBM_KERNEL_KINDS]) 
   // of this state and write that of the next
   bytes[KIND_FD] = th ? Nf * ((2.0 * (1 + K) + D + 2.0 + (ctx->cfg.flame_sensor ? 2.0 : 0.0)) * F) + 4.0 * N : 0.0;
   bytes[KIND_SENSOR] = (th && ctx->cfg.flame_sensor) ? Nf * 4.0 * F + N : 0.0;
-  bytes[KIND_PTH] = (th && ctx->cfg.closed_domain) ? 16.0 * ctx->nblocks_fd : 0.0;
+  bytes[KIND_PTH] = (th && ctx->cfg.closed_domain) ? 16.0 * fd_slots(ctx) : 0.0;
   // LB: populations read + written, link word, and (thermal) rho, Lambda, T read + u written
   bytes[KIND_LB] = Nf * (2.0 * Q * S + (th ? (3.0 + D) * F : 0.0)) + 4.0 * N;
   return LBM_OK;
@@ -1316,6 +1407,9 @@ template <typename R> lbm_status set_fd_walls(lbm_ctx* ctx, const std::vector<in
       }
   }
   const size_t nr = w.size() / W;
+  if (nr > 0 && ctx->fdc_d.mixavg)
+    return fail(ctx, LBM_ERR_UNSUPPORTED, "ghost-point (curved) walls with mixture-averaged diffusion");
+  ctx->n_fd_wall_rows = nr;
   if (nr > 0) {
     if (!ctx->fd_row && !(ctx->fd_row = (int*)dalloc(ctx, N * sizeof(int))))
       return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
@@ -1406,10 +1500,10 @@ lbm_status adjoint_supported(lbm_ctx* ctx) {
   const lbm_config& c = ctx->cfg;
   const bool hi1 = c.omega_hi[0] == 1.0 && c.omega_hi[1] == 1.0;
   if (c.dim != 2 || c.storage == LBM_STORE_F16 || c.collision != LBM_COLL_CUMULANT || !hi1 || c.closed_domain ||
-      c.flame_sensor || ctx->n_wall > 0 || ctx->fdc_d.varcp)
+      c.flame_sensor || ctx->n_wall > 0 || ctx->fdc_d.varcp || ctx->fdc_d.mixavg)
     return fail(ctx, LBM_ERR_UNSUPPORTED,
                 "adjoint: 2-D, FP32/FP64 storage, cumulant collision with default higher-order rates, open domain, "
-                "no flame sensor, half-way walls, constant heat capacity");
+                "no flame sensor, half-way walls, constant heat capacity, constant Lewis numbers");
   return LBM_OK;
 }
 }  // namespace
@@ -1480,6 +1574,8 @@ lbm_status lbm_set_wall_links(lbm_ctx* ctx, long long n_links, const int* cell, 
   if (!ctx) return LBM_ERR_ARG;
   if (!ctx->have_geo) return fail(ctx, LBM_ERR_STATE, "set_geometry must come first");
   if (n_links < 0 || (n_links > 0 && (!cell || !dir || !q))) return fail(ctx, LBM_ERR_ARG, "null argument");
+  if (n_links > 0 && ctx->fdc_d.mixavg)
+    return fail(ctx, LBM_ERR_UNSUPPORTED, "interpolated walls with mixture-averaged diffusion");
   CK(cudaSetDevice(ctx->dev), "cudaSetDevice");
   return ctx->f64 ? set_wall_impl<double>(ctx, n_links, cell, dir, q)
                   : set_wall_impl<float>(ctx, n_links, cell, dir, q);

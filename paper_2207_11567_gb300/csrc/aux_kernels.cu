@@ -180,13 +180,16 @@ __global__ void get_fields_kernel(int D, Geo g, unsigned bits, int K, const S* _
 // the same partial layout as the per-step reduction of the finite-difference kernel.
 template <typename R>
 __global__ void init_integral_kernel(Geo g, const uint8_t* __restrict__ mask, const R* __restrict__ T,
-                                     const R* __restrict__ Y, FDConst<R> c, void* __restrict__ partials) {
+                                     const R* __restrict__ Y, FDConst<R> c, void* __restrict__ partials,
+                                     unsigned long long* __restrict__ bad) {
   const int r = blockIdx.x * AUX_BLOCK + threadIdx.x;
   R v = R(0);
   if (r < g.N && mask[r] == 0) {
     R s = R(0);
     for (int k = 0; k < c.K; ++k) s += Y[(size_t)k * g.N + r] * (R)c.inv_W[k];
     v = (R)c.I_scale / (s * T[r]);
+    // bad: count of fluid cells whose term the fixed-point sum cannot hold (non-finite, |v| >= 2^30)
+    if (sizeof(R) == 4 && bad && !fix32_in_range((float)v)) atomicAdd(bad, 1ull);
   }
   if constexpr (sizeof(R) == 4) {
     __shared__ long long sh[AUX_BLOCK];
@@ -339,14 +342,16 @@ cudaError_t launch_get_fields(int D, const Geo& g, unsigned bits, int K, const S
 
 template <typename R>
 cudaError_t launch_init_integral(const Geo& g, const uint8_t* mask, const R* T, const R* Y, const FDConst<R>& c,
-                                 void* partials, int nblocks, cudaStream_t st) {
-  init_integral_kernel<R><<<nblocks, AUX_BLOCK, 0, st>>>(g, mask, T, Y, c, partials);
+                                 void* partials, int nblocks, cudaStream_t st, unsigned long long* bad) {
+  init_integral_kernel<R><<<nblocks, AUX_BLOCK, 0, st>>>(g, mask, T, Y, c, partials, bad);
   return cudaGetLastError();
 }
 template cudaError_t launch_init_integral<float>(const Geo&, const uint8_t*, const float*, const float*,
-                                                 const FDConst<float>&, void*, int, cudaStream_t);
+                                                 const FDConst<float>&, void*, int, cudaStream_t,
+                                                 unsigned long long*);
 template cudaError_t launch_init_integral<double>(const Geo&, const uint8_t*, const double*, const double*,
-                                                  const FDConst<double>&, void*, int, cudaStream_t);
+                                                  const FDConst<double>&, void*, int, cudaStream_t,
+                                                  unsigned long long*);
 
 int pth_stage_words() { return 2 * PTH_BLOCKS; }
 

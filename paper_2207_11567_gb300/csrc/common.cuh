@@ -66,6 +66,7 @@ template <typename R> struct FDConst {
   R dt_phys;              // s
   R inv_cp;               // 1 / cp
   R inv_rho_ref;
+  R rho_ref_f;            // 1 / inv_rho_ref
   R F, sensor_beta, inv_wref, sensor_Ta;
   R eps_T, eps_Y;
   R T_in, Y_in[MAX_SP];
@@ -88,6 +89,12 @@ template <typename R> struct FDConst {
   R cp_poly[MAX_SP][5];
   R hW_poly[MAX_SP][6];
   R cp_in;
+  // mixture-averaged species diffusion (lbm_set_transport; mixavg = 0: constant Lewis numbers):
+  // pair Lewis numbers Le_kj (rho D_kj = mu / (Pr Le_kj)), the inlet state's 1 / Le_k^mix and W
+  int mixavg;
+  R Le_pair[MAX_SP][MAX_SP];
+  R inv_Lemix_in[MAX_SP];
+  R W_in;
 };
 
 // ---------------------------------------------------------------------------- storage
@@ -119,12 +126,15 @@ template <typename R> __device__ __forceinline__ R ldg(const R* p) { return __ld
 // ---------------------------------------------------------------------------- fixed point
 // x * 2^32 as a 64-bit integer, using integer operations only (the value of a float is
 // mantissa * 2^(exponent - 23), so the product is a shift of the mantissa). Bits below 2^-32
-// are truncated; |x| must stay below 2^30. Summing these integers is exact and independent of
-// the order, which makes the reductions deterministic.
+// are truncated. Summing these integers is exact and independent of the order, which makes the
+// reductions deterministic. |x| >= 2^30, infinities and NaN saturate to +-2^62 (no shift past the
+// word); callers that take terms from outside check the range themselves (fix32_in_range).
+__device__ __forceinline__ bool fix32_in_range(float x) { return fabsf(x) < 1073741824.0f; }
 __device__ __forceinline__ long long f32_to_fix32(float x) {
   const unsigned b = __float_as_uint(x);
   const int e = (int)((b >> 23) & 0xffu);
   if (e == 0) return 0;  // zero or subnormal: below the resolution
+  if (e >= 127 + 30) return (b >> 31) ? -(1LL << 62) : (1LL << 62);
   const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
   const int sh = e - 127 - 23 + 32;
   long long v = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0);
@@ -197,6 +207,10 @@ template <typename R> struct FDArgs {
   // that of the distance-2 wall ghost seen past the fluid neighbour (phi_1 + w (phi_r - phi_1))
   const int* fd_row;
   const R* fd_w;      // [rows][2][2 D]
+  int* flag;          // error bits: 4 = a plane load of the tiled update did not arrive in time
+  const R* mix;       // mixture-averaged diffusion: per cell G_k [K][N] and W [N] (mix_coeff_kernel)
+  int walls_only;     // fd_step_kernel: update only the cells flagged SW_WALL
+  int part_offset;    // fd_step_kernel: first partial slot it writes
   FDConst<R> c;
 };
 

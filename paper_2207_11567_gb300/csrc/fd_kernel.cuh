@@ -170,7 +170,12 @@ template <int DEG, typename R> __device__ __forceinline__ R hW_eval(const R (&a)
 // lambda = F mu c_p / Pr per cell (face value the arithmetic mean, a ghost neighbour's c_p from its
 // ghost T and Y), centred gradients. The species fields run first so that the neighbours' c_p and
 // the species-enthalpy flux are summed before the temperature field.
-template <int D, typename R, int NK, int NR, bool FAST, int VDEG, bool GW = false>
+// MIX: mixture-averaged species diffusion. With G_k = F mu / (Pr Le_k^mix) and W per cell (from
+// mix_coeff_kernel; ghosts: the own cell's values, the inlet state's at the inlet) and, per face,
+// the arithmetic means G_k,f, Y_k,f and dlnW = (W_n - W_r) / mean W, the species term is
+//   sum_faces [G_k,f (dY_k + Y_k,f dlnW) - Y_k,f C_f],  C_f = sum_j G_j,f (dY_j + Y_j,f dlnW)
+// (differences neighbour minus cell), the Hirschfelder-Curtiss flux with its correction velocity.
+template <int D, typename R, int NK, int NR, bool FAST, int VDEG, bool GW = false, bool MIX = false>
 __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z, int r, uint32_t sw, R& termI,
                                         R& termM) {
   const FDConst<R>& c = a.c;
@@ -326,6 +331,37 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
       }
     }
     R tflux = R(0);
+    // MIX: per face dlnW and the correction sum C_f (ghost neighbours as in the species stencil)
+    R mdl[MIX ? 3 : 1][2], mcr[MIX ? 3 : 1][2];
+    R Wm = R(0);
+    if constexpr (MIX) {
+      Wm = a.mix[(size_t)K * N + r];
+      const R muin = c.nu_lat * powr<R>(c.T_in * c.T_ref_inv, c.mu_exp);
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          const int kk = k1[ax][sd];
+          const int j = i1[ax][sd];
+          const R Wn = kk == NB_FLUID ? a.mix[(size_t)K * N + j] : (kk == NB_INLET ? c.W_in : Wm);
+          const R dl = (Wn - Wm) / (R(0.5) * (Wn + Wm));
+          R cr = R(0);
+#pragma unroll
+          for (int jj = 0; jj < KMAX; ++jj) {
+            if (NK > 0 || jj < K) {
+              const R Gr = a.mix[(size_t)jj * N + r];
+              const R Gn = kk == NB_FLUID ? a.mix[(size_t)jj * N + j]
+                                          : (kk == NB_INLET ? Fr * muin * c.inv_Pr * c.inv_Lemix_in[jj] : Gr);
+              const R Yn = kk == NB_FLUID ? ldg(a.Y + (size_t)jj * N + j) : (kk == NB_INLET ? c.Y_in[jj] : Yr[jj]);
+              const R Yb = R(0.5) * (Yr[jj] + Yn);
+              cr += R(0.5) * (Gr + Gn) * ((Yn - Yr[jj]) + Yb * dl);
+            }
+          }
+          mdl[ax][sd] = dl;
+          mcr[ax][sd] = cr;
+        }
+      }
+    }
     // fields: 0 = T, 1.. = Y_k (VCP: the species first, T last)
 #pragma unroll 1
     for (int it = 0; it <= K; ++it) {
@@ -392,6 +428,19 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
             dif += R(0.5) * (Frm + FMn[ax][1] * cpn[ax][1]) * dp1 - R(0.5) * (Frm + FMn[ax][0] * cpn[ax][0]) * dm1;
             tflux += gYw[ax] * (p1 - m1);
           }
+        } else if (MIX && fi > 0) {
+          const R Gr = a.mix[(size_t)(fi - 1) * N + r];
+#pragma unroll
+          for (int sd = 0; sd < 2; ++sd) {
+            const int kk = k1[ax][sd];
+            const R Gn = kk == NB_FLUID ? a.mix[(size_t)(fi - 1) * N + i1[ax][sd]]
+                                        : (kk == NB_INLET ? Fr * c.nu_lat * powr<R>(c.T_in * c.T_ref_inv, c.mu_exp) *
+                                                                c.inv_Pr * c.inv_Lemix_in[fi - 1]
+                                                          : Gr);
+            const R pn = sd ? p1 : m1;
+            const R Yb = R(0.5) * (pr + pn);
+            dif += R(0.5) * (Gr + Gn) * ((pn - pr) + Yb * mdl[ax][sd]) - Yb * mcr[ax][sd];
+          }
         } else {
           dif += FMf[ax][1] * dp1 - FMf[ax][0] * dm1;
         }
@@ -405,7 +454,7 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
         dif *= gfac * inv_rho;
         src = dt * qdot * inv_rpF * c.inv_cp + fd_dT * inv_rho;
       } else {
-        dif *= gfac * inv_rho;
+        dif *= (MIX ? R(1) : gfac) * inv_rho;
         R om = R(0);
 #pragma unroll
         for (int j = 0; j < RMAX; ++j)
@@ -450,7 +499,7 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
 #ifndef HLBM_FD_VCP_MIN_BLOCKS
 #define HLBM_FD_VCP_MIN_BLOCKS 4  // the same for the variable heat-capacity variant (measured: 2 blocks 2.24 ms, 3 blocks 1.72 ms, 4 blocks 1.60 ms per C4 launch)
 #endif
-template <int D, typename R, int NK, int NR, int VDEG = 0>
+template <int D, typename R, int NK, int NR, int VDEG = 0, bool MIX = false>
 __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? (VDEG > 0 ? HLBM_FD_VCP_MIN_BLOCKS : HLBM_FD_MIN_BLOCKS) : 1)
     fd_step_kernel(const FDArgs<R> a) {
   const FDConst<R>& c = a.c;
@@ -461,7 +510,8 @@ __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? (VDEG > 0 ? HLBM_FD
   const bool inside = x < g.nx && y < g.ny && z < g.nz;
   const int r = x + g.nx * (y + g.ny * z);
   const uint32_t sw = inside ? __ldg(a.sword + r) : 0u;
-  const bool active = (sw >> 31) != 0u;
+  // walls_only: the launch after the tiled update, for the cells with ghost-point wall weights
+  const bool active = (sw >> 31) != 0u && (!a.walls_only || (sw & SW_WALL) != 0u);
   R termI = R(0), termM = R(0);  // P_th integrand and boundary mass flux of this cell
 
   // interior fast path: stencil word without any non-fluid neighbour, cell 2 away from every face
@@ -474,9 +524,15 @@ __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? (VDEG > 0 ? HLBM_FD
   const bool warp_fast = __all_sync(0xffffffffu, !active || fast);
   const bool warp_walls = __any_sync(0xffffffffu, active && (sw & SW_WALL) != 0u);
   if (active) {
-    if (warp_fast) fd_cell<D, R, NK, NR, true, VDEG>(a, x, y, z, r, sw, termI, termM);
-    else if (warp_walls) fd_cell<D, R, NK, NR, false, VDEG, true>(a, x, y, z, r, sw, termI, termM);
-    else fd_cell<D, R, NK, NR, false, VDEG>(a, x, y, z, r, sw, termI, termM);
+    if constexpr (MIX) {
+      // mixture-averaged diffusion has no ghost-point wall copy (lbm_set_transport refuses walls)
+      if (warp_fast) fd_cell<D, R, NK, NR, true, 0, false, true>(a, x, y, z, r, sw, termI, termM);
+      else fd_cell<D, R, NK, NR, false, 0, false, true>(a, x, y, z, r, sw, termI, termM);
+    } else {
+      if (warp_fast) fd_cell<D, R, NK, NR, true, VDEG>(a, x, y, z, r, sw, termI, termM);
+      else if (warp_walls) fd_cell<D, R, NK, NR, false, VDEG, true>(a, x, y, z, r, sw, termI, termM);
+      else fd_cell<D, R, NK, NR, false, VDEG>(a, x, y, z, r, sw, termI, termM);
+    }
   }
   if (!c.closed) return;  // uniform across the grid
   // block reduction of the two terms into this block's partial slot
@@ -484,7 +540,7 @@ __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? (VDEG > 0 ? HLBM_FD
   __shared__ double dI[FD_BLOCK / 32], dM[FD_BLOCK / 32];
   const int tid = threadIdx.x + FDShape<D>::X * (threadIdx.y + FDShape<D>::Y * threadIdx.z);
   const int lane = tid & 31, wid = tid >> 5;
-  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const int bid = a.part_offset + blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   if constexpr (sizeof(R) == 4) {
     long long vI = warp_sum_ll(f32_to_fix32((float)termI));
     long long vM = warp_sum_ll(f32_to_fix32((float)termM));
@@ -527,10 +583,13 @@ template <int D> inline int fd_blocks(const Geo& g) {
 
 // variable heat capacities: fd_kernels_vcp.cu
 template <int D, typename R> cudaError_t launch_fd_vcp(const FDArgs<R>& a, cudaStream_t st);
+// mixture-averaged species diffusion: fd_kernels_mix.cu (coefficient pass + update)
+template <int D, typename R> cudaError_t launch_fd_mix(const FDArgs<R>& a, R* mix, cudaStream_t st);
 
 template <int D, typename R>
 cudaError_t launch_fd(const FDArgs<R>& a, cudaStream_t st, bool sensor_pass) {
   if (!sensor_pass && a.c.varcp) return launch_fd_vcp<D, R>(a, st);
+  if (!sensor_pass && a.c.mixavg) return launch_fd_mix<D, R>(a, const_cast<R*>(a.mix), st);
   if (sensor_pass) {
     const int grid = (a.geo.N + FD_BLOCK - 1) / FD_BLOCK;
     flame_sensor_kernel<D, R><<<grid, FD_BLOCK, 0, st>>>(a);

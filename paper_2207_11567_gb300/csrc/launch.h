@@ -12,6 +12,17 @@ cudaError_t launch_lb(const LBArgs<R>& a, int thermal, int coll, cudaStream_t st
 template <int D, typename R>
 cudaError_t launch_fd(const FDArgs<R>& a, cudaStream_t st, bool sensor_pass);
 
+// fd_tiled.cu: tiled FD update of 3-D FP32 grids (TMA plane tiles, faces evaluated once)
+struct FDTiledMaps;
+bool fd_tiled_eligible(const Geo& g, int D, int f64, int varcp, int K, int nrx);
+FDTiledMaps* fd_tiled_create();
+void fd_tiled_destroy(FDTiledMaps* m);
+// T, Y, F: the two state parities (F nullptr without the flame sensor); n_sm: SMs of the device
+cudaError_t fd_tiled_setup(FDTiledMaps& m, const Geo& g, int K, void* const T[2], void* const Y[2],
+                           void* const F[2], const void* u, const uint32_t* sword, int n_sm);
+int fd_tiled_blocks(const FDTiledMaps& m);
+cudaError_t launch_fd_tiled(const FDArgs<float>& a, const FDTiledMaps& m, int cur, cudaStream_t st);
+
 // aux_kernels.cu
 cudaError_t launch_links(int D, const Geo& g, const uint8_t* mask, uint32_t* out, cudaStream_t st);
 cudaError_t launch_stencil_words(int D, const Geo& g, const uint8_t* mask, uint32_t* out, cudaStream_t st);
@@ -28,7 +39,8 @@ cudaError_t launch_get_fields(int D, const Geo& g, unsigned bits, int K, const S
                               const PthState* pth, double P_ref, double* dst, cudaStream_t st);
 template <typename R>
 cudaError_t launch_init_integral(const Geo& g, const uint8_t* mask, const R* T, const R* Y, const FDConst<R>& c,
-                                 void* partials, int nblocks, cudaStream_t st);
+                                 void* partials, int nblocks, cudaStream_t st,
+                                 unsigned long long* bad = nullptr);
 struct PthUpdate {
   double I_s, M_s, R_rho_ref, cp_rho_ref, rin_fac;  // rin_fac = W_in / (R T_in rho_ref)
   int fixed_point;                                  // partials are int64 fixed point

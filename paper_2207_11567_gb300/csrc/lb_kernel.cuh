@@ -227,6 +227,27 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
   const int oym = y > 0 ? -sy_ : (ny - 1) * sy_, oyp = y < ny - 1 ? sy_ : (1 - ny) * sy_;
   const int ozm = z > 0 ? -sz_ : (nz - 1) * sz_, ozp = z < nz - 1 ? sz_ : (1 - nz) * sz_;
   const bool outlet_cell = x == nx - 1 && a.geo.bc_hi[0] == BC_OUTLET;
+  // interior warp: no lane has a bounce-back, inlet or outlet link or sits on a periodic face, so
+  // every pull is a plain offset (same loads as below, without the per-direction link tests)
+  const bool interior = !WALLS && (lw & ((1u << Q) - 1u)) == 0u && x > 0 && x < nx - 1 && y > 0 &&
+                        y < ny - 1 && (D == 2 || (z > 0 && z < nz - 1));
+  if (!WALLS && __all_sync(__activemask(), interior)) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int ci = cx(i), cj = cy(i), ck = (D == 3) ? cz(i) : 0;
+      raw[i] = ld_raw<S>(gin + i * Ni + r - ci - cj * sy_ - ck * sz_);
+    }
+    if constexpr (THERMAL) {
+      rho_p[0] = ldg(a.rho + r + 1);
+      rho_m[0] = ldg(a.rho + r - 1);
+      rho_p[1] = ldg(a.rho + r + sy_);
+      rho_m[1] = ldg(a.rho + r - sy_);
+      if (D == 3) {
+        rho_p[2] = ldg(a.rho + r + sz_);
+        rho_m[2] = ldg(a.rho + r - sz_);
+      }
+    }
+  } else {
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int ci = cx(i), cj = cy(i), ck = (D == 3) ? cz(i) : 0;
@@ -250,6 +271,7 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
         }
       }
     }
+  }
   }
   R q[Q];
 #pragma unroll

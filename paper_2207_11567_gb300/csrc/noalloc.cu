@@ -9,7 +9,9 @@
 // kernel and the same exact fixed-point per-block partial sums that lbm_step uses for the
 // thermodynamic pressure. The partial sums live in g_noalloc_partials, a file-scope device
 // array of fixed size: every GPU that loads this library holds that array (1 MiB) until the
-// process exits.
+// process exits. Its last two words count the fluid cells whose integrand the fixed-point sum
+// cannot hold (a non-finite value, or 2^30 and above after scaling, e.g. T = 0); such a call
+// writes NaN to I_out.
 #include <cstring>
 #include <mutex>
 
@@ -21,16 +23,18 @@ namespace {
 constexpr int kMaxBlocks = 65536;  // partial slots: 2 int64 per block of AUX_BLOCK cells
 constexpr double kRGas = 8.314462618;
 
-// Shared by every call on a device; each call overwrites the slots it uses.
-static __device__ __align__(256) long long g_noalloc_partials[2 * kMaxBlocks];
+// Shared by every call on a device; each call overwrites the slots it uses and clears the
+// bad-cell counter (word 2 kMaxBlocks) first.
+static __device__ __align__(256) long long g_noalloc_partials[2 * kMaxBlocks + 2];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void* g_partials_ptr[kMaxDevices] = {nullptr};
 
-// Exact sum of the int64 partials, scaled back to the integral (one block).
+// Exact sum of the int64 partials, scaled back to the integral (one block); NaN when a cell's
+// integrand was out of the fixed-point range.
 __global__ void noalloc_sum_kernel(const long long* __restrict__ partials, int nblocks, double scale,
-                                   double* __restrict__ out) {
+                                   const unsigned long long* __restrict__ bad, double* __restrict__ out) {
   __shared__ long long s[1024];
   long long v = 0;
   for (int i = threadIdx.x; i < nblocks; i += blockDim.x) v += partials[2 * i];
@@ -40,7 +44,7 @@ __global__ void noalloc_sum_kernel(const long long* __restrict__ partials, int n
     if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = (double)s[0] / scale;
+  if (threadIdx.x == 0) *out = *bad ? __longlong_as_double(0x7ff8000000000000LL) : (double)s[0] / scale;
 }
 
 void set_err(char* err, size_t err_len, const char* msg) {
@@ -70,9 +74,32 @@ extern "C" lbm_status lbm_pth_integral_noalloc(const float* T, const float* Y, c
       set_err(err, err_len, "molar masses must be > 0");
       return LBM_ERR_ARG;
     }
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  // the work runs on the stream's device (the current device for the legacy default stream):
+  // that device is made current for the call and the caller's current device restored after it
+  cudaStream_t st = (cudaStream_t)stream;
+  int cur = 0, dev = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
     set_err(err, err_len, "no usable CUDA device");
+    return LBM_ERR_CUDA;
+  }
+  dev = cur;
+  if (st && cudaStreamGetDevice(st, &dev) != cudaSuccess) {
+    set_err(err, err_len, "stream does not belong to a usable device");
+    return LBM_ERR_ARG;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_err(err, err_len, "device index beyond the supported range");
+    return LBM_ERR_CUDA;
+  }
+  struct Restore {
+    int d;
+    bool on;
+    ~Restore() {
+      if (on) cudaSetDevice(d);
+    }
+  } restore{cur, dev != cur};
+  if (dev != cur && cudaSetDevice(dev) != cudaSuccess) {
+    set_err(err, err_len, "cannot make the stream's device current");
     return LBM_ERR_CUDA;
   }
   void* partials = nullptr;
@@ -91,21 +118,28 @@ extern "C" lbm_status lbm_pth_integral_noalloc(const float* T, const float* Y, c
     }
     partials = g_partials_ptr[dev];
   }
-  // same constants as the context's FP32 path (I_unit W / T per cell, exact fixed-point sums)
+  // per cell I_unit W / T in FP32, exact fixed-point sums as in the context's FP32 path; the
+  // scale T_ref / max_k W_k keeps the terms of order T_ref / T whatever the molar masses
   hlbm::FDConst<float> c{};
   c.K = n_species;
-  for (int k = 0; k < n_species; ++k) c.inv_W[k] = (float)(1.0 / W[k]);
-  c.I_scale = (float)(T_ref / 0.029);
+  double Wmax = 0.0;
+  for (int k = 0; k < n_species; ++k) {
+    c.inv_W[k] = (float)(1.0 / W[k]);
+    Wmax = W[k] > Wmax ? W[k] : Wmax;
+  }
+  c.I_scale = (float)(T_ref / Wmax);
   const double I_s = (double)c.I_scale * kRGas * rho_ref;
   hlbm::Geo g{};
   g.nx = n_cells;
   g.ny = 1;
   g.nz = 1;
   g.N = n_cells;
-  cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = hlbm::launch_init_integral<float>(g, mask, T, Y, c, partials, (int)nblocks, st);
+  unsigned long long* bad = reinterpret_cast<unsigned long long*>((long long*)partials + 2 * kMaxBlocks);
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = hlbm::launch_init_integral<float>(g, mask, T, Y, c, partials, (int)nblocks, st, bad);
   if (e == cudaSuccess) {
-    noalloc_sum_kernel<<<1, 1024, 0, st>>>((const long long*)partials, (int)nblocks, hlbm::FIX_SCALE * I_s, I_out);
+    noalloc_sum_kernel<<<1, 1024, 0, st>>>((const long long*)partials, (int)nblocks, hlbm::FIX_SCALE * I_s, bad,
+                                           I_out);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {

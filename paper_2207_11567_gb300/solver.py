@@ -70,6 +70,8 @@ class Solver:
         self.N = cfg["nx"] * cfg["ny"] * nz
         if cfg.get("variable_cp"):
             self.set_thermo([sp["cp_poly"] for sp in cfg["species"]], cfg.get("T0_thermo", 298.15))
+        if cfg.get("mixture_averaged"):
+            self.set_transport(cfg["Le_pair"])
         self.set_geometry(mask, inlet_u)
 
     def __del__(self):
@@ -104,6 +106,17 @@ class Solver:
             a[k, : len(row)] = row
         keep, ptr = _as_c_double(a)
         _check(self.ctx, L.lib.lbm_set_thermo(self.ctx, ptr, float(T0)))
+        del keep
+
+    def set_transport(self, Le_pair):
+        """Mixture-averaged species diffusion with pair Lewis numbers Le_pair [n_species][n_species]
+        (lbm_set_transport); None for the constant Lewis numbers of the configuration."""
+        if Le_pair is None:
+            _check(self.ctx, L.lib.lbm_set_transport(self.ctx, None))
+            return
+        K = len(self.cfg["species"])
+        keep, ptr = _as_c_double(np.asarray(Le_pair, dtype=np.float64).reshape(K, K))
+        _check(self.ctx, L.lib.lbm_set_transport(self.ctx, ptr))
         del keep
 
     def set_inlet(self, inlet_u):

@@ -4,7 +4,12 @@ FP64 path: relative L-infinity <= 1e-10 on every field. FP32 path: relative L-in
 <= max(1e-5, 3 x storage floor) per field, where the storage floor is the error of the FP64
 oracle whose state is rounded to FP32 after every step (what FP32 storage alone costs; in
 low-Mach runs the pressure fluctuations are ~1e-2 of the population values, so P_h sits at that
-floor). FP16 storage: relative L2 <= 2e-3 on velocity, temperature and mass fractions."""
+floor), and at most a fixed ceiling per field: 1e-5 on u, T, Y, rho and 5e-5 on P_h, g, Lambda
+for the well-conditioned cases; for the reactive burner, whose FP32 storage floor alone is far
+above 1e-5 (the fractional reaction orders make it ill-conditioned), ceilings at about three times
+the floors measured on GB300, so that a floor that grew would fail. Each FP32 test prints the
+plain errors next to the floors. FP16 storage: relative L2 <= 2e-3 on velocity, temperature and
+mass fractions."""
 import numpy as np
 import pytest
 
@@ -14,6 +19,12 @@ from tests.parity import compare, gpu_run, oracle_run, rel_l2, storage_floor
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-5
+CAP = {"u": 1e-5, "T": 1e-5, "Y": 1e-5, "rho": 1e-5, "P_h": 5e-5, "g": 5e-5, "lam": 5e-5}
+# reactive burner, FP32, storage floors measured on GB300: sensor + closed domain, 30 steps (Y 1.2e-4,
+# Lambda 2.5e-4, the other fields below 1e-5); no sensor, open domain, 200 steps (u 2.5e-4, P_h
+# 1.1e-4, g 2.9e-4, T 8.7e-5, Y 1.4e-3, rho 1.9e-5, Lambda 2.0e-2)
+CAP_SWIRL_30 = dict(CAP, Y=4e-4, lam=8e-4)
+CAP_SWIRL_200 = {"u": 1e-3, "T": 3e-4, "Y": 5e-3, "rho": 1e-4, "P_h": 5e-4, "g": 1e-3, "lam": 6e-2}
 
 
 def _check(errs, tol):
@@ -21,11 +32,13 @@ def _check(errs, tol):
     assert not bad, f"errors above {tol}: {bad} (all: {errs})"
 
 
-def _check32(wl, steps, gpu, st):
+def _check32(wl, steps, gpu, st, cap=CAP):
     errs = compare(wl, gpu, st)
     floor = storage_floor(wl, steps, st)
-    bad = {k: (v, floor[k]) for k, v in errs.items() if not (v <= max(TOL32, 3.0 * floor[k]))}
-    assert not bad, f"FP32 errors above max(1e-5, 3 x floor): {bad} (errors {errs}, floor {floor})"
+    print(f"{wl.name} {steps} steps, FP32 relative L-inf (plain target 1e-5):",
+          {k: f"{v:.2e} {'<=' if v <= TOL32 else '>'} 1e-5, floor {floor[k]:.2e}" for k, v in errs.items()})
+    bad = {k: (v, floor[k], cap[k]) for k, v in errs.items() if not (v <= max(TOL32, 3.0 * floor[k]) and v <= cap[k])}
+    assert not bad, f"FP32 errors above max(1e-5, 3 x floor) or the ceiling: {bad} (errors {errs}, floor {floor})"
 
 
 @pytest.mark.parametrize("coll", ["bgk", "cumulant"])
@@ -37,13 +50,14 @@ def test_box2d_f32(coll):
 
 
 def test_box3d_f32_cumulant_general_rates():
+    """200 steps (the stated horizon): every field within the plain 1e-5 (measured 2.7e-6 at most)."""
     wl = W.generate.box(3, (21, 18, 13), storage="f32", tau=0.65, seed=2, pert=2e-3, U=0.03)
     wl.cfg["omega_hi"] = [1.2, 0.9, 1.1, 1.3]
     wl.cfg["omega_bulk"] = 1.4
     wl.cfg["smag_cs"] = 0.17
-    o, st = oracle_run(wl, 40)
-    gpu = gpu_run(wl, 40)
-    _check32(wl, 40, gpu, st)
+    o, st = oracle_run(wl, 200)
+    gpu = gpu_run(wl, 200)
+    _check32(wl, 200, gpu, st, cap={k: TOL32 for k in CAP})
 
 
 def test_chamber2d_f32_thermal():
@@ -61,8 +75,20 @@ def test_swirl3d_f32_reactive_closed():
     gpu = gpu_run(wl, 30)
     assert np.array_equal(gpu["links"].astype(np.int64), o.links_packed().numpy())
     assert np.array_equal(gpu["stencil_words"].astype(np.int64), o.stencil_words_packed().numpy())
-    _check32(wl, 30, gpu, st)
+    _check32(wl, 30, gpu, st, cap=CAP_SWIRL_30)
     assert abs(gpu["scalars"]["P_th"] - st["P_th"]) / st["P_th"] < 1e-6
+
+
+def test_swirl3d_f32_reactive_200_steps():
+    """The reactive burner (thickening F = 8 without the sensor, open domain) over 200 steps, in the
+    launch configuration of the benchmark (tiled FD update): at the FP32 storage floor, which is far
+    above 1e-5 here (the oracle rounded to FP32 each step moves Y by 1.4e-3 and Lambda by 2e-2)."""
+    wl = W.generate.swirl_3d(40, 24, 24, reactive=True, seed=4, dt=2e-6)
+    wl.cfg["flame_sensor"] = False
+    wl.cfg["closed_domain"] = False
+    o, st = oracle_run(wl, 200)
+    gpu = gpu_run(wl, 200)
+    _check32(wl, 200, gpu, st, cap=CAP_SWIRL_200)
 
 
 def test_flame2d_f64():
@@ -104,5 +130,9 @@ def test_f16_storage_500_steps(case):
     # state is only rounded to FP16 (or even FP32) after every step already moves by ~5e-3 in u
     # and Y, so the bound is that storage floor: FP16 storage adds nothing beyond its rounding
     floor = storage_floor(wl, 500, st, metric=rel_l2, store_round="f16")
-    bad = {k: (errs[k], floor[k]) for k in keys if not errs[k] <= max(2e-3, 1.5 * floor[k])}
-    assert not bad, f"FP16 errors above max(2e-3, 1.5 x FP16 storage floor): {bad}"
+    print("FP16 reactive swirl, 500 steps, relative L2 (plain target 2e-3):",
+          {k: f"{errs[k]:.2e}, FP16 floor {floor[k]:.2e}" for k in keys})
+    # ceilings about twice the floors measured on GB300 (u 4.5e-3, T 1.4e-4, Y 5.9e-3)
+    cap = {"u": 1e-2, "T": 1e-3, "Y": 1.2e-2}
+    bad = {k: (errs[k], floor[k]) for k in keys if not (errs[k] <= max(2e-3, 1.5 * floor[k]) and errs[k] <= cap[k])}
+    assert not bad, f"FP16 errors above max(2e-3, 1.5 x FP16 storage floor) or the ceiling: {bad}"
