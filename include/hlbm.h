@@ -107,7 +107,11 @@ typedef struct {
                          max(Y_fuel,0) max(Y_ox,0) exp(-sensor_Ta / T)                      */
   int sensor_species, sensor_oxidizer;  /* fuel and oxidizer indices                        */
   double sensor_beta, sensor_wref, sensor_Ta; /* -, -, K                                    */
-  int closed_domain;  /* 1: thermodynamic pressure from the global mass constraint           */
+  int closed_domain;  /* 1: the global mass balance is reduced every step (FP64): M += inlet
+                         minus outlet mass flux, I = sum W / (R T rho_ref); without a pressure
+                         outlet P_th = M / I (a confined domain), with an outlet (bc_hi[0] =
+                         LBM_BC_OUTLET) the domain is open to the ambient there and P_th stays at
+                         P_th0 while M is still tracked. 0: P_th = P_th0, nothing reduced      */
   int n_species, n_reactions;
   lbm_species sp[LBM_MAX_SPECIES];
   lbm_reaction rx[LBM_MAX_REACTIONS];

@@ -5,7 +5,11 @@
   1. FD: from (T^n, Y^n, u^n) compute T^{n+1}, Y^{n+1}, and rho^n, Lambda^n at level n.
   2. Thermodynamic pressure (not in the paper; Eq. 3 assumes it constant). Closed domain:
      P^{n+1} = M^{n+1} / I^{n+1}, I = sum_fluid W / (R T rho_ref), M^{n+1} = M^n + inlet mass
-     flux - outlet mass flux (lattice mass per step). Open domain: P constant.
+     flux - outlet mass flux (lattice mass per step). Open domain: P constant. A closed domain
+     with a pressure outlet is open to the ambient through it: P stays at its initial (ambient)
+     value, while M and I are still reduced every step (the mass balance of the domain). Coupling
+     P = M / I to the outlet flux instead drifts: the outflow answers the expansion only after an
+     acoustic delay, P rises and the reactive burner turns non-finite within a few thousand steps.
      Lambda used by the LB gets -(P^{n+1} - P^n) / P^n; the FD energy equation uses the
      increment of the previous step.
   3. LB: pull g* of the previous step, moments with rho^n, source with grad rho^n (central
@@ -119,7 +123,8 @@ class Oracle:
             elif p.closed:
                 M1 = st["M"] + self._mass_flux(st, rho)
                 I1 = self._integral(torch.where(fluid, T1, st["T"]), torch.where(fluid, Y1, st["Y"]))
-                P1 = M1 / I1
+                P1 = st["P_th"] if p.outlet else M1 / I1
+                new["I"] = I1
             else:
                 M1, P1 = st["M"], st["P_th"]
             dP = P1 - st["P_th"]
@@ -210,4 +215,4 @@ def first_step_pressure(cfg, mask, inlet_u, T, Y, u):
     T1, Y1, rho, _ = fdm.fd_update(p, grid, nb, T, Y, u, uin_r, p.P_th0, 0.0)
     M1 = M0 + boundary_mass_flux(p, at_inlet, at_outlet, uin_r, st, rho)
     I1 = pth_integral(p, grid, torch.where(grid.fluid, T1, T), torch.where(grid.fluid, Y1, Y))
-    return M1 / I1
+    return p.P_th0 if p.outlet else M1 / I1

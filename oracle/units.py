@@ -24,6 +24,8 @@ class Params:
         self.rho_ref = cfg.get("rho_ref", 1.0)
         self.P_th0 = cfg.get("P_th0", 101325.0)
         self.closed = bool(cfg.get("closed_domain", False))
+        # a pressure outlet holds the thermodynamic pressure at its ambient (initial) value
+        self.outlet = cfg.get("bc", {}).get("x", ("", ""))[1] == "outlet"
         self.dt = cfg["dt"]
         self.smag_cs = cfg.get("smag_cs", 0.0)
         self.collision = cfg.get("collision", "cumulant")

@@ -502,6 +502,7 @@ lbm_status lbm_init(const lbm_config* cfg, lbm_ctx** out) {
   pu.cp_rho_ref = c.cp * c.rho_ref;
   pu.rin_fac = c.thermal ? ctx->W_in / (R_GAS * c.T_in * c.rho_ref) : 0.0;
   pu.fixed_point = ctx->f64 ? 0 : 1;
+  pu.hold = c.bc_hi[0] == LBM_BC_OUTLET ? 1 : 0;
 
   // device state
   const size_t N = ctx->N;

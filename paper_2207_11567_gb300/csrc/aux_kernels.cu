@@ -289,9 +289,10 @@ __global__ void __launch_bounds__(PTH_THREADS) pth_update_kernel(PthUpdate pu, c
   }
   if (t == 0) {
     const double P_old = pth->P;
-    // set-up: M = P_th0 I0 and nothing moves; step: P^{n+1} = M^{n+1} / I^{n+1}
+    // set-up: M = P_th0 I0 and nothing moves; step: P^{n+1} = M^{n+1} / I^{n+1}, or, with a
+    // pressure outlet (hold), P stays at the ambient value while M keeps the mass balance
     const double M_new = init ? P_old * I : pth->M + mflux;
-    const double P_new = init ? P_old : M_new / I;
+    const double P_new = (init || pu.hold) ? P_old : M_new / I;
     const double dP = P_new - P_old;
     pth->M = M_new;
     pth->P = P_new;

@@ -44,6 +44,7 @@ cudaError_t launch_init_integral(const Geo& g, const uint8_t* mask, const R* T, 
 struct PthUpdate {
   double I_s, M_s, R_rho_ref, cp_rho_ref, rin_fac;  // rin_fac = W_in / (R T_in rho_ref)
   int fixed_point;                                  // partials are int64 fixed point
+  int hold;                                         // pressure outlet: P stays, M is still reduced
 };
 // stage: pth_stage_words() 8-byte words; counter: zero before the first launch (kept zero after)
 int pth_stage_words();

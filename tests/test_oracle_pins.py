@@ -1067,3 +1067,31 @@ def test_trace_species_diffuses_with_the_bath_average_of_its_pair_coefficients()
     mu = p.nu_lat * (900.0 / p.T_ref) ** p.mu_exp
     expect = -(mu / (p.Pr * Le_mix)) / rho.mean() * (2 - 2 * math.cos(k))
     assert abs(mode / expect - 1) < 1e-4, (mode.item(), expect.item())
+
+
+def test_outlet_holds_the_thermodynamic_pressure_and_the_mass_balance_still_closes():
+    """A closed-domain chamber with a pressure outlet (reading of the thermodynamic pressure with
+    an outlet): the domain is open to the ambient through the outlet, so P_th stays at its initial
+    value exactly and the LB sees the FD update's Lambda unchanged (no -dP/P term), while the
+    reduction keeps the domain's mass balance: M after n steps equals M0 plus the sum of the
+    inlet-minus-outlet mass fluxes of the steps, and I is the integral of the current state."""
+    from oracle.step import boundary_mass_flux, pth_integral
+    wl = W.generate.chamber_2d(nx=32, ny=12, inlet=True, dt=5e-7, storage="f64", seed=9, u_init=0.01,
+                               n_rows=1, per_row=1)
+    wl.cfg["closed_domain"] = True
+    o = Oracle(wl.cfg, wl.mask, wl.inlet_u)
+    assert o.p.outlet
+    st = o.init_state(T=wl.T, Y=wl.Y, u=wl.u, P_h=wl.P_h)
+    M = st["M"]
+    for _ in range(6):
+        T0, Y0 = st["T"], st["Y"]
+        rho = o.density(T0, Y0, st["P_th"])
+        M = M + boundary_mass_flux(o.p, o.at_inlet, o.at_outlet, o.uin_r, st, rho)
+        lam_fd = fdm.fd_update(o.p, o.grid, o.nb, T0, Y0, st["u"], o.uin_r, st["P_th"], st["dP_lag"])[3]
+        st = o.step(st)
+        assert st["P_th"] == wl.cfg["P_th0"] and st["dP_lag"] == 0.0
+        assert torch.equal(st["lam"], lam_fd)
+    assert abs(st["M"] - M) <= 1e-12 * abs(M)
+    assert abs(st["I"] - pth_integral(o.p, o.grid, st["T"], st["Y"])) <= 1e-12 * st["I"]
+    # the mass balance moved: the fluxes are not zero on this case
+    assert abs(M - o.init_state(T=wl.T, Y=wl.Y, u=wl.u, P_h=wl.P_h)["M"]) > 1e-8 * abs(M)
