@@ -462,6 +462,8 @@ def main():
                     help="with --only: record N probe cells after every step during the timed steps")
     ap.add_argument("--varcp", action="store_true",
                     help="variable species heat capacities (c_p,k(T) polynomials) in the energy equation")
+    ap.add_argument("--mixavg", action="store_true",
+                    help="mixture-averaged species diffusion (synthetic pair Lewis numbers)")
     ap.add_argument("--curved", action="store_true",
                     help="c3/c4: interpolated bounce-back on the injector cylinders and the exhaust cone")
     ap.add_argument("--horizon", type=int, default=0,
@@ -526,6 +528,15 @@ def main():
             wl = make_plain()
             if wl.cfg.get("thermal"):
                 variable_cp(wl.cfg)
+            return wl
+    if args.mixavg:
+        from workloads.configs import mixture_averaged
+        make_plain2 = make
+
+        def make():
+            wl = make_plain2()
+            if wl.cfg.get("thermal"):
+                mixture_averaged(wl.cfg)
             return wl
     if args.only:
         r = run_variant(make(), args.only, args.steps, args.warmup, torch, profile_steps=2, stats=args.stats,
