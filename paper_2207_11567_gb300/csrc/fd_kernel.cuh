@@ -90,8 +90,19 @@ template <typename R> __device__ __forceinline__ R weno3(R a, R b, R c, R eps) {
   return fdiv<R>(t1 * q0 + R(2) * t0 * q1, t1 + R(2) * t0);
 }
 
-// Reaction rates q_j (mol/(m^3 s)) of one cell. NR > 0: reaction count known at compile time.
-template <int NR, typename R>
+// Y[k] for a run-time species index k, by selects over the KMAX register values (an indexed
+// access would place the array in local memory).
+template <int KMAX, typename R> __device__ __forceinline__ R pick_species(const R* Y, int k) {
+  R v = Y[0];
+#pragma unroll
+  for (int i = 1; i < KMAX; ++i) v = (k == i) ? Y[i] : v;
+  return v;
+}
+
+// Reaction rates q_j (mol/(m^3 s)) of one cell. NR > 0: reaction count known at compile time;
+// NK > 0: species count known (Y then holds NK values in registers). Concentration powers: order 1
+// as is, order 1/2 as a square root, others as x^n.
+template <int NR, typename R, int NK = 0>
 __device__ __forceinline__ void reaction_rates(const FDConst<R>& c, R T, const R* Y, R rho_phys, R* q) {
   const int nr = NR > 0 ? NR : c.nrx;
 #pragma unroll
@@ -109,8 +120,9 @@ __device__ __forceinline__ void reaction_rates(const FDConst<R>& c, R T, const R
       if (m >= c.nord[j]) break;
       const int k = c.ord_k[j][m];
       const R n = c.ord_n[j][m];
-      const R conc = rho_phys * fmax(Y[k], R(0)) * c.inv_W[k];
-      v *= (n == R(1)) ? conc : powr<R>(conc, n);
+      const R yk = NK > 0 ? pick_species<NK, R>(Y, k) : Y[k];
+      const R conc = rho_phys * fmax(yk, R(0)) * c.inv_W[k];
+      v *= (n == R(1)) ? conc : (n == R(0.5) ? sqrt(conc) : powr<R>(conc, n));
     }
     q[j] = v;
   }
@@ -252,7 +264,7 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
     const R rho_phys = rho / c.inv_rho_ref;
     const R inv_rho = R(1) / rho;
     R q[RMAX];
-    reaction_rates<NR, R>(c, Tr, Yr, rho_phys, q);
+    reaction_rates<NR, R, NK>(c, Tr, Yr, rho_phys, q);
     const R Fr = a.Floc ? ldg(a.Floc + r) : c.F;
     const R mur = c.nu_lat * powr<R>(Tr * c.T_ref_inv, c.mu_exp);
     // variable heat capacities: mixture c_p and the heat of each reaction at T_r
