@@ -109,6 +109,12 @@ __global__ void __launch_bounds__(FDA_THREADS) fd_adjoint_kernel(const FDAdjArgs
   __shared__ R part[MAX_SP + 1][PA_N][FDA_CELLS];
   __shared__ R sh_q[MAX_RX][FDA_CELLS];
   __shared__ R sh_mu[5][FDA_CELLS];  // mu(T_r), then mu at the distance-1 points (-x, +x, -y, +y)
+  // inputs of the per-cell reverse of the shared terms, staged by all warps so that the one warp
+  // that runs that dependent chain reads shared memory only: the field sums of the partial
+  // adjoints, the cell's mass fractions and the adjoint of rho^n from the LB step
+  __shared__ R sh_tot[PA_N][FDA_CELLS];
+  __shared__ R sh_Y[MAX_SP][FDA_CELLS];
+  __shared__ R sh_rhob[FDA_CELLS];
   const FDArgs<R>& a = A.f;
   const FDConst<R>& c = a.c;
   const Geo& g = a.geo;
@@ -120,6 +126,20 @@ __global__ void __launch_bounds__(FDA_THREADS) fd_adjoint_kernel(const FDAdjArgs
   const int x = r % g.nx, y = r / g.nx;
   FDStencil2 S;
   fd_stencil2(g, sw, r, x, y, S);
+  // adjoint of rho^n from the LB step: own part and the density-gradient parts of the cells that
+  // hold this cell as their -x / +x / -y / +y neighbour (zero where that cell is solid or mirrored)
+  if (act && fi == (K > 0 ? 1 : 0)) {
+    R rhob = A.rho_own[r];
+    const int xm = x > 0 ? r - 1 : (g.bc_lo[0] == BC_PERIODIC ? r + g.nx - 1 : -1);
+    const int xp = x < g.nx - 1 ? r + 1 : (g.bc_hi[0] == BC_PERIODIC ? r - g.nx + 1 : -1);
+    const int ym = y > 0 ? r - g.nx : (g.bc_lo[1] == BC_PERIODIC ? r + (g.ny - 1) * g.nx : -1);
+    const int yp = y < g.ny - 1 ? r + g.nx : (g.bc_hi[1] == BC_PERIODIC ? r - (g.ny - 1) * g.nx : -1);
+    if (xm >= 0) rhob += A.rho_nb[xm];
+    if (xp >= 0) rhob += A.rho_nb[N + xp];
+    if (ym >= 0) rhob += A.rho_nb[2 * N + ym];
+    if (yp >= 0) rhob += A.rho_nb[3 * N + yp];
+    sh_rhob[tx] = rhob;
+  }
 
   // ------------------------------------------------------------ forward: shared quantities
   R Tr = R(1), W = R(1), rho = R(1), rho_phys = R(1), inv_rho = R(1);
@@ -198,6 +218,7 @@ __global__ void __launch_bounds__(FDA_THREADS) fd_adjoint_kernel(const FDAdjArgs
     const R eps = fi == 0 ? c.eps_T : c.eps_Y;
     const R gfac = c.inv_Pr * (fi == 0 ? R(1) : c.inv_Le[fi - 1]);
     const R pr = phi[r];
+    if (fi > 0) sh_Y[fi - 1][tx] = pr;
     R pm2[2], pm1[2], pp1[2], pp2[2];
     R dif = R(0);
 #pragma unroll
@@ -288,6 +309,14 @@ __global__ void __launch_bounds__(FDA_THREADS) fd_adjoint_kernel(const FDAdjArgs
 #pragma unroll
   for (int p = 0; p < PA_N; ++p) part[fi][p][tx] = pa[p];
   __syncthreads();
+  // field sums of the partial adjoints, spread over the block's warps
+  if (act)
+    for (int p = fi; p < PA_N; p += K + 1) {
+      R v = R(0);
+      for (int f = 0; f <= K; ++f) v += part[f][p][tx];
+      sh_tot[p][tx] = v;
+    }
+  __syncthreads();
   // ---------------------- shared terms, once per cell (thread fi = 0): sums over the fields,
   // reverse of the rate law, rho = P W / (R T), W and mu(T); the center adjoint of each species
   // goes to the field threads through shared memory
@@ -295,11 +324,7 @@ __global__ void __launch_bounds__(FDA_THREADS) fd_adjoint_kernel(const FDAdjArgs
   if (act && fi == 0) {
     R tot[PA_N];
 #pragma unroll
-    for (int p = 0; p < PA_N; ++p) {
-      R v = R(0);
-      for (int f = 0; f <= K; ++f) v += part[f][p][tx];
-      tot[p] = v;
-    }
+    for (int p = 0; p < PA_N; ++p) tot[p] = sh_tot[p][tx];
     R Trb = tot[PA_TR], Wb = tot[PA_W];
     R rho_physb = -tot[PA_INVRPF] * inv_rpF / rho_phys;
     for (int k = 0; k < K; ++k) sh_add[k][tx] = R(0);
@@ -312,26 +337,15 @@ __global__ void __launch_bounds__(FDA_THREADS) fd_adjoint_kernel(const FDAdjArgs
       for (int m = 0; m < MAX_ORD; ++m) {
         if (m >= c.nord[j]) break;
         const int k = c.ord_k[j][m];
-        const R yk = a.Y[(size_t)k * N + r];
+        const R yk = sh_Y[k][tx];
         if (yk > R(0)) {
           rho_physb += qq * c.ord_n[j][m] / rho_phys;
           sh_add[k][tx] += qq * c.ord_n[j][m] / yk;
         }
       }
     }
-    // adjoint of rho^n: own LB part, density-gradient parts of the cells holding it as their
-    // -x / +x / -y / +y neighbour (zero where that cell is solid or mirrored it), this update
-    R rhob = A.rho_own[r];
-    {
-      const int xm = x > 0 ? r - 1 : (g.bc_lo[0] == BC_PERIODIC ? r + g.nx - 1 : -1);
-      const int xp = x < g.nx - 1 ? r + 1 : (g.bc_hi[0] == BC_PERIODIC ? r - g.nx + 1 : -1);
-      const int ym = y > 0 ? r - g.nx : (g.bc_lo[1] == BC_PERIODIC ? r + (g.ny - 1) * g.nx : -1);
-      const int yp = y < g.ny - 1 ? r + g.nx : (g.bc_hi[1] == BC_PERIODIC ? r - (g.ny - 1) * g.nx : -1);
-      if (xm >= 0) rhob += A.rho_nb[xm];
-      if (xp >= 0) rhob += A.rho_nb[N + xp];
-      if (ym >= 0) rhob += A.rho_nb[2 * N + ym];
-      if (yp >= 0) rhob += A.rho_nb[3 * N + yp];
-    }
+    // adjoint of rho^n: from the LB step (staged above) and this update
+    R rhob = sh_rhob[tx];
     rhob += rho_physb / c.inv_rho_ref;
     rhob -= tot[PA_INVRHO] * inv_rho * inv_rho;
     Wb += rhob * fdr / Tr;
