@@ -1,5 +1,6 @@
 // Adjoint step and objective of the 2-D hybrid step (not in the paper): the exact discrete
-// reverse of one lbm_step (FD update -> LB stream-collide), and the fuel-consumption objective
+// reverse of one lbm_step (FD update -> LB stream-collide; the LB adjoint then the FD adjoint,
+// which leaves the T and Y adjoints in slot form), and the fuel-consumption objective
 // J = sum over fluid cells of the fuel consumption rate -omega_F with its gradient.
 #include "adjoint_fd.cuh"
 #include "adjoint_lb.cuh"
@@ -135,20 +136,24 @@ cudaError_t launch_adjoint_step2d(const AdjBuffers<R>& b, const LBArgs<R>& lbf, 
   if (e != cudaSuccess) return e;
   R* out_u = b.out + 9 * (size_t)N;
   if (!thermal) return cudaMemcpyAsync(out_u, b.u_lb, 2 * (size_t)N * sizeof(R), cudaMemcpyDeviceToDevice, st);
-  const int fb = (N + FDA_CELLS - 1) / FDA_CELLS;
-  const dim3 fblock(FDA_CELLS, K + 1);
   FDAdjArgs<R> fa{};
   fa.f = fdf;
-  fa.Tbar_out = b.in + 11 * (size_t)N;
-  fa.Ybar_out = b.in + 12 * (size_t)N;
+  if (!b.slots_in) {
+    fa.Tbar_out = b.in + 11 * (size_t)N;
+    fa.Ybar_out = b.in + 12 * (size_t)N;
+  }
+  fa.slots_in = b.slots_in;
   fa.rho_own = b.rho_own;
   fa.rho_nb = b.rho_nb;
   fa.lam_bar = b.lam_bar;
+  fa.T_lb = b.T_lb;
+  fa.u_lb = b.u_lb;
   fa.slots = b.slots;
-  fa.u_bar = b.u_fd;
-  fd_adjoint_kernel<R><<<fb, fblock, 0, st>>>(fa);
-  fd_adjoint_gather<R><<<fb, fblock, 0, st>>>(g, fdf.sword, K, b.slots, b.T_lb, b.u_fd, b.u_lb,
-                                                 b.out + 11 * (size_t)N, b.out + 12 * (size_t)N, out_u);
+  fa.u_out = out_u;
+  const int fb = (N + FDA_BLOCK - 1) / FDA_BLOCK;
+  if (K == 6) fd_adjoint_kernel<R, 6><<<fb, FDA_BLOCK, 0, st>>>(fa);
+  else if (K == 4) fd_adjoint_kernel<R, 4><<<fb, FDA_BLOCK, 0, st>>>(fa);
+  else fd_adjoint_kernel<R, 0><<<fb, FDA_BLOCK, 0, st>>>(fa);
   return cudaGetLastError();
 }
 
@@ -166,6 +171,13 @@ template <typename R> cudaError_t launch_zero_solid_pops(const Geo& g, const uin
 }
 
 template <typename R>
+cudaError_t launch_adjoint_gather(const Geo& g, const uint32_t* sword, int K, const R* slots, R* Tbar, R* Ybar,
+                                  cudaStream_t st) {
+  fd_adjoint_gather<R><<<(g.N + FDA_BLOCK - 1) / FDA_BLOCK, FDA_BLOCK, 0, st>>>(g, sword, K, slots, Tbar, Ybar);
+  return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_fuel_objective(const FDArgs<R>& fdf, int fuel, R* Tbar, R* Ybar, double* partials, int nblocks,
                                   cudaStream_t st) {
   fuel_objective_kernel<R><<<nblocks, FD_BLOCK, 0, st>>>(fdf, fuel, Tbar, Ybar, partials);
@@ -176,6 +188,10 @@ template cudaError_t launch_adjoint_step2d<float>(const AdjBuffers<float>&, cons
                                                   bool, cudaStream_t);
 template cudaError_t launch_adjoint_step2d<double>(const AdjBuffers<double>&, const LBArgs<double>&,
                                                    const FDArgs<double>&, bool, cudaStream_t);
+template cudaError_t launch_adjoint_gather<float>(const Geo&, const uint32_t*, int, const float*, float*, float*,
+                                                  cudaStream_t);
+template cudaError_t launch_adjoint_gather<double>(const Geo&, const uint32_t*, int, const double*, double*, double*,
+                                                   cudaStream_t);
 template cudaError_t launch_zero_solid_pops<float>(const Geo&, const uint32_t*, float*, cudaStream_t);
 template cudaError_t launch_zero_solid_pops<double>(const Geo&, const uint32_t*, double*, cudaStream_t);
 template cudaError_t launch_initial_T_adjoint<float>(const FDArgs<float>&, const float*, float*, cudaStream_t);

@@ -3,11 +3,13 @@
 // adjoint step is not in the paper; it is the exact transpose of the discrete update written by
 // hand. Upwind choices and the max(Y, 0) of the rate law are held fixed (their derivative is 0).
 //
-// Each fluid cell recomputes its forward update, reverses it, and writes the adjoint of every
-// stencil value it read into one of 9 slots per field (center, distance-1 and distance-2 points
-// on each side of each axis); a ghost value's adjoint is folded onto the cell it copies (inlet
-// values are constants). fd_adjoint_gather then sums, for each cell, the slots of the cells
-// whose stencils contain it.
+// One thread per fluid cell recomputes its forward update and reverses it, field after field,
+// writing the adjoint of every stencil value it read into one of 9 slots per field (center,
+// distance-1 and distance-2 points on each side of each axis); a ghost value's adjoint is folded
+// onto the cell it copies (inlet values are constants). The adjoint of a cell's T and Y_k is the
+// sum of its own center slot and the slots of the cells whose stencils contain it: the next
+// reverse step forms that sum for its own cell as it starts (slot form, double-buffered), and
+// fd_adjoint_gather forms it for every cell where a reverse sweep ends.
 #pragma once
 #include "common.cuh"
 #include "fd_kernel.cuh"
@@ -16,13 +18,16 @@ namespace hlbm {
 
 template <typename R> struct FDAdjArgs {
   FDArgs<R> f;           // forward arguments of state n (T, Y, u, stencil words, constants)
-  const R* Tbar_out;     // [N] adjoint of T^{n+1}
-  const R* Ybar_out;     // [K][N] adjoint of Y^{n+1}
+  const R* Tbar_out;     // [N] adjoint of T^{n+1}, or null: slot form in slots_in
+  const R* Ybar_out;     // [K][N] adjoint of Y^{n+1} (with Tbar_out)
+  const R* slots_in;     // [9][1+K][N] slot form of the adjoint of T^{n+1}, Y^{n+1}
   const R* rho_own;      // [N] adjoint of rho^n used by the cell's own LB update
   const R* rho_nb;       // [4][N] adjoint of the +x, -x, +y, -y neighbour rho in a cell's LB update
   const R* lam_bar;      // [N] adjoint of Lambda^n (from the LB adjoint)
-  R* slots;              // [9][1+K][N] stencil-value adjoints
-  R* u_bar;              // [2][N] adjoint of u^n through the advection (center only)
+  const R* T_lb;         // [N] adjoint of T^n through the LB step's viscosity law
+  const R* u_lb;         // [2][N] adjoint of u^n through the LB step's outlet rule
+  R* slots;              // [9][1+K][N] stencil-value adjoints of this step (slot form of T^n, Y^n)
+  R* u_out;              // [2][N] adjoint of u^n: advection part plus u_lb (0 on solid cells)
 };
 
 // reverse of one WENO3 face b + (tbc dab + 2 tab dbc) / (2 (tbc + 2 tab)), t = (d^2 + eps)^2
@@ -50,11 +55,8 @@ template <typename R> __device__ __forceinline__ R weno_face(R b, R dab, R dbc, 
 __device__ __forceinline__ int slot1(int ax, int sd) { return 1 + 2 * (2 * ax + sd); }
 __device__ __forceinline__ int slot2(int ax, int sd) { return 2 + 2 * (2 * ax + sd); }
 
-// Thread layout of the adjoint kernels: blockDim = (FDA_CELLS, K + 1), x the cell within the
-// block, y the field (0: T, k + 1: Y_k), so that a cell's fields are reversed in parallel.
-constexpr int FDA_CELLS = 32;
-constexpr int FDA_THREADS = FDA_CELLS * (MAX_SP + 1);
-// per-field partial adjoints of the quantities the fields share, summed over the fields
+constexpr int FDA_BLOCK = 64;
+// partial adjoints of the quantities the fields share, summed over the fields
 enum { PA_INVRHO = 0, PA_INVRPF, PA_QDOT, PA_TR, PA_W, PA_FM, PA_UR = PA_FM + 4, PA_Q = PA_UR + 2,
        PA_N = PA_Q + MAX_RX };
 
@@ -85,140 +87,154 @@ __device__ __forceinline__ void fd_stencil2(const Geo& g, uint32_t sw, int r, in
     }
 }
 
-// Rate q_j of one cell, the same arithmetic as reaction_rates of the forward kernel.
-template <typename R>
-__device__ __forceinline__ R rate_of(const FDConst<R>& c, int j, R T, const R* __restrict__ Y, size_t N, int r,
-                                     R rho_phys) {
-  R v;
-  if constexpr (sizeof(R) == 4) v = c.A[j] * arrhenius(c.ER_hi[j], c.ER_lo[j], T);
-  else v = c.A[j] * exp(-c.ER_hi[j] / T);
-  if (c.beta[j] != R(0)) v *= powr<R>(T, c.beta[j]);
+
+// Cells whose stencil point (axis, side, distance) is the fluid cell s: src[2 (2 ax + sd) + dist - 1]
+// is that cell, or -1 where it is not fluid or its point there is a ghost. Its slot 1 + t holds the
+// adjoint of s read through that point.
+__device__ __forceinline__ void slot_sources(const Geo& g, const uint32_t* __restrict__ sword, int s, int x, int y,
+                                             int src[8]) {
+  const int pos[2] = {x, y}, dims[2] = {g.nx, g.ny}, strides[2] = {1, g.nx};
 #pragma unroll
-  for (int m = 0; m < MAX_ORD; ++m) {
-    if (m >= c.nord[j]) break;
-    const int k = c.ord_k[j][m];
-    const R n = c.ord_n[j][m];
-    const R conc = rho_phys * fmax(Y[(size_t)k * N + r], R(0)) * c.inv_W[k];
-    v *= (n == R(1)) ? conc : powr<R>(conc, n);
-  }
+  for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      const int sg = sd ? 1 : -1;
+      const bool per = g.bc_lo[ax] == BC_PERIODIC;
+#pragma unroll
+      for (int dist = 1; dist <= 2; ++dist) {
+        int qd = pos[ax] - dist * sg;
+        bool ok = true;
+        if (qd < 0 || qd >= dims[ax]) {
+          if (per) qd = ((qd % dims[ax]) + dims[ax]) % dims[ax];
+          else ok = false;
+        }
+        int rc = -1;
+        if (ok) {
+          const int cand = s + (qd - pos[ax]) * strides[ax];
+          const uint32_t w = __ldg(sword + cand);
+          if ((w >> 31) && ((w >> (4 * (2 * ax + sd) + 2 * (dist - 1))) & 3u) == 0u) rc = cand;
+        }
+        src[2 * (2 * ax + sd) + dist - 1] = rc;
+      }
+    }
+}
+
+// Sum of one field's slots for the fluid cell s: its own center slot, then slot 1 + t of src[t].
+template <typename R>
+__device__ __forceinline__ R slot_sum(const R* __restrict__ sl, size_t fs, int s, const int src[8]) {
+  R v = sl[s];
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+    if (src[t] >= 0) v += sl[(size_t)(1 + t) * fs + src[t]];
   return v;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(FDA_THREADS) fd_adjoint_kernel(const FDAdjArgs<R> A) {
-  __shared__ R part[MAX_SP + 1][PA_N][FDA_CELLS];
-  __shared__ R sh_q[MAX_RX][FDA_CELLS];
-  __shared__ R sh_mu[5][FDA_CELLS];  // mu(T_r), then mu at the distance-1 points (-x, +x, -y, +y)
-  // inputs of the per-cell reverse of the shared terms, staged by all warps so that the one warp
-  // that runs that dependent chain reads shared memory only: the field sums of the partial
-  // adjoints, the cell's mass fractions and the adjoint of rho^n from the LB step
-  __shared__ R sh_tot[PA_N][FDA_CELLS];
-  __shared__ R sh_Y[MAX_SP][FDA_CELLS];
-  __shared__ R sh_rhob[FDA_CELLS];
+// One thread per cell. NK > 0: that many species (fields unrolled); NK = 0: c.K <= MAX_SP.
+template <typename R, int NK>
+__global__ void __launch_bounds__(FDA_BLOCK, sizeof(R) == 4 ? 7 : 1) fd_adjoint_kernel(const FDAdjArgs<R> A) {
+  constexpr int NF = (NK > 0 ? NK : MAX_SP) + 1;  // fields held in registers
   const FDArgs<R>& a = A.f;
   const FDConst<R>& c = a.c;
   const Geo& g = a.geo;
-  const int N = g.N, K = c.K;
-  const int tx = threadIdx.x, fi = threadIdx.y;
-  const int r = blockIdx.x * FDA_CELLS + tx;
-  const uint32_t sw = r < N ? __ldg(a.sword + r) : 0u;
-  const bool act = (sw >> 31) != 0u;  // every thread reaches the barriers below
+  const int N = g.N, K = NK > 0 ? NK : c.K;
+  const int r = blockIdx.x * FDA_BLOCK + threadIdx.x;
+  if (r >= N) return;
+  const uint32_t sw = __ldg(a.sword + r);
+  if (!(sw >> 31)) {
+    A.u_out[r] = R(0);
+    A.u_out[N + r] = R(0);
+    return;
+  }
   const int x = r % g.nx, y = r / g.nx;
   FDStencil2 S;
   fd_stencil2(g, sw, r, x, y, S);
+  const size_t fs = (size_t)(K + 1) * N;  // stride between slots
+
+  // adjoints of T^{n+1}, Y^{n+1} at this cell
+  R ob[NF];
+  if (A.Tbar_out) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      if (f <= K) ob[f] = f == 0 ? A.Tbar_out[r] : A.Ybar_out[(size_t)(f - 1) * N + r];
+  } else {
+    int src[8];
+    slot_sources(g, a.sword, r, x, y, src);
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      if (f <= K) ob[f] = slot_sum<R>(A.slots_in + (size_t)f * N, fs, r, src);
+  }
   // adjoint of rho^n from the LB step: own part and the density-gradient parts of the cells that
   // hold this cell as their -x / +x / -y / +y neighbour (zero where that cell is solid or mirrored)
-  if (act && fi == (K > 0 ? 1 : 0)) {
-    R rhob = A.rho_own[r];
+  R rhob_lb = A.rho_own[r];
+  {
     const int xm = x > 0 ? r - 1 : (g.bc_lo[0] == BC_PERIODIC ? r + g.nx - 1 : -1);
     const int xp = x < g.nx - 1 ? r + 1 : (g.bc_hi[0] == BC_PERIODIC ? r - g.nx + 1 : -1);
     const int ym = y > 0 ? r - g.nx : (g.bc_lo[1] == BC_PERIODIC ? r + (g.ny - 1) * g.nx : -1);
     const int yp = y < g.ny - 1 ? r + g.nx : (g.bc_hi[1] == BC_PERIODIC ? r - (g.ny - 1) * g.nx : -1);
-    if (xm >= 0) rhob += A.rho_nb[xm];
-    if (xp >= 0) rhob += A.rho_nb[N + xp];
-    if (ym >= 0) rhob += A.rho_nb[2 * N + ym];
-    if (yp >= 0) rhob += A.rho_nb[3 * N + yp];
-    sh_rhob[tx] = rhob;
+    if (xm >= 0) rhob_lb += A.rho_nb[xm];
+    if (xp >= 0) rhob_lb += A.rho_nb[N + xp];
+    if (ym >= 0) rhob_lb += A.rho_nb[2 * N + ym];
+    if (yp >= 0) rhob_lb += A.rho_nb[3 * N + yp];
   }
+  const R lamb = A.lam_bar[r];
 
   // ------------------------------------------------------------ forward: shared quantities
-  R Tr = R(1), W = R(1), rho = R(1), rho_phys = R(1), inv_rho = R(1);
   const R F = c.F;
   const R fdr = sizeof(R) == 4 ? (R)a.pth->fd_rho : (R)a.pth->fd_rho_d;
-  R Tn[2][2];
-  if (act) {
-    Tr = a.T[r];
-    R sW = R(0);
-    for (int k = 0; k < K; ++k) sW += a.Y[(size_t)k * N + r] * c.inv_W[k];
-    W = R(1) / sW;
-    rho = fdr * W / Tr;
-    rho_phys = rho / c.inv_rho_ref;
-    inv_rho = R(1) / rho;
+  const R Tr = a.T[r];
+  R Y[MAX_SP];
+  R sW = R(0);
 #pragma unroll
-    for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-        const int kk = S.k1[ax][sd];
-        Tn[ax][sd] = kk == NB_FLUID ? a.T[S.i1[ax][sd]] : (kk == NB_INLET ? c.T_in : Tr);
-      }
-    // transcendental work shared out over the cell's threads: task 0 the rates, task 1 mu(T_r),
-    // tasks 2..5 mu at the distance-1 points
-    for (int t = fi; t < 6; t += K + 1) {
-      if (t == 0) {
-#pragma unroll
-        for (int j = 0; j < MAX_RX; ++j)
-          if (j < c.nrx) sh_q[j][tx] = rate_of<R>(c, j, Tr, a.Y, N, r, rho_phys);
-      } else {
-        const R Tt = t == 1 ? Tr : Tn[(t - 2) >> 1][(t - 2) & 1];
-        sh_mu[t - 1][tx] = c.nu_lat * powr<R>(Tt * c.T_ref_inv, c.mu_exp);
-      }
-    }
+  for (int k = 0; k < MAX_SP; ++k) {
+    Y[k] = (k < K) ? a.Y[(size_t)k * N + r] : R(0);
+    if (k < K) sW += Y[k] * c.inv_W[k];
   }
-  __syncthreads();
-  R q[MAX_RX], mun[2][2], FMf[2][2], uf[2][2], ur[2] = {R(0), R(0)};
-  R mur = R(0), inv_rpF = R(0), qdot = R(0);
-  if (act) {
+  const R W = R(1) / sW;
+  const R rho = fdr * W / Tr;
+  const R rho_phys = rho / c.inv_rho_ref;
+  const R inv_rho = R(1) / rho;
+  R Tn[2][2], mun[2][2], FMf[2][2], uf[2][2];
+  const R ur[2] = {a.u[r], a.u[N + r]};
+  const R mur = c.nu_lat * powr<R>(Tr * c.T_ref_inv, c.mu_exp);
 #pragma unroll
-    for (int j = 0; j < MAX_RX; ++j) {
-      q[j] = j < c.nrx ? sh_q[j][tx] : R(0);
-      qdot += c.heat[j] * q[j];
+  for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      const int kk = S.k1[ax][sd], j = S.i1[ax][sd];
+      Tn[ax][sd] = kk == NB_FLUID ? a.T[j] : (kk == NB_INLET ? c.T_in : Tr);
+      mun[ax][sd] = c.nu_lat * powr<R>(Tn[ax][sd] * c.T_ref_inv, c.mu_exp);
+      FMf[ax][sd] = R(0.5) * (F * mur + F * mun[ax][sd]);
+      R un;
+      if (kk == NB_FLUID) un = a.u[ax * N + j];
+      else if (kk == NB_INLET) un = a.inlet_u[ax * g.ny + y];
+      else if (kk == NB_OUTLET) un = ur[ax];
+      else un = R(0);
+      uf[ax][sd] = R(0.5) * (ur[ax] + un);
     }
-    mur = sh_mu[0][tx];
-    ur[0] = a.u[r];
-    ur[1] = a.u[N + r];
+  // rates q_j: the forward kernel's arithmetic
+  R q[MAX_RX], qdot = R(0);
 #pragma unroll
-    for (int ax = 0; ax < 2; ++ax)
+  for (int j = 0; j < MAX_RX; ++j) q[j] = R(0);
+  reaction_rates<0, R, MAX_SP>(c, Tr, Y, rho_phys, q);
 #pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-        const int kk = S.k1[ax][sd], j = S.i1[ax][sd];
-        mun[ax][sd] = sh_mu[1 + 2 * ax + sd][tx];
-        FMf[ax][sd] = R(0.5) * (F * mur + F * mun[ax][sd]);
-        R un;
-        if (kk == NB_FLUID) un = a.u[ax * N + j];
-        else if (kk == NB_INLET) un = a.inlet_u[ax * g.ny + y];
-        else if (kk == NB_OUTLET) un = ur[ax];
-        else un = R(0);
-        uf[ax][sd] = R(0.5) * (ur[ax] + un);
-      }
-    inv_rpF = R(1) / (rho_phys * F);
-  }
+  for (int j = 0; j < MAX_RX; ++j) qdot += c.heat[j] * q[j];
+  const R inv_rpF = R(1) / (rho_phys * F);
   const R dt = c.dt_phys;
 
-  // ------------------------------------------------------------- this thread's field
-  // pointb: adjoints of the 9 stencil values (slot order), constant indices only
-  R pointb[9];
+  // ------------------------------------------------------------- field after field
+  R tot[PA_N];
 #pragma unroll
-  for (int p = 0; p < 9; ++p) pointb[p] = R(0);
-  R pa[PA_N];
+  for (int p = 0; p < PA_N; ++p) tot[p] = R(0);
+  R c0[NF];     // center slot of each field (before the shared terms)
+  R pT[9];      // slots of T (the viscosity law adds to its distance-1 points below)
 #pragma unroll
-  for (int p = 0; p < PA_N; ++p) pa[p] = R(0);
-  if (act) {
-    const R* phi = fi == 0 ? a.T : a.Y + (size_t)(fi - 1) * N;
-    const R phin = fi == 0 ? c.T_in : c.Y_in[fi - 1];
-    const R eps = fi == 0 ? c.eps_T : c.eps_Y;
-    const R gfac = c.inv_Pr * (fi == 0 ? R(1) : c.inv_Le[fi - 1]);
-    const R pr = phi[r];
-    if (fi > 0) sh_Y[fi - 1][tx] = pr;
+  for (int f = 0; f < NF; ++f) {
+    if (f > K) break;
+    const R* phi = f == 0 ? a.T : a.Y + (size_t)(f - 1) * N;
+    const R phin = f == 0 ? c.T_in : c.Y_in[f - 1];
+    const R eps = f == 0 ? c.eps_T : c.eps_Y;
+    const R gfac = c.inv_Pr * (f == 0 ? R(1) : c.inv_Le[f - 1]);
+    const R pr = f == 0 ? Tr : Y[f - 1];
     R pm2[2], pm1[2], pp1[2], pp2[2];
     R dif = R(0);
 #pragma unroll
@@ -230,34 +246,36 @@ __global__ void __launch_bounds__(FDA_THREADS) fd_adjoint_kernel(const FDAdjArgs
       dif += FMf[ax][1] * (pp1[ax] - pr) - FMf[ax][0] * (pr - pm1[ax]);
     }
     R om = R(0), src;
-    if (fi == 0) {
+    if (f == 0) {
       src = dt * qdot * inv_rpF * c.inv_cp;
     } else {
 #pragma unroll
-      for (int j = 0; j < MAX_RX; ++j) om += c.nu[j][fi - 1] * q[j];
-      src = dt * c.W[fi - 1] * om * inv_rpF;
+      for (int j = 0; j < MAX_RX; ++j) om += c.nu[j][f - 1] * q[j];
+      src = dt * c.W[f - 1] * om * inv_rpF;
     }
     const R NA = gfac * inv_rho * dif + src;
     // reverse. Lambda = NA_T / T + sum_k W / W_k NA_k; out = phi - adv + NA
-    const R lamb = A.lam_bar[r];
-    const R outb = fi == 0 ? A.Tbar_out[r] : A.Ybar_out[(size_t)(fi - 1) * N + r];
+    const R outb = ob[f];
     R NAb;
-    if (fi == 0) {
-      pa[PA_TR] = -lamb * NA / (Tr * Tr);
+    if (f == 0) {
+      tot[PA_TR] += -lamb * NA / (Tr * Tr);
       NAb = outb + lamb / Tr;
     } else {
-      pa[PA_W] = lamb * c.inv_W[fi - 1] * NA;
-      NAb = outb + lamb * W * c.inv_W[fi - 1];
+      tot[PA_W] += lamb * c.inv_W[f - 1] * NA;
+      NAb = outb + lamb * W * c.inv_W[f - 1];
     }
+    R pointb[9];
+#pragma unroll
+    for (int p = 1; p < 9; ++p) pointb[p] = R(0);
     pointb[0] = outb;
-    pa[PA_INVRHO] = NAb * gfac * dif;
+    tot[PA_INVRHO] += NAb * gfac * dif;
     const R gi = NAb * gfac * inv_rho;
 #pragma unroll
     for (int ax = 0; ax < 2; ++ax) {
       const R m2 = pm2[ax], m1 = pm1[ax], p1 = pp1[ax], p2 = pp2[ax];
       R m2b = R(0), m1b = R(0), p1b = R(0), p2b = R(0), prb = R(0);
-      pa[PA_FM + 2 * ax + 1] += gi * (p1 - pr);
-      pa[PA_FM + 2 * ax] -= gi * (pr - m1);
+      tot[PA_FM + 2 * ax + 1] += gi * (p1 - pr);
+      tot[PA_FM + 2 * ax] -= gi * (pr - m1);
       p1b += gi * FMf[ax][1];
       prb -= gi * (FMf[ax][1] + FMf[ax][0]);
       m1b += gi * FMf[ax][0];
@@ -266,7 +284,7 @@ __global__ void __launch_bounds__(FDA_THREADS) fd_adjoint_kernel(const FDAdjArgs
       const R fp = up ? weno_face<R>(pr, dm1, dp1, eps) : weno_face<R>(p1, -dp2, -dp1, eps);
       const R fm = um ? weno_face<R>(m1, dm2, dm1, eps) : weno_face<R>(pr, -dp1, -dm1, eps);
       const R advb = -outb;
-      pa[PA_UR + ax] += advb * (fp - fm);
+      tot[PA_UR + ax] += advb * (fp - fm);
       const R fpb = advb * ur[ax], fmb = -advb * ur[ax];
       R bb, dab, dbc;
       if (up) {
@@ -296,157 +314,105 @@ __global__ void __launch_bounds__(FDA_THREADS) fd_adjoint_kernel(const FDAdjArgs
         if (kk2 == 0) pointb[slot2(ax, sd)] += v2;
       }
     }
-    if (fi == 0) {
-      pa[PA_QDOT] = NAb * dt * inv_rpF * c.inv_cp;
-      pa[PA_INVRPF] = NAb * dt * qdot * c.inv_cp;
+    if (f == 0) {
+      tot[PA_QDOT] += NAb * dt * inv_rpF * c.inv_cp;
+      tot[PA_INVRPF] += NAb * dt * qdot * c.inv_cp;
     } else {
-      const R omb = NAb * dt * c.W[fi - 1] * inv_rpF;
-      pa[PA_INVRPF] = NAb * dt * c.W[fi - 1] * om;
+      const R omb = NAb * dt * c.W[f - 1] * inv_rpF;
+      tot[PA_INVRPF] += NAb * dt * c.W[f - 1] * om;
 #pragma unroll
-      for (int j = 0; j < MAX_RX; ++j) pa[PA_Q + j] = c.nu[j][fi - 1] * omb;
+      for (int j = 0; j < MAX_RX; ++j) tot[PA_Q + j] += c.nu[j][f - 1] * omb;
+    }
+    c0[f] = pointb[0];
+    if (f == 0) {
+#pragma unroll
+      for (int p = 1; p < 9; ++p) pT[p] = pointb[p];
+    } else {
+      R* out = A.slots + (size_t)f * N + r;
+#pragma unroll
+      for (int p = 1; p < 9; ++p) out[(size_t)p * fs] = pointb[p];
     }
   }
+
+  // ---------------------- shared terms: reverse of the rate law, rho = P W / (R T), W and mu(T)
+  R Trb = tot[PA_TR], Wb = tot[PA_W];
+  R rho_physb = -tot[PA_INVRPF] * inv_rpF / rho_phys;
+  R add[MAX_SP];  // center adjoint of each species from the shared terms
 #pragma unroll
-  for (int p = 0; p < PA_N; ++p) part[fi][p][tx] = pa[p];
-  __syncthreads();
-  // field sums of the partial adjoints, spread over the block's warps
-  if (act)
-    for (int p = fi; p < PA_N; p += K + 1) {
-      R v = R(0);
-      for (int f = 0; f <= K; ++f) v += part[f][p][tx];
-      sh_tot[p][tx] = v;
-    }
-  __syncthreads();
-  // ---------------------- shared terms, once per cell (thread fi = 0): sums over the fields,
-  // reverse of the rate law, rho = P W / (R T), W and mu(T); the center adjoint of each species
-  // goes to the field threads through shared memory
-  __shared__ R sh_add[MAX_SP][FDA_CELLS];
-  if (act && fi == 0) {
-    R tot[PA_N];
+  for (int k = 0; k < MAX_SP; ++k) add[k] = R(0);
 #pragma unroll
-    for (int p = 0; p < PA_N; ++p) tot[p] = sh_tot[p][tx];
-    R Trb = tot[PA_TR], Wb = tot[PA_W];
-    R rho_physb = -tot[PA_INVRPF] * inv_rpF / rho_phys;
-    for (int k = 0; k < K; ++k) sh_add[k][tx] = R(0);
+  for (int j = 0; j < MAX_RX; ++j) {
+    if (j >= c.nrx) break;
+    const R qq = q[j] * (tot[PA_Q + j] + c.heat[j] * tot[PA_QDOT]);
+    Trb += qq * ((c.ER_hi[j] + c.ER_lo[j]) / (Tr * Tr) + c.beta[j] / Tr);
 #pragma unroll
-    for (int j = 0; j < MAX_RX; ++j) {
-      if (j >= c.nrx) break;
-      const R qq = q[j] * (tot[PA_Q + j] + c.heat[j] * tot[PA_QDOT]);
-      Trb += qq * ((c.ER_hi[j] + c.ER_lo[j]) / (Tr * Tr) + c.beta[j] / Tr);
+    for (int m = 0; m < MAX_ORD; ++m) {
+      if (m >= c.nord[j]) break;
+      const int k = c.ord_k[j][m];
+      const R yk = pick_species<MAX_SP, R>(Y, k);
+      if (yk > R(0)) {
+        rho_physb += qq * c.ord_n[j][m] / rho_phys;
+        const R d = qq * c.ord_n[j][m] / yk;
 #pragma unroll
-      for (int m = 0; m < MAX_ORD; ++m) {
-        if (m >= c.nord[j]) break;
-        const int k = c.ord_k[j][m];
-        const R yk = sh_Y[k][tx];
-        if (yk > R(0)) {
-          rho_physb += qq * c.ord_n[j][m] / rho_phys;
-          sh_add[k][tx] += qq * c.ord_n[j][m] / yk;
-        }
+        for (int kk = 0; kk < MAX_SP; ++kk)
+          if (kk == k) add[kk] += d;
       }
     }
-    // adjoint of rho^n: from the LB step (staged above) and this update
-    R rhob = sh_rhob[tx];
-    rhob += rho_physb / c.inv_rho_ref;
-    rhob -= tot[PA_INVRHO] * inv_rho * inv_rho;
-    Wb += rhob * fdr / Tr;
-    Trb -= rhob * rho / Tr;
-    const R sWb = -Wb * W * W;
-    for (int k = 0; k < K; ++k) sh_add[k][tx] += sWb * c.inv_W[k];
-    // face coefficients FM = F (mu_r + mu_n) / 2, mu = nu (T / T_ref)^mu_exp
-    R murb = R(0);
-#pragma unroll
-    for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-        const R munb = R(0.5) * F * tot[PA_FM + 2 * ax + sd];
-        murb += munb;
-        const R dmu = munb * c.mu_exp * mun[ax][sd] / Tn[ax][sd];
-        const int kk = S.k1[ax][sd];
-        if (kk == NB_FLUID) pointb[slot1(ax, sd)] += dmu;
-        else if (kk != NB_INLET) Trb += dmu;
-      }
-    Trb += murb * c.mu_exp * mur / Tr;
-    pointb[0] += Trb;
-    A.u_bar[r] = tot[PA_UR];
-    A.u_bar[N + r] = tot[PA_UR + 1];
   }
-  __syncthreads();
-  if (!act) return;
-  if (fi > 0) pointb[0] += sh_add[fi - 1][tx];
-  const size_t fs = (size_t)(K + 1) * N;  // stride between slots
-  R* out = A.slots + (size_t)fi * N + r;
+  // adjoint of rho^n: from the LB step and this update
+  R rhob = rhob_lb;
+  rhob += rho_physb / c.inv_rho_ref;
+  rhob -= tot[PA_INVRHO] * inv_rho * inv_rho;
+  Wb += rhob * fdr / Tr;
+  Trb -= rhob * rho / Tr;
+  const R sWb = -Wb * W * W;
+  // face coefficients FM = F (mu_r + mu_n) / 2, mu = nu (T / T_ref)^mu_exp
+  R murb = R(0);
 #pragma unroll
-  for (int p = 0; p < 9; ++p) out[(size_t)p * fs] = pointb[p];
+  for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      const R munb = R(0.5) * F * tot[PA_FM + 2 * ax + sd];
+      murb += munb;
+      const R dmu = munb * c.mu_exp * mun[ax][sd] / Tn[ax][sd];
+      const int kk = S.k1[ax][sd];
+      if (kk == NB_FLUID) pT[slot1(ax, sd)] += dmu;
+      else if (kk != NB_INLET) Trb += dmu;
+    }
+  Trb += murb * c.mu_exp * mur / Tr;
+  // center slots (T: with the LB step's adjoint of T^n), the slots of T, the velocity adjoint
+  A.slots[r] = (c0[0] + Trb) + A.T_lb[r];
+  {
+    R* out = A.slots + r;
+#pragma unroll
+    for (int p = 1; p < 9; ++p) out[(size_t)p * fs] = pT[p];
+  }
+#pragma unroll
+  for (int f = 1; f < NF; ++f)
+    if (f <= K) A.slots[(size_t)f * N + r] = c0[f] + (add[f - 1] + sWb * c.inv_W[f - 1]);
+  A.u_out[r] = tot[PA_UR] + A.u_lb[r];
+  A.u_out[N + r] = tot[PA_UR + 1] + A.u_lb[N + r];
 }
 
-// Sum of the slot adjoints for every (cell, field): the cell's own center slot plus the
-// distance-1 and distance-2 slots of the cells whose stencil points land on it. Same thread
-// layout as fd_adjoint_kernel; the field-0 thread of each cell finds those cells once.
+// Adjoint of T and Y_k from the slot form, for every cell (0 on solid cells): where a reverse
+// sweep ends.
 template <typename R>
-__global__ void __launch_bounds__(FDA_THREADS)
+__global__ void __launch_bounds__(FDA_BLOCK)
     fd_adjoint_gather(Geo g, const uint32_t* __restrict__ sword, int K, const R* __restrict__ slots,
-                      const R* __restrict__ T_lb, const R* __restrict__ u_fd, const R* __restrict__ u_lb,
-                      R* __restrict__ Tbar, R* __restrict__ Ybar, R* __restrict__ ubar) {
-  __shared__ int src[8][FDA_CELLS];  // cell whose (axis, side, distance) point is s, or -1
-  const int tx = threadIdx.x, fi = threadIdx.y;
-  const int s = blockIdx.x * FDA_CELLS + tx;
+                      R* __restrict__ Tbar, R* __restrict__ Ybar) {
+  const int s = blockIdx.x * FDA_BLOCK + threadIdx.x;
   const int N = g.N;
-  const bool inside = s < N;
-  const bool fluid = inside && (__ldg(sword + s) >> 31);
-  if (fi == 0 && fluid) {
-    const int x = s % g.nx, y = s / g.nx;
-    const int pos[2] = {x, y}, dims[2] = {g.nx, g.ny}, strides[2] = {1, g.nx};
-#pragma unroll
-    for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-        const int sg = sd ? 1 : -1;
-        const bool per = g.bc_lo[ax] == BC_PERIODIC;
-#pragma unroll
-        for (int dist = 1; dist <= 2; ++dist) {
-          int qd = pos[ax] - dist * sg;
-          bool ok = true;
-          if (qd < 0 || qd >= dims[ax]) {
-            if (per) qd = ((qd % dims[ax]) + dims[ax]) % dims[ax];
-            else ok = false;
-          }
-          int rc = -1;
-          if (ok) {
-            // that cell's stencil point is s only when the point is a real (fluid) neighbour
-            const int cand = s + (qd - pos[ax]) * strides[ax];
-            const uint32_t w = __ldg(sword + cand);
-            if ((w >> 31) && ((w >> (4 * (2 * ax + sd) + 2 * (dist - 1))) & 3u) == 0u) rc = cand;
-          }
-          src[2 * (2 * ax + sd) + dist - 1][tx] = rc;
-        }
-      }
-  }
-  __syncthreads();
-  if (!inside || fi > K) return;
-  R* dst = fi == 0 ? Tbar + s : Ybar + (size_t)(fi - 1) * N + s;
-  if (!fluid) {
-    *dst = R(0);
-    if (fi == 0) {
-      ubar[s] = R(0);
-      ubar[N + s] = R(0);
-    }
+  if (s >= N) return;
+  if (!(__ldg(sword + s) >> 31)) {
+    Tbar[s] = R(0);
+    for (int k = 0; k < K; ++k) Ybar[(size_t)k * N + s] = R(0);
     return;
   }
+  int src[8];
+  slot_sources(g, sword, s, s % g.nx, s / g.nx, src);
   const size_t fs = (size_t)(K + 1) * N;
-  const R* sl = slots + (size_t)fi * N;
-  R v = sl[s];
-#pragma unroll
-  for (int t = 0; t < 8; ++t) {
-    const int rc = src[t][tx];
-    if (rc >= 0) v += sl[(size_t)(1 + t) * fs + rc];  // slot 1 + t: distance 1 + (t & 1), side t >> 1
-  }
-  if (fi == 0) {
-    *dst = v + T_lb[s];
-    ubar[s] = u_fd[s] + u_lb[s];
-    ubar[N + s] = u_fd[N + s] + u_lb[N + s];
-  } else {
-    *dst = v;
-  }
+  Tbar[s] = slot_sum<R>(slots, fs, s, src);
+  for (int k = 0; k < K; ++k) Ybar[(size_t)k * N + s] = slot_sum<R>(slots + (size_t)(k + 1) * N, fs, s, src);
 }
 
 }  // namespace hlbm

@@ -74,7 +74,7 @@ template <typename R> __device__ __forceinline__ void deq2(R ux, R uy, R* dq, R*
 }
 
 template <typename R, bool THERMAL>
-__global__ void __launch_bounds__(LB_BLOCK) lb_adjoint_kernel(const LBAdjArgs<R> A) {
+__global__ void __launch_bounds__(LB_BLOCK, sizeof(R) == 4 ? 4 : 1) lb_adjoint_kernel(const LBAdjArgs<R> A) {
   const LBArgs<R>& a = A.f;
   constexpr int Q = 9;
   const int nx = a.geo.nx, ny = a.geo.ny;

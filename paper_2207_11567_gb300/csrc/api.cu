@@ -1130,7 +1130,14 @@ template <typename R> lbm_status ensure_adj_ws(lbm_ctx* ctx, R** scratch, R** bu
   return LBM_OK;
 }
 
-template <typename R> AdjBuffers<R> adj_buffers(lbm_ctx* ctx, R* w, const R* in, R* out, void* grad_inlet) {
+// Slot array i (0 or 1) of the adjoint scratch: the slot form of the T and Y adjoints, written by
+// one reverse step and read by the next.
+template <typename R> R* adj_slots(lbm_ctx* ctx, R* w, int i) {
+  return w + (9 + (size_t)i * 9 * (ctx->K + 1)) * ctx->N;
+}
+
+template <typename R>
+AdjBuffers<R> adj_buffers(lbm_ctx* ctx, R* w, const R* in, R* out, void* grad_inlet, const R* slots_in, R* slots) {
   const size_t N = ctx->N;
   AdjBuffers<R> b{};
   b.in = in;
@@ -1139,11 +1146,22 @@ template <typename R> AdjBuffers<R> adj_buffers(lbm_ctx* ctx, R* w, const R* in,
   b.lam_bar = w; w += N;
   b.T_lb = w; w += N;
   b.u_lb = w; w += 2 * N;
-  b.rho_nb = w; w += 4 * N;
-  b.slots = w; w += 9 * (size_t)(ctx->K + 1) * N;
-  b.u_fd = w;
+  b.rho_nb = w;
+  b.slots_in = slots_in;
+  b.slots = slots;
   b.inlet_bar = (R*)grad_inlet;
   return b;
+}
+
+// End of a reverse sweep: the T and Y adjoints from the slot form (slot array sp, when sp >= 0)
+// into the adjoint buffer that holds the rest of it.
+template <typename R> lbm_status adj_finish(lbm_ctx* ctx, R* scratch, int sp, R* adj_buf) {
+  if (sp < 0) return LBM_OK;
+  const size_t N = ctx->N;
+  CK(launch_adjoint_gather<R>(ctx->geo, ctx->sword, ctx->K, adj_slots<R>(ctx, scratch, sp), adj_buf + 11 * N,
+                              adj_buf + 12 * N, ctx->st),
+     "adjoint gather");
+  return LBM_OK;
 }
 
 template <typename R> lbm_status adjoint_step_impl(lbm_ctx* ctx, const void* state_n, void* adj, void* grad_inlet) {
@@ -1154,9 +1172,11 @@ template <typename R> lbm_status adjoint_step_impl(lbm_ctx* ctx, const void* sta
   if ((st = lbm_load_state(ctx, state_n)) != LBM_OK) return st;
   const int cur = ctx->cur;
   if (th) CK(run_fd(ctx, cur, false), "forward FD for the adjoint");  // rho^n, Lambda^n
-  const AdjBuffers<R> b = adj_buffers<R>(ctx, scratch, (const R*)adj, buf, grad_inlet);
+  const AdjBuffers<R> b =
+      adj_buffers<R>(ctx, scratch, (const R*)adj, buf, grad_inlet, nullptr, adj_slots<R>(ctx, scratch, 0));
   CK(launch_adjoint_step2d<R>(b, make_lb_args<R>(ctx, cur, false), make_fd_args<R>(ctx, cur), th, ctx->st),
      "adjoint kernels");
+  if ((st = adj_finish<R>(ctx, scratch, th ? 0 : -1, buf)) != LBM_OK) return st;
   CK(cudaMemcpyAsync(adj, buf, state_words(ctx) * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
   return LBM_OK;
 }
@@ -1226,10 +1246,11 @@ lbm_status seg_recompute(lbm_ctx* ctx, const void* checkpoint, int n, R* ws, cud
 // Reverse of one recomputed segment on stream st: the adjoint step over the states n - 1 .. 0,
 // read in place, alternating between the two buffers pp[0], pp[1]; *which selects the one that
 // holds the incoming adjoint and, on return, the one that holds the adjoint of the segment's
-// first state.
+// first state. *sp: slot array holding the T and Y adjoints of the incoming state in slot form,
+// or -1 when they are in pp[*which]; on return, the slot array of the segment's first state.
 template <typename R>
 lbm_status seg_reverse(lbm_ctx* ctx, const void* checkpoint, int n, R* ws, R* scratch, R* const pp[2], int* which,
-                       void* grad_inlet, cudaStream_t st) {
+                       int* sp, void* grad_inlet, cudaStream_t st) {
   const size_t N = ctx->N;
   const bool th = ctx->cfg.thermal != 0;
   const size_t sw = state_words(ctx), slot_w = sw + (th ? 2 * N : 0);
@@ -1250,9 +1271,13 @@ lbm_status seg_reverse(lbm_ctx* ctx, const void* checkpoint, int n, R* ws, R* sc
       fdf.T = sk + 11 * N;
       fdf.Y = sk + 12 * N;
     }
-    const AdjBuffers<R> b = adj_buffers<R>(ctx, scratch, pp[*which], pp[1 - *which], grad_inlet);
+    const int so = *sp >= 0 ? 1 - *sp : 0;
+    const AdjBuffers<R> b = adj_buffers<R>(ctx, scratch, pp[*which], pp[1 - *which], grad_inlet,
+                                           *sp >= 0 ? adj_slots<R>(ctx, scratch, *sp) : nullptr,
+                                           adj_slots<R>(ctx, scratch, so));
     CK(launch_adjoint_step2d<R>(b, lbf, fdf, th, st), "adjoint kernels");
     *which ^= 1;
+    if (th) *sp = so;
   }
   return LBM_OK;
 }
@@ -1275,8 +1300,10 @@ lbm_status adjoint_segment_impl(lbm_ctx* ctx, const void* checkpoint, int n, voi
   if ((st = seg_recompute<R>(ctx, checkpoint, n, ws, ctx->st)) != LBM_OK) return st;
   CK(launch_zero_solid_pops<R>(ctx->geo, ctx->links, (R*)adj, ctx->st), "zero solid adjoint");
   R* const pp[2] = {(R*)adj, buf};
-  int which = 0;
-  if ((st = seg_reverse<R>(ctx, checkpoint, n, ws, scratch, pp, &which, grad_inlet, ctx->st)) != LBM_OK) return st;
+  int which = 0, sp = -1;
+  if ((st = seg_reverse<R>(ctx, checkpoint, n, ws, scratch, pp, &which, &sp, grad_inlet, ctx->st)) != LBM_OK)
+    return st;
+  if ((st = adj_finish<R>(ctx, scratch, sp, pp[which])) != LBM_OK) return st;
   if (which != 0)
     CK(cudaMemcpyAsync(adj, buf, sw * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
   return LBM_OK;
@@ -1312,7 +1339,7 @@ lbm_status adjoint_sweep_impl(lbm_ctx* ctx, const void* const* ckpt, int S, int 
   if ((st = seg_recompute<R>(ctx, ckpt[S - 1], len(S - 1), half[(S - 1) & 1], ctx->st2)) != LBM_OK) return st;
   CK(cudaEventRecord(rec[(S - 1) & 1], ctx->st2), "event");
   R* const pp[2] = {(R*)adj, buf};
-  int which = 0;
+  int which = 0, sp = -1;
   for (int s = S - 1; s >= 0; --s) {
     if (s >= 1) {
       // the half of segment s - 1 was last read by the reverse of segment s + 1
@@ -1321,11 +1348,12 @@ lbm_status adjoint_sweep_impl(lbm_ctx* ctx, const void* const* ckpt, int S, int 
       CK(cudaEventRecord(rec[(s - 1) & 1], ctx->st2), "event");
     }
     CK(cudaStreamWaitEvent(ctx->st, rec[s & 1], 0), "event wait");
-    if ((st = seg_reverse<R>(ctx, ckpt[s], len(s), half[s & 1], scratch, pp, &which, grad_inlet, ctx->st)) !=
+    if ((st = seg_reverse<R>(ctx, ckpt[s], len(s), half[s & 1], scratch, pp, &which, &sp, grad_inlet, ctx->st)) !=
         LBM_OK)
       return st;
     CK(cudaEventRecord(rev[s & 1], ctx->st), "event");
   }
+  if ((st = adj_finish<R>(ctx, scratch, sp, pp[which])) != LBM_OK) return st;
   if (which != 0)
     CK(cudaMemcpyAsync(adj, buf, sw * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
   return LBM_OK;

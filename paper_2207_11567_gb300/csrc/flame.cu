@@ -14,7 +14,7 @@
 //   delta_L = (T_max - T_min) / max |dT/dx| over the column means (centred differences);
 //   x_f     = first crossing of (T_min + T_max) / 2 by the column means from low x, linear in x;
 //   burnt state = column means of T and Y_k at the last column holding fluid.
-#include "adjoint_fd.cuh"
+#include "fd_kernel.cuh"
 #include "launch.h"
 
 namespace hlbm {
@@ -45,17 +45,23 @@ __global__ void __launch_bounds__(FL_BLOCK) flame_columns_kernel(FDArgs<R> a, in
     const int r = x + g.nx * j;
     if (!(__ldg(a.sword + r) >> 31)) continue;
     const R Tr = a.T[r];
-    R sW = R(0);
+    R sW = R(0), Yr[MAX_SP];
 #pragma unroll
-    for (int k = 0; k < MAX_SP; ++k)
+    for (int k = 0; k < MAX_SP; ++k) {
+      Yr[k] = R(0);
       if (k < c.K) {
-        const R Yk = a.Y[(size_t)k * N + r];
-        sW += Yk * c.inv_W[k];
-        acc[3 + k] += (double)Yk;
+        Yr[k] = a.Y[(size_t)k * N + r];
+        sW += Yr[k] * c.inv_W[k];
+        acc[3 + k] += (double)Yr[k];
       }
+    }
     const R rho_phys = fdr / (sW * Tr) / c.inv_rho_ref;  // P_th W / (R T)
+    R q[MAX_RX];
+#pragma unroll
+    for (int jr = 0; jr < MAX_RX; ++jr) q[jr] = R(0);
+    reaction_rates<0, R, MAX_SP>(c, Tr, Yr, rho_phys, q);
     R w = R(0);
-    for (int jr = 0; jr < c.nrx; ++jr) w += c.nu[jr][fuel] * rate_of<R>(c, jr, Tr, a.Y, N, r, rho_phys);
+    for (int jr = 0; jr < c.nrx; ++jr) w += c.nu[jr][fuel] * q[jr];
     const R Floc = c.sensor ? sensor_floc<R>(c, Tr, a.Y[(size_t)c.sensor_species * N + r],
                                              a.Y[(size_t)c.sensor_oxidizer * N + r])
                             : c.F;

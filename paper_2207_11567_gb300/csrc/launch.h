@@ -53,16 +53,25 @@ cudaError_t launch_pth_update(const PthUpdate& pu, const void* partials, int nbl
 constexpr int AUX_BLOCK = 256;
 
 // adjoint.cu: one adjoint step. in: adjoint of state n+1, out: adjoint of state n, both in the
-// lbm_save_state layout (g 9N, u 2N, T N, Y KN). Scratch arrays and the population part of out
-// must hold zeros on solid cells (they are never written there): zero them once at allocation.
+// lbm_save_state layout (g 9N, u 2N, T N, Y KN). In thermal runs the step leaves the T and Y parts
+// of state n in slot form in `slots` ([9][K+1][N], see adjoint_fd.cuh) and does not write them in
+// `out`; it reads those of state n+1 from slots_in, or from `in` where slots_in is null.
+// launch_adjoint_gather writes the fields from the slot form. Scratch arrays and the population
+// part of out must hold zeros on solid cells (they are never written there): zero them once at
+// allocation.
 template <typename R> struct AdjBuffers {
   const R* in; R* out;
-  R* rho_own; R* lam_bar; R* T_lb; R* u_lb; R* rho_nb; R* slots; R* u_fd;
+  R* rho_own; R* lam_bar; R* T_lb; R* u_lb; R* rho_nb;
+  const R* slots_in; R* slots;
   R* inlet_bar;
 };
+// rho_own, lam_bar, T_lb (N each), u_lb (2N), rho_nb (4N), two slot arrays (9 (K + 1) N each)
 template <typename R> constexpr size_t adj_scratch_words(size_t N, int K) {
-  return (1 + 1 + 1 + 2 + 4 + 9 * (size_t)(K + 1) + 2) * N;
+  return (1 + 1 + 1 + 2 + 4 + 2 * 9 * (size_t)(K + 1)) * N;
 }
+template <typename R>
+cudaError_t launch_adjoint_gather(const Geo& g, const uint32_t* sword, int K, const R* slots, R* Tbar, R* Ybar,
+                                  cudaStream_t st);
 template <typename R>
 cudaError_t launch_adjoint_step2d(const AdjBuffers<R>& b, const LBArgs<R>& lbf, const FDArgs<R>& fdf, bool thermal,
                                   cudaStream_t st);
