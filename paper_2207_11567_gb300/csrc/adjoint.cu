@@ -112,9 +112,25 @@ cudaError_t launch_initial_T_adjoint(const FDArgs<R>& fdf, const R* adj0, R* gra
   return cudaGetLastError();
 }
 
+// Launch with programmatic stream serialization when pdl is set (see pdl_wait in common.cuh).
+template <typename Arg>
+cudaError_t launch_ex(void (*kern)(Arg), dim3 grid, dim3 block, cudaStream_t st, bool pdl, const Arg& arg) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, arg);
+}
+
 template <typename R>
 cudaError_t launch_adjoint_step2d(const AdjBuffers<R>& b, const LBArgs<R>& lbf, const FDArgs<R>& fdf, bool thermal,
-                                  cudaStream_t st) {
+                                  bool pdl, cudaStream_t st) {
   const Geo& g = lbf.geo;
   const int N = g.N, K = thermal ? fdf.c.K : 0;
   LBAdjArgs<R> la{};
@@ -130,9 +146,8 @@ cudaError_t launch_adjoint_step2d(const AdjBuffers<R>& b, const LBArgs<R>& lbf, 
   la.rho_nb = b.rho_nb;
   la.inlet_bar = b.inlet_bar;
   const dim3 lgrid((g.nx + LB_BLOCK - 1) / LB_BLOCK, g.ny, 1);
-  if (thermal) lb_adjoint_kernel<R, true><<<lgrid, LB_BLOCK, 0, st>>>(la);
-  else lb_adjoint_kernel<R, false><<<lgrid, LB_BLOCK, 0, st>>>(la);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = thermal ? launch_ex<LBAdjArgs<R>>(lb_adjoint_kernel<R, true>, lgrid, dim3(LB_BLOCK), st, pdl, la)
+                          : launch_ex<LBAdjArgs<R>>(lb_adjoint_kernel<R, false>, lgrid, dim3(LB_BLOCK), st, false, la);
   if (e != cudaSuccess) return e;
   R* out_u = b.out + 9 * (size_t)N;
   if (!thermal) return cudaMemcpyAsync(out_u, b.u_lb, 2 * (size_t)N * sizeof(R), cudaMemcpyDeviceToDevice, st);
@@ -151,10 +166,9 @@ cudaError_t launch_adjoint_step2d(const AdjBuffers<R>& b, const LBArgs<R>& lbf, 
   fa.slots = b.slots;
   fa.u_out = out_u;
   const int fb = (N + FDA_BLOCK - 1) / FDA_BLOCK;
-  if (K == 6) fd_adjoint_kernel<R, 6><<<fb, FDA_BLOCK, 0, st>>>(fa);
-  else if (K == 4) fd_adjoint_kernel<R, 4><<<fb, FDA_BLOCK, 0, st>>>(fa);
-  else fd_adjoint_kernel<R, 0><<<fb, FDA_BLOCK, 0, st>>>(fa);
-  return cudaGetLastError();
+  // the LB adjoint of this step precedes it in the stream
+  void (*fk)(FDAdjArgs<R>) = K == 6 ? fd_adjoint_kernel<R, 6> : (K == 4 ? fd_adjoint_kernel<R, 4> : fd_adjoint_kernel<R, 0>);
+  return launch_ex<FDAdjArgs<R>>(fk, dim3(fb), dim3(FDA_BLOCK), st, true, fa);
 }
 
 namespace {
@@ -184,10 +198,10 @@ cudaError_t launch_fuel_objective(const FDArgs<R>& fdf, int fuel, R* Tbar, R* Yb
   return cudaGetLastError();
 }
 
-template cudaError_t launch_adjoint_step2d<float>(const AdjBuffers<float>&, const LBArgs<float>&, const FDArgs<float>&,
+template cudaError_t launch_adjoint_step2d<float>(const AdjBuffers<float>&, const LBArgs<float>&, const FDArgs<float>&, bool,
                                                   bool, cudaStream_t);
 template cudaError_t launch_adjoint_step2d<double>(const AdjBuffers<double>&, const LBArgs<double>&,
-                                                   const FDArgs<double>&, bool, cudaStream_t);
+                                                   const FDArgs<double>&, bool, bool, cudaStream_t);
 template cudaError_t launch_adjoint_gather<float>(const Geo&, const uint32_t*, int, const float*, float*, float*,
                                                   cudaStream_t);
 template cudaError_t launch_adjoint_gather<double>(const Geo&, const uint32_t*, int, const double*, double*, double*,

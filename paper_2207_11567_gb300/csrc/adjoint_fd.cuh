@@ -141,6 +141,8 @@ __global__ void __launch_bounds__(FDA_BLOCK, sizeof(R) == 4 ? 7 : 1) fd_adjoint_
   if (r >= N) return;
   const uint32_t sw = __ldg(a.sword + r);
   if (!(sw >> 31)) {
+    pdl_wait();
+    pdl_trigger();
     A.u_out[r] = R(0);
     A.u_out[N + r] = R(0);
     return;
@@ -163,21 +165,6 @@ __global__ void __launch_bounds__(FDA_BLOCK, sizeof(R) == 4 ? 7 : 1) fd_adjoint_
     for (int f = 0; f < NF; ++f)
       if (f <= K) ob[f] = slot_sum<R>(A.slots_in + (size_t)f * N, fs, r, src);
   }
-  // adjoint of rho^n from the LB step: own part and the density-gradient parts of the cells that
-  // hold this cell as their -x / +x / -y / +y neighbour (zero where that cell is solid or mirrored)
-  R rhob_lb = A.rho_own[r];
-  {
-    const int xm = x > 0 ? r - 1 : (g.bc_lo[0] == BC_PERIODIC ? r + g.nx - 1 : -1);
-    const int xp = x < g.nx - 1 ? r + 1 : (g.bc_hi[0] == BC_PERIODIC ? r - g.nx + 1 : -1);
-    const int ym = y > 0 ? r - g.nx : (g.bc_lo[1] == BC_PERIODIC ? r + (g.ny - 1) * g.nx : -1);
-    const int yp = y < g.ny - 1 ? r + g.nx : (g.bc_hi[1] == BC_PERIODIC ? r - (g.ny - 1) * g.nx : -1);
-    if (xm >= 0) rhob_lb += A.rho_nb[xm];
-    if (xp >= 0) rhob_lb += A.rho_nb[N + xp];
-    if (ym >= 0) rhob_lb += A.rho_nb[2 * N + ym];
-    if (yp >= 0) rhob_lb += A.rho_nb[3 * N + yp];
-  }
-  const R lamb = A.lam_bar[r];
-
   // ------------------------------------------------------------ forward: shared quantities
   const R F = c.F;
   const R fdr = sizeof(R) == 4 ? (R)a.pth->fd_rho : (R)a.pth->fd_rho_d;
@@ -220,6 +207,25 @@ __global__ void __launch_bounds__(FDA_BLOCK, sizeof(R) == 4 ? 7 : 1) fd_adjoint_
   for (int j = 0; j < MAX_RX; ++j) qdot += c.heat[j] * q[j];
   const R inv_rpF = R(1) / (rho_phys * F);
   const R dt = c.dt_phys;
+
+  // the LB adjoint of this step (the predecessor kernel) has completed: its outputs and every
+  // write of this kernel after this point
+  pdl_wait();
+  pdl_trigger();
+  // adjoint of rho^n from the LB step: own part and the density-gradient parts of the cells that
+  // hold this cell as their -x / +x / -y / +y neighbour (zero where that cell is solid or mirrored)
+  R rhob_lb = A.rho_own[r];
+  {
+    const int xm = x > 0 ? r - 1 : (g.bc_lo[0] == BC_PERIODIC ? r + g.nx - 1 : -1);
+    const int xp = x < g.nx - 1 ? r + 1 : (g.bc_hi[0] == BC_PERIODIC ? r - g.nx + 1 : -1);
+    const int ym = y > 0 ? r - g.nx : (g.bc_lo[1] == BC_PERIODIC ? r + (g.ny - 1) * g.nx : -1);
+    const int yp = y < g.ny - 1 ? r + g.nx : (g.bc_hi[1] == BC_PERIODIC ? r - (g.ny - 1) * g.nx : -1);
+    if (xm >= 0) rhob_lb += A.rho_nb[xm];
+    if (xp >= 0) rhob_lb += A.rho_nb[N + xp];
+    if (ym >= 0) rhob_lb += A.rho_nb[2 * N + ym];
+    if (yp >= 0) rhob_lb += A.rho_nb[3 * N + yp];
+  }
+  const R lamb = A.lam_bar[r];
 
   // ------------------------------------------------------------- field after field
   R tot[PA_N];

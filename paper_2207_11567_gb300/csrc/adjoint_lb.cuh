@@ -211,6 +211,10 @@ __global__ void __launch_bounds__(LB_BLOCK, sizeof(R) == 4 ? 4 : 1) lb_adjoint_k
   for (int j = 0; j < 3; ++j) bwd3(t2[3 * j], t2[3 * j + 1], t2[3 * j + 2], ux, xs[3 * j], xs[3 * j + 1], xs[3 * j + 2]);
 
   // ---------------------------------------------------------------- reverse
+  // the adjoint of state n + 1 and every output: after the predecessor kernel (the FD adjoint of
+  // the step after this one) has completed
+  pdl_wait();
+  pdl_trigger();
   R rhob = R(0), Sb = R(0), uxb = A.ubar_out[r], uyb = A.ubar_out[N + r];
   R xib[Q], xsb[Q];
 #pragma unroll

@@ -1174,7 +1174,7 @@ template <typename R> lbm_status adjoint_step_impl(lbm_ctx* ctx, const void* sta
   if (th) CK(run_fd(ctx, cur, false), "forward FD for the adjoint");  // rho^n, Lambda^n
   const AdjBuffers<R> b =
       adj_buffers<R>(ctx, scratch, (const R*)adj, buf, grad_inlet, nullptr, adj_slots<R>(ctx, scratch, 0));
-  CK(launch_adjoint_step2d<R>(b, make_lb_args<R>(ctx, cur, false), make_fd_args<R>(ctx, cur), th, ctx->st),
+  CK(launch_adjoint_step2d<R>(b, make_lb_args<R>(ctx, cur, false), make_fd_args<R>(ctx, cur), th, false, ctx->st),
      "adjoint kernels");
   if ((st = adj_finish<R>(ctx, scratch, th ? 0 : -1, buf)) != LBM_OK) return st;
   CK(cudaMemcpyAsync(adj, buf, state_words(ctx) * sizeof(R), cudaMemcpyDeviceToDevice, ctx->st), "copy adjoint");
@@ -1275,7 +1275,8 @@ lbm_status seg_reverse(lbm_ctx* ctx, const void* checkpoint, int n, R* ws, R* sc
     const AdjBuffers<R> b = adj_buffers<R>(ctx, scratch, pp[*which], pp[1 - *which], grad_inlet,
                                            *sp >= 0 ? adj_slots<R>(ctx, scratch, *sp) : nullptr,
                                            adj_slots<R>(ctx, scratch, so));
-    CK(launch_adjoint_step2d<R>(b, lbf, fdf, th, st), "adjoint kernels");
+    // within a segment, each LB adjoint follows the previous step's FD adjoint directly
+    CK(launch_adjoint_step2d<R>(b, lbf, fdf, th, th && k < n - 1, st), "adjoint kernels");
     *which ^= 1;
     if (th) *sp = so;
   }

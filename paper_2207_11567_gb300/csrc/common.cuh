@@ -121,6 +121,13 @@ template <> __device__ __forceinline__ void st_pop<__half, float>(__half* p, flo
   *reinterpret_cast<unsigned short*>(p) = __half_as_ushort(__float2half_rn(v));
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start before its predecessor in the stream has finished. pdl_wait blocks until that predecessor
+// has completed and its writes are visible (it returns at once without one); pdl_trigger lets the
+// next such kernel start. Kernels call pdl_trigger only after pdl_wait, so that when a kernel
+// starts, every kernel before its predecessor has completed.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 template <typename R> __device__ __forceinline__ R ldg(const R* p) { return __ldg(p); }
 
 // ---------------------------------------------------------------------------- fixed point

@@ -56,7 +56,9 @@ constexpr int AUX_BLOCK = 256;
 // lbm_save_state layout (g 9N, u 2N, T N, Y KN). In thermal runs the step leaves the T and Y parts
 // of state n in slot form in `slots` ([9][K+1][N], see adjoint_fd.cuh) and does not write them in
 // `out`; it reads those of state n+1 from slots_in, or from `in` where slots_in is null.
-// launch_adjoint_gather writes the fields from the slot form. Scratch arrays and the population
+// launch_adjoint_gather writes the fields from the slot form. pdl: the LB adjoint may start as the
+// previous step's FD adjoint ends (it must be the kernel just before it in the stream, with no
+// other dependency in between); the FD adjoint always does so after the LB adjoint. Scratch arrays and the population
 // part of out must hold zeros on solid cells (they are never written there): zero them once at
 // allocation.
 template <typename R> struct AdjBuffers {
@@ -74,7 +76,7 @@ cudaError_t launch_adjoint_gather(const Geo& g, const uint32_t* sword, int K, co
                                   cudaStream_t st);
 template <typename R>
 cudaError_t launch_adjoint_step2d(const AdjBuffers<R>& b, const LBArgs<R>& lbf, const FDArgs<R>& fdf, bool thermal,
-                                  cudaStream_t st);
+                                  bool pdl, cudaStream_t st);
 template <typename R> cudaError_t launch_zero_solid_pops(const Geo& g, const uint32_t* links, R* pops, cudaStream_t st);
 template <typename R>
 cudaError_t launch_initial_T_adjoint(const FDArgs<R>& fdf, const R* adj0, R* gradT, cudaStream_t st);
