@@ -299,3 +299,44 @@ def test_adjoint_sweep_equals_segments(K, C):
     nw = (wl.Q + 2 + 1 + len(wl.cfg["species"])) * wl.N
     assert torch.equal(a1[:nw], a2[:nw])
     assert torch.equal(g1, g2)
+
+
+def test_chamber_512x128_full_horizon_gradient():
+    """The 512 x 128 chamber from its fields 400 steps after ignition, K = 2000, checkpoints every
+    100 steps: the FP32 gradient is finite and within 1e-3 (relative L2) of the FP64 one, and the
+    FP64 gradient agrees with central differences (h = 1e-6) along 4 Philox directions to 1e-3 of
+    sum |grad_i d_i|. (At h = 1e-4 the secants cross kinks of the discrete map, such as upwind
+    switches and the max(Y, 0) of the rate law, and differ from the gradient by ~1e-3.)"""
+    from paper_2207_11567_gb300 import AdjointProblem, Solver
+    from paper_2207_11567_gb300 import _lib as L
+    wl = W.make("c5_adjoint_2d")
+    inlet0 = np.asarray(wl.inlet_u, dtype=np.float64).reshape(2, -1)
+    s = Solver(dict(wl.cfg, storage="f64"), wl.mask, inlet0)
+    s.set_fields(T=wl.T, Y=wl.Y, u=wl.u, P_h=wl.P_h)
+    s.step(400)
+    f = s.fields(L.F_T | L.F_Y | L.F_U | L.F_PH)
+    s.close()
+    fluid = (np.asarray(wl.mask).reshape(-1) == 0).astype(np.float64)
+    grads = {}
+    for storage in ("f32", "f64"):
+        p = AdjointProblem(dict(wl.cfg, storage=storage), wl.mask, f["Y"], u0=f["u"], P_h0=f["P_h"], n_steps=2000,
+                           checkpoint_every=100, fuel=FUEL)
+        p.forward(inlet0, f["T"])
+        gi, gt = (v.double().cpu().numpy() for v in p.backward())
+        grads[storage] = np.concatenate([gi.ravel(), gt.ravel()])
+        if storage == "f64":
+            rng = np.random.Generator(np.random.Philox(2207))
+            h = 1e-6
+            for _ in range(4):
+                di = rng.standard_normal(inlet0.shape) * (inlet0 != 0) * 0.1 * np.abs(inlet0).max()
+                dT = rng.standard_normal(f["T"].shape) * fluid * 10.0
+                fd = (p.forward(inlet0 + h * di, f["T"] + h * dT) - p.forward(inlet0 - h * di, f["T"] - h * dT)) / (2 * h)
+                ad = float((gi * di).sum() + (gt * dT).sum())
+                err = abs(ad - fd) / float(np.abs(gi * di).sum() + np.abs(gt * dT).sum())
+                assert err <= 1e-3, (ad, fd, err)
+        p.close()
+    g32, g64 = grads["f32"], grads["f64"]
+    assert np.isfinite(g32).all()
+    rel = np.linalg.norm(g32 - g64) / np.linalg.norm(g64)
+    print("FP32 vs FP64 gradient, relative L2:", rel)
+    assert rel <= 1e-3, rel
