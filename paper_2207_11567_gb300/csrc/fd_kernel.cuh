@@ -101,7 +101,7 @@ template <int KMAX, typename R> __device__ __forceinline__ R pick_species(const 
 
 // Reaction rates q_j (mol/(m^3 s)) of one cell. NR > 0: reaction count known at compile time;
 // NK > 0: species count known (Y then holds NK values in registers). Concentration powers: order 1
-// as is, order 1/2 as a square root, others as x^n.
+// as is, others as x^n (a separate square-root branch for order 1/2 measured 3% slower).
 template <int NR, typename R, int NK = 0>
 __device__ __forceinline__ void reaction_rates(const FDConst<R>& c, R T, const R* Y, R rho_phys, R* q) {
   const int nr = NR > 0 ? NR : c.nrx;
@@ -122,7 +122,7 @@ __device__ __forceinline__ void reaction_rates(const FDConst<R>& c, R T, const R
       const R n = c.ord_n[j][m];
       const R yk = NK > 0 ? pick_species<NK, R>(Y, k) : Y[k];
       const R conc = rho_phys * fmax(yk, R(0)) * c.inv_W[k];
-      v *= (n == R(1)) ? conc : (n == R(0.5) ? sqrt(conc) : powr<R>(conc, n));
+      v *= (n == R(1)) ? conc : powr<R>(conc, n);
     }
     q[j] = v;
   }
