@@ -364,17 +364,30 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
   const R rl3 = rho * lam * third;  // rho cs2 Lambda
 
   // ------------------------------ source xi_i = Xi_i / w_i (Eq. 2) and pre-conditioning (Eq. 13)
-  // s_i = q_i + xi_i / 2, S = sum w s; d_i = h_i / w_i - 1 = 3 (s_i - S) / rho
+  // s_i = q_i + xi_i / 2, S = sum w s; d_i = h_i / w_i - 1 = 3 (s_i - S) / rho.
+  // With full relaxation of orders 3..6 the collision reads the source only through the central
+  // moments of w xi of orders 0..2 (the higher ones are overwritten), which have closed forms on
+  // the product-weight lattices: with L = rho cs2 Lambda and G = u . grad rho,
+  //   k_0 = L + G/3, k_a = -u_a k_0, k_aa = L u_a^2 + L/3 + (G + 2 g_a u_a)/9,
+  //   k_ab = L u_a u_b + (g_a u_b + g_b u_a)/9 (a != b);
+  // they are added to the moments after the forward transform (SRC_MOM); otherwise the source is
+  // added per direction here.
+  constexpr bool SRC_MOM = THERMAL && COLL == COLL_CUMULANT_FULL;
   R Ssum = R(0);
+  R k0 = R(0);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    if constexpr (THERMAL) {
+    if constexpr (THERMAL && !SRC_MOM) {
       const R cu = (R)cx(i) * ux + (R)cy(i) * uy + ((D == 3) ? (R)cz(i) * uz : R(0));
       const R cg = (R)cx(i) * gx + (R)cy(i) * gy + ((D == 3) ? (R)cz(i) * gz : R(0));
       const R e = cu + R(1.5) * cu * cu - R(0.5) * usq;  // (f^eq/rho - w)/w * cs2
       q[i] += R(0.5) * (e * (cg - udg) + rl3);
     }
     Ssum += (R)wgt<D>(i) * q[i];
+  }
+  if constexpr (SRC_MOM) {
+    k0 = rl3 + third * udg;
+    Ssum += R(0.5) * k0;
   }
   const R three_over_rho = R(3) * inv_rho;
   // d_i = h_i / w_i - 1; the cumulant path works on w_i d_i (w_i folded into the factor)
@@ -405,6 +418,23 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
     if constexpr (D == 3) {
 #pragma unroll
       for (int j = 0; j < 9; ++j) chim_fwd(q[j], q[j + 9], q[j + 18], uz);
+    }
+    if constexpr (SRC_MOM) {
+      // (3 / rho) (1/2) times the moments k of w xi listed above, orders 0..2
+      const R h = R(1.5) * inv_rho, ninth = R(1) / R(9);
+      const R u3[3] = {ux, uy, uz}, g3[3] = {gx, gy, gz};
+      q[0] += h * k0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int ja = a == 0 ? 1 : (a == 1 ? 3 : 9);  // index of the first-order moment along a
+        q[ja] += h * (-u3[a] * k0);
+        q[2 * ja] += h * (rl3 * (u3[a] * u3[a] + third) + ninth * (udg + R(2) * g3[a] * u3[a]));
+#pragma unroll
+        for (int b = a + 1; b < D; ++b) {
+          const int jb = b == 1 ? 3 : 9;
+          q[ja + jb] += h * (rl3 * u3[a] * u3[b] + ninth * (g3[a] * u3[b] + g3[b] * u3[a]));
+        }
+      }
     }
     // full relaxation of orders 3..6 reads only the second-order moments, and orders 0 and 1
     // pass through unchanged: there the deviation is removed and restored for order 2 and
