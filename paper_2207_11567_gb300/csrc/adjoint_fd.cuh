@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(FDA_BLOCK, sizeof(R) == 4 ? 7 : 1) fd_adjoint_
   R q[MAX_RX], qdot = R(0);
 #pragma unroll
   for (int j = 0; j < MAX_RX; ++j) q[j] = R(0);
-  reaction_rates<0, R, MAX_SP>(c, Tr, Y, rho_phys, q);
+  reaction_rates<0, R, MAX_SP>(c, Tr, R(1) / Tr, Y, rho_phys, q);
 #pragma unroll
   for (int j = 0; j < MAX_RX; ++j) qdot += c.heat[j] * q[j];
   const R inv_rpF = R(1) / (rho_phys * F);

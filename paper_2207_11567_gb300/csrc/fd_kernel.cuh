@@ -52,9 +52,9 @@ __device__ __forceinline__ int nb_classify(const Geo& g, const uint8_t* __restri
 }
 
 // exp(-E / (R T)) with the exponent argument E/(R T) carried in float-float arithmetic
-// (error ~1e-13 relative before the final float rounding of the exponential).
-__device__ __forceinline__ float arrhenius(float ER_hi, float ER_lo, float T) {
-  const float r = 1.0f / T;
+// (error ~1e-13 relative before the final float rounding of the exponential). r: 1 / T, correctly
+// rounded (the caller's IEEE reciprocal, shared with its other uses).
+__device__ __forceinline__ float arrhenius(float ER_hi, float ER_lo, float T, float r) {
   const float e = fmaf(-T, r, 1.0f);  // exact residual of the reciprocal
   const float rlo = r * e;
   const float hi = ER_hi * r;
@@ -102,15 +102,16 @@ template <int KMAX, typename R> __device__ __forceinline__ R pick_species(const 
 // Reaction rates q_j (mol/(m^3 s)) of one cell. NR > 0: reaction count known at compile time;
 // NK > 0: species count known (Y then holds NK values in registers). Concentration powers: order 1
 // as is, others as x^n (a separate square-root branch for order 1/2 measured 3% slower).
+// inv_T: 1 / T, correctly rounded.
 template <int NR, typename R, int NK = 0>
-__device__ __forceinline__ void reaction_rates(const FDConst<R>& c, R T, const R* Y, R rho_phys, R* q) {
+__device__ __forceinline__ void reaction_rates(const FDConst<R>& c, R T, R inv_T, const R* Y, R rho_phys, R* q) {
   const int nr = NR > 0 ? NR : c.nrx;
 #pragma unroll
   for (int j = 0; j < (NR > 0 ? NR : MAX_RX); ++j) {
     if (NR == 0 && j >= nr) break;
     R v;
     if constexpr (sizeof(R) == 4) {
-      v = c.A[j] * arrhenius(c.ER_hi[j], c.ER_lo[j], T);
+      v = c.A[j] * arrhenius(c.ER_hi[j], c.ER_lo[j], T, inv_T);
     } else {
       v = c.A[j] * exp(-c.ER_hi[j] / T);
     }
@@ -264,7 +265,7 @@ __device__ __forceinline__ void fd_cell(const FDArgs<R>& a, int x, int y, int z,
     const R rho_phys = rho / c.inv_rho_ref;
     const R inv_rho = R(1) / rho;
     R q[RMAX];
-    reaction_rates<NR, R, NK>(c, Tr, Yr, rho_phys, q);
+    reaction_rates<NR, R, NK>(c, Tr, R(1) / Tr, Yr, rho_phys, q);
     const R Fr = a.Floc ? ldg(a.Floc + r) : c.F;
     const R mur = c.nu_lat * powr<R>(Tr * c.T_ref_inv, c.mu_exp);
     // variable heat capacities: mixture c_p and the heat of each reaction at T_r

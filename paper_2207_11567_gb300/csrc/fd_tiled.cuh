@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(TT_THREADS, 2)
       rho = fdr * W * inv_T;
       const float rho_phys = rho * c.rho_ref_f;
       inv_rho = 1.0f / rho;
-      reaction_rates<NR, float, NK>(c, Tr, Yr, rho_phys, q);
+      reaction_rates<NR, float, NK>(c, Tr, inv_T, Yr, rho_phys, q);
 #pragma unroll
       for (int j = 0; j < NR; ++j) qdot += c.heat[j] * q[j];
       inv_rpF = inv_rho * c.inv_rho_ref / Fr;

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(FL_BLOCK) flame_columns_kernel(FDArgs<R> a, in
     R q[MAX_RX];
 #pragma unroll
     for (int jr = 0; jr < MAX_RX; ++jr) q[jr] = R(0);
-    reaction_rates<0, R, MAX_SP>(c, Tr, Yr, rho_phys, q);
+    reaction_rates<0, R, MAX_SP>(c, Tr, R(1) / Tr, Yr, rho_phys, q);
     R w = R(0);
     for (int jr = 0; jr < c.nrx; ++jr) w += c.nu[jr][fuel] * q[jr];
     const R Floc = c.sensor ? sensor_floc<R>(c, Tr, a.Y[(size_t)c.sensor_species * N + r],
