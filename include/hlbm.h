@@ -331,7 +331,11 @@ lbm_status lbm_kernel_bytes(const lbm_ctx* ctx, double bytes[LBM_KERNEL_KINDS]);
  * shifted form); overwritten with the adjoint of state n. grad_inlet: device array [dim][ny] of
  * the field type to which the adjoint of the inlet-face velocity is added. The context's own
  * state is replaced by state_n (used to recompute the forward step). Upwind choices and the
- * max(Y, 0) of the rate law are held fixed (derivative 0 across their switches). */
+ * max(Y, 0) of the rate law are held fixed (derivative 0 across their switches). Workspace owned
+ * by the library, allocated at the first adjoint call: (9 + 18 (n_species + 1)) N values of the
+ * field type plus one state (per-cell adjoints of the LB step's rho, Lambda, T and u, and two
+ * arrays of stencil-point adjoints through which consecutive reverse steps pass the T and Y
+ * adjoints). */
 lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* state_n, void* adj, void* grad_inlet);
 
 /* Reverse sweep over one checkpoint segment (same support as lbm_adjoint_step): from the state
