@@ -31,10 +31,10 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-def _one_step(storage, smooth=True):
+def _one_step(storage, smooth=True, wl=None):
     from oracle.step import Oracle
     from paper_2207_11567_gb300 import from_workload
-    wl = _case(storage, smooth=smooth)
+    wl = _case(storage, smooth=smooth) if wl is None else wl
     dt = torch.float64 if storage == "f64" else torch.float32
     s = from_workload(wl)
     s.step(3)
@@ -52,6 +52,33 @@ def _one_step(storage, smooth=True):
     got["inlet"] = gin.double().cpu().numpy().reshape(2, -1)
     s.close()
     return {k: _rel(got[k], ref[k]) for k in ref}
+
+
+def _flame_case(storage, extra_species=False):
+    """Planar flame, 40 x 6, periodic in y (the slot sums wrap there), one-step chemistry with 4
+    species, or 5 with a trace of H2O taken from N2 (the field-count-generic adjoint kernel); a
+    seeded transverse velocity keeps the y-face velocities off zero."""
+    from workloads.configs import species
+    wl = W.generate.flame_2d(nx=40, ny=6, storage=storage, seed=3)
+    rng = np.random.default_rng(9)
+    wl.u[1] = 0.001 * rng.standard_normal(wl.N)
+    if extra_species:
+        tr = 1e-3
+        wl.cfg["species"] = list(wl.cfg["species"]) + species(["H2O"])
+        wl.Y = np.vstack([wl.Y, np.full((1, wl.N), tr)])
+        wl.Y[3] -= tr
+        y_in = list(wl.cfg["Y_in"]) + [tr]
+        y_in[3] -= tr
+        wl.cfg["Y_in"] = y_in
+    return wl
+
+
+@pytest.mark.parametrize("extra_species", [False, True])
+def test_one_step_adjoint_planar_flame_f64(extra_species):
+    wl = _flame_case("f64", extra_species)
+    assert len(wl.cfg["species"]) == (5 if extra_species else 4)
+    errs = _one_step("f64", wl=wl)
+    assert max(errs.values()) < 1e-10, errs
 
 
 def test_one_step_adjoint_f64():
@@ -249,12 +276,13 @@ def test_adjoint_rejects_unsupported_configs():
     s.close()
 
 
-@pytest.mark.parametrize("n", [3, 4])
-def test_adjoint_segment_equals_single_steps(n):
+@pytest.mark.parametrize("n,case", [(3, "chamber"), (4, "chamber"), (4, "flame")])
+def test_adjoint_segment_equals_single_steps(n, case):
     """lbm_adjoint_segment (recompute in the library, reverse over stored states, alternating
-    buffers) gives the same bits as n lbm_adjoint_step calls on saved states."""
+    buffers, the T and Y adjoints passed between steps in slot form) gives the same bits as n
+    lbm_adjoint_step calls on saved states."""
     from paper_2207_11567_gb300 import from_workload
-    wl = _case("f32")
+    wl = _case("f32") if case == "chamber" else _flame_case("f32")
     s = from_workload(wl)
     s.step(2)
     states = [s.save_state()]
