@@ -6,7 +6,8 @@
 // Per fluid cell the forward is recomputed from state n, then every operation is reversed in
 // the opposite order. Population adjoints go back to the unique place each pulled population
 // came from (a pull has exactly one consumer per stored population), so no atomics are needed.
-// Density-gradient adjoints are written per cell and gathered by the caller.
+// Density-gradient adjoints are written per cell and neighbour side; the FD adjoint of the same
+// step sums, for each cell, those of the cells that hold it as a neighbour.
 #pragma once
 #include "common.cuh"
 
