@@ -109,16 +109,19 @@ template <> __device__ __forceinline__ float ld_pop<float, float>(const float* p
 template <> __device__ __forceinline__ double ld_pop<double, double>(const double* p) { return __ldg(p); }
 
 // raw load of the stored value (no conversion) and its conversion, for two-phase streaming
+// Population loads and stores. The 2-byte (FP16) ones carry the streaming cache hint (each
+// population is read and written once per step): 1.4% faster FP16 stream-collide on C4, while
+// the same hint on the 4-byte populations made the FP32 one 7% slower.
 template <typename S> __device__ __forceinline__ S ld_raw(const S* p) { return __ldg(p); }
 template <> __device__ __forceinline__ __half ld_raw<__half>(const __half* p) {
-  return __ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p)));
+  return __ushort_as_half(__ldcs(reinterpret_cast<const unsigned short*>(p)));
 }
 template <typename S, typename R> __device__ __forceinline__ R cvt_pop(S v) { return (R)v; }
 template <> __device__ __forceinline__ float cvt_pop<__half, float>(__half v) { return __half2float(v); }
 
 template <typename S, typename R> __device__ __forceinline__ void st_pop(S* p, R v) { *p = (S)v; }
 template <> __device__ __forceinline__ void st_pop<__half, float>(__half* p, float v) {
-  *reinterpret_cast<unsigned short*>(p) = __half_as_ushort(__float2half_rn(v));
+  __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(__float2half_rn(v)));
 }
 
 // Programmatic dependent launch: a kernel launched with programmatic stream serialization may

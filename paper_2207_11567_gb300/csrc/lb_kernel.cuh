@@ -205,10 +205,11 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
   const S* __restrict__ gin = (const S*)a.g_in;
   const R third = R(1) / R(3);
 
-  R rho = R(1), lam = R(0);
+  R rho = R(1), lam = R(0), T_early = R(0);
   if constexpr (THERMAL) {
     rho = ldg(a.rho + r);
     lam = ldg(a.lam + r);
+    T_early = ldg(a.T + r);
     if constexpr (sizeof(R) == 8) lam += (R)a.pth->lb_lam_d;
     else lam += (R)a.pth->lb_lam;
   }
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
   // ---------------------------------------------------------------- relaxation time
   R tau0;
   if constexpr (THERMAL) {
-    const R Tr = ldg(a.T + r);
+    const R Tr = T_early;
     tau0 = R(3) * a.nu_lat * pw<R>(Tr * a.T_ref_inv, a.mu_exp) * inv_rho + R(0.5);
   } else {
     tau0 = R(3) * a.nu_lat + R(0.5);
