@@ -106,11 +106,11 @@ __global__ void __launch_bounds__(LB_BLOCK, sizeof(R) == 4 ? 4 : 1) lb_adjoint_k
     const int ci = cx(i), cj = cy(i);
     if ((lw >> i) & 1u) {
       src[i] = -1;
-      qin[i] = gin[(Q - 1 - i) * N + r];
+      qin[i] = ld_raw<R>(gin + (Q - 1 - i) * N + r);
     } else {
       const int s = r + (ci == 1 ? oxm : (ci == -1 ? oxp : 0)) + (cj == 1 ? oym : (cj == -1 ? oyp : 0));
       src[i] = s;
-      qin[i] = gin[i * N + s];
+      qin[i] = ld_raw<R>(gin + i * N + s);
       if constexpr (THERMAL) {
         if (ci * ci + cj * cj == 1) {
           const R rs = a.rho[s];
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(LB_BLOCK, sizeof(R) == 4 ? 4 : 1) lb_adjoint_k
   R xib[Q], xsb[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const R ob_ = A.gbar_out[i * N + r];
+    const R ob_ = ld_raw<R>(A.gbar_out + i * N + r);
     const R dstar = xs[i] / (R)wgt<2>(i);
     rhob += third * dstar * ob_;
     Sb += ob_;

@@ -109,11 +109,11 @@ template <> __device__ __forceinline__ float ld_pop<float, float>(const float* p
 template <> __device__ __forceinline__ double ld_pop<double, double>(const double* p) { return __ldg(p); }
 
 // raw load of the stored value (no conversion) and its conversion, for two-phase streaming
-// Population loads and stores. The 2-byte (FP16) ones carry the streaming cache hint (each
-// population is read and written once per step): 1.4% faster FP16 stream-collide on C4, while
-// the same hint on the 4-byte populations made the FP32 one 7% slower. The 4-byte loads ask L2
-// for 256-byte prefetches (0.9% faster on C4; not allocating them in L1 made it 5% slower: the
-// x-shifted pulls of neighbouring warps share lines there).
+// Population loads and stores (C4 stream-collide, A/B in one call each). Loads ask L2 for
+// 256-byte prefetches: FP32 0.703 -> 0.697 ms, FP16 0.719 -> 0.708 ms (against the streaming
+// hint); not allocating the FP32 loads in L1 made the kernel 5% slower (the x-shifted pulls of
+// neighbouring warps share lines there), and the streaming hint on FP32 loads and stores 7%
+// slower. The 2-byte stores keep the streaming hint (each population is written once per step).
 template <typename S> __device__ __forceinline__ S ld_raw(const S* p) { return __ldg(p); }
 template <> __device__ __forceinline__ float ld_raw<float>(const float* p) {
   float v;
@@ -121,7 +121,9 @@ template <> __device__ __forceinline__ float ld_raw<float>(const float* p) {
   return v;
 }
 template <> __device__ __forceinline__ __half ld_raw<__half>(const __half* p) {
-  return __ushort_as_half(__ldcs(reinterpret_cast<const unsigned short*>(p)));
+  unsigned short v;
+  asm("ld.global.nc.L2::256B.u16 %0, [%1];" : "=h"(v) : "l"(p));
+  return __ushort_as_half(v);
 }
 template <typename S, typename R> __device__ __forceinline__ R cvt_pop(S v) { return (R)v; }
 template <> __device__ __forceinline__ float cvt_pop<__half, float>(__half v) { return __half2float(v); }
