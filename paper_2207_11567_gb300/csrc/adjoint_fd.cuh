@@ -287,25 +287,33 @@ __global__ void __launch_bounds__(FDA_BLOCK, sizeof(R) == 4 ? 7 : 1) fd_adjoint_
       m1b += gi * FMf[ax][0];
       const bool up = uf[ax][1] >= R(0), um = uf[ax][0] >= R(0);
       const R dm2 = m1 - m2, dm1 = pr - m1, dp1 = p1 - pr, dp2 = p2 - p1;
-      const R fp = up ? weno_face<R>(pr, dm1, dp1, eps) : weno_face<R>(p1, -dp2, -dp1, eps);
-      const R fm = um ? weno_face<R>(m1, dm2, dm1, eps) : weno_face<R>(pr, -dp1, -dm1, eps);
+      // each face from its upwind side: the stencil differences picked by selects and one
+      // evaluation (one copy of the face code per field keeps the kernel in the instruction cache)
+      const R pa = up ? dm1 : -dp2, pb = up ? dp1 : -dp1;  // + face
+      const R ma = um ? dm2 : -dp1, mb = um ? dm1 : -dm1;  // - face
+      const R fp = weno_face<R>(up ? pr : p1, pa, pb, eps);
+      const R fm = weno_face<R>(um ? m1 : pr, ma, mb, eps);
       const R advb = -outb;
       tot[PA_UR + ax] += advb * (fp - fm);
       const R fpb = advb * ur[ax], fmb = -advb * ur[ax];
       R bb, dab, dbc;
-      if (up) {
-        weno_face_rev<R>(dm1, dp1, eps, fpb, bb, dab, dbc);
-        prb += bb + dab - dbc; m1b -= dab; p1b += dbc;
-      } else {
-        weno_face_rev<R>(-dp2, -dp1, eps, fpb, bb, dab, dbc);
-        p1b += bb + dab - dbc; p2b -= dab; prb += dbc;
+      weno_face_rev<R>(pa, pb, eps, fpb, bb, dab, dbc);
+      {
+        // up: base pr, differences (m1 -> pr, pr -> p1); else base p1, (p2 -> p1, p1 -> pr)
+        const R t = bb + dab - dbc;
+        prb += up ? t : dbc;
+        m1b -= up ? dab : R(0);
+        p1b += up ? dbc : t;
+        p2b -= up ? R(0) : dab;
       }
-      if (um) {
-        weno_face_rev<R>(dm2, dm1, eps, fmb, bb, dab, dbc);
-        m1b += bb + dab - dbc; m2b -= dab; prb += dbc;
-      } else {
-        weno_face_rev<R>(-dp1, -dm1, eps, fmb, bb, dab, dbc);
-        prb += bb + dab - dbc; p1b -= dab; m1b += dbc;
+      weno_face_rev<R>(ma, mb, eps, fmb, bb, dab, dbc);
+      {
+        // um: base m1, differences (m2 -> m1, m1 -> pr); else base pr, (p1 -> pr, pr -> m1)
+        const R t = bb + dab - dbc;
+        m1b += um ? t : dbc;
+        m2b -= um ? dab : R(0);
+        prb += um ? dbc : t;
+        p1b -= um ? R(0) : dab;
       }
       pointb[0] += prb;
       // distance-1 points: a fluid neighbour's slot, the cell itself (zero-gradient ghost) or
