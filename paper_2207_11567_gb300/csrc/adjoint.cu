@@ -112,22 +112,6 @@ cudaError_t launch_initial_T_adjoint(const FDArgs<R>& fdf, const R* adj0, R* gra
   return cudaGetLastError();
 }
 
-// Launch with programmatic stream serialization when pdl is set (see pdl_wait in common.cuh).
-template <typename Arg>
-cudaError_t launch_ex(void (*kern)(Arg), dim3 grid, dim3 block, cudaStream_t st, bool pdl, const Arg& arg) {
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kern, arg);
-}
-
 template <typename R>
 cudaError_t launch_adjoint_step2d(const AdjBuffers<R>& b, const LBArgs<R>& lbf, const FDArgs<R>& fdf, bool thermal,
                                   bool pdl, cudaStream_t st) {

@@ -342,14 +342,19 @@ cudaError_t run_lb(lbm_ctx* c, int cur, bool want_out) {
   const bool hi1 = c->cfg.omega_hi[0] == 1.0 && c->cfg.omega_hi[1] == 1.0 && c->cfg.omega_hi[2] == 1.0 &&
                    c->cfg.omega_hi[3] == 1.0;
   const int co = c->cfg.collision == LBM_COLL_CUMULANT ? (hi1 ? COLL_CUMULANT_FULL : COLL_CUMULANT) : COLL_BGK;
+  // in a closed domain the step launches the thermodynamic-pressure update just before: the
+  // stream-collide may start with it and waits for its state (programmatic dependent launch)
+  const bool pdl = th && c->cfg.closed_domain;
   if (c->f64) {
     auto a = make_lb_args<double>(c, cur, want_out);
-    return c->D == 2 ? launch_lb<2, double, double>(a, th, co, c->st) : launch_lb<3, double, double>(a, th, co, c->st);
+    return c->D == 2 ? launch_lb<2, double, double>(a, th, co, c->st, pdl)
+                     : launch_lb<3, double, double>(a, th, co, c->st, pdl);
   }
   auto a = make_lb_args<float>(c, cur, want_out);
   if (c->cfg.storage == LBM_STORE_F16)
-    return c->D == 2 ? launch_lb<2, __half, float>(a, th, co, c->st) : launch_lb<3, __half, float>(a, th, co, c->st);
-  return c->D == 2 ? launch_lb<2, float, float>(a, th, co, c->st) : launch_lb<3, float, float>(a, th, co, c->st);
+    return c->D == 2 ? launch_lb<2, __half, float>(a, th, co, c->st, pdl)
+                     : launch_lb<3, __half, float>(a, th, co, c->st, pdl);
+  return c->D == 2 ? launch_lb<2, float, float>(a, th, co, c->st, pdl) : launch_lb<3, float, float>(a, th, co, c->st, pdl);
 }
 
 // the tiled update applies (3-D FP32, constant heat capacity, grid and chemistry it supports)

@@ -251,6 +251,9 @@ __global__ void __launch_bounds__(PTH_THREADS) pth_update_kernel(PthUpdate pu, c
   __shared__ long long sI[PTH_THREADS], sM[PTH_THREADS];
   __shared__ double dI[PTH_THREADS], dM[PTH_THREADS];
   __shared__ bool last;
+  // the stream-collide that follows may start now: it reads the state this kernel writes only
+  // after its own pdl_wait
+  pdl_trigger();
   const int t = threadIdx.x, b = blockIdx.x, nb = gridDim.x;
   const int chunk = (nblocks + nb - 1) / nb;
   const int i0 = b * chunk, i1 = min(nblocks, i0 + chunk);

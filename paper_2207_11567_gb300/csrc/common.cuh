@@ -140,6 +140,22 @@ template <> __device__ __forceinline__ void st_pop<__half, float>(__half* p, flo
 // starts, every kernel before its predecessor has completed.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch with programmatic stream serialization when pdl is set (see pdl_wait).
+template <typename Arg>
+cudaError_t launch_ex(void (*kern)(Arg), dim3 grid, dim3 block, cudaStream_t st, bool pdl, const Arg& arg) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, arg);
+}
 template <typename R> __device__ __forceinline__ R ldg(const R* p) { return __ldg(p); }
 
 // ---------------------------------------------------------------------------- fixed point

@@ -8,7 +8,7 @@
 namespace hlbm {
 
 template <int D, typename S, typename R>
-cudaError_t launch_lb(const LBArgs<R>& a, int thermal, int coll, cudaStream_t st);
+cudaError_t launch_lb(const LBArgs<R>& a, int thermal, int coll, cudaStream_t st, bool pdl = false);
 template <int D, typename R>
 cudaError_t launch_fd(const FDArgs<R>& a, cudaStream_t st, bool sensor_pass);
 

@@ -210,8 +210,6 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
     rho = ldg(a.rho + r);
     lam = ldg(a.lam + r);
     T_early = ldg(a.T + r);
-    if constexpr (sizeof(R) == 8) lam += (R)a.pth->lb_lam_d;
-    else lam += (R)a.pth->lb_lam;
   }
   R rho_p[3] = {rho, rho, rho}, rho_m[3] = {rho, rho, rho};  // rho at r + e_a, r - e_a
 
@@ -273,6 +271,13 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
       }
     }
   }
+  }
+  // the thermodynamic-pressure state of this step: after the kernel that updates it (launched just
+  // before this one; the loads above read only what earlier kernels wrote)
+  pdl_wait();
+  if constexpr (THERMAL) {
+    if constexpr (sizeof(R) == 8) lam += (R)a.pth->lb_lam_d;
+    else lam += (R)a.pth->lb_lam;
   }
   R q[Q];
 #pragma unroll
@@ -531,12 +536,15 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
   if (!isfinite(usq)) atomicOr(a.flag, 1);
 }
 
+// pdl: the kernel may start while the one before it in the stream (the thermodynamic-pressure
+// update) runs; it reads that kernel's state after pdl_wait.
 template <int D, typename S, typename R>
-cudaError_t launch_lb(const LBArgs<R>& a, int thermal, int coll, cudaStream_t st) {
+cudaError_t launch_lb(const LBArgs<R>& a, int thermal, int coll, cudaStream_t st, bool pdl) {
   const dim3 grid((a.geo.nx + LB_BLOCK - 1) / LB_BLOCK, a.geo.ny, a.geo.nz);
 #define LB_LAUNCH(TH, CO)                                                                         \
   do {                                                                                            \
-    lb_step_kernel<D, S, R, TH, CO, false><<<grid, LB_BLOCK, 0, st>>>(a);                          \
+    cudaError_t e_ = launch_ex<LBArgs<R>>(lb_step_kernel<D, S, R, TH, CO, false>, grid, dim3(LB_BLOCK), st, pdl, a); \
+    if (e_ != cudaSuccess) return e_;                                                             \
     if (a.n_wall > 0)                                                                             \
       lb_step_kernel<D, S, R, TH, CO, true><<<(a.n_wall + LB_BLOCK - 1) / LB_BLOCK, LB_BLOCK, 0, st>>>(a); \
   } while (0)
