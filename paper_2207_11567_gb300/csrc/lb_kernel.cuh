@@ -198,19 +198,19 @@ __global__ void __launch_bounds__(LB_BLOCK, LB_MIN_BLOCKS) lb_step_kernel(const 
     if (x >= nx) return;
     r = x + nx * (y + ny * z);
   }
-  const uint32_t lw = __ldg(a.links + r);
-  if (!(lw >> 31)) return;
-  if (!WALLS && (lw & LINK_WALL)) return;  // done by the wall-list launch
-  const size_t N = (size_t)a.geo.N;
-  const S* __restrict__ gin = (const S*)a.g_in;
-  const R third = R(1) / R(3);
-
+  // the cell's rho, Lambda and T are loaded together with its link word (every cell has them)
   R rho = R(1), lam = R(0), T_early = R(0);
   if constexpr (THERMAL) {
     rho = ldg(a.rho + r);
     lam = ldg(a.lam + r);
     T_early = ldg(a.T + r);
   }
+  const uint32_t lw = __ldg(a.links + r);
+  if (!(lw >> 31)) return;
+  if (!WALLS && (lw & LINK_WALL)) return;  // done by the wall-list launch
+  const size_t N = (size_t)a.geo.N;
+  const S* __restrict__ gin = (const S*)a.g_in;
+  const R third = R(1) / R(3);
   R rho_p[3] = {rho, rho, rho}, rho_m[3] = {rho, rho, rho};  // rho at r + e_a, r - e_a
 
   // ---------------------------------------------------------------- pull streaming
