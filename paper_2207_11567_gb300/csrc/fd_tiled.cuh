@@ -50,8 +50,8 @@ template <int NK> struct TTLayout {
   static constexpr int RING = TT_SLOTS * NP * TT_PLANE;                 // words
   static constexpr int XF = RING;                                      // float2 [4][TT_Y][TT_X + 1]
   static constexpr int YF = XF + 4 * 2 * TT_Y * (TT_X + 1);            // float2 [4][TT_Y + 1][TT_X]
-  static constexpr int FM = YF + 4 * 2 * (TT_Y + 1) * TT_X;            // [TT_FY][TT_FX]
-  static constexpr int BAR = (FM + TT_FX * TT_FY + 1) & ~1;           // uint64 [TT_SLOTS]
+  static constexpr int FM = YF + 4 * 2 * (TT_Y + 1) * TT_X;            // [2][TT_FY][TT_FX]
+  static constexpr int BAR = (FM + 2 * TT_FX * TT_FY + 1) & ~1;       // uint64 [TT_SLOTS]
   static constexpr int RED = BAR + 2 * TT_SLOTS;                       // int64 [8][2]
   static constexpr int WORDS = RED + 2 * 2 * 8;
   static constexpr size_t BYTES = (size_t)WORDS * 4;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(TT_THREADS, 2)
   float* ring = sm;
   float2* XF = reinterpret_cast<float2*>(sm + L::XF);
   float2* YF = reinterpret_cast<float2*>(sm + L::YF);
-  float* FMs = sm + L::FM;
+  float* FMbuf = sm + L::FM;  // F mu tiles of planes z (z & 1) and z + 1
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::BAR);
   long long* red = reinterpret_cast<long long*>(sm + L::RED);
 
@@ -322,6 +322,37 @@ __global__ void __launch_bounds__(TT_THREADS, 2)
   const float dt = c.dt_phys;
   long long accI = 0, accM = 0;  // fixed-point P_th integrand and boundary mass flux of this thread
 
+  // inlet / outlet ghost values into the x halo of plane zp, held in slot sp (single viewer each)
+  auto ghosts = [&](int zp, float* sp) {
+    if (tid < 2 * TT_PY) {
+      const int row = tid % TT_PY, col = tid / TT_PY;  // col 0, 1: x = -1, -2 or x = nx, nx + 1
+      const int yy = y0 - TT_HY + row;
+      if (inlet_tile) {
+        const int pi = row * TT_PX + TT_HX - 1 - col;
+#pragma unroll
+        for (int f = 0; f <= NK; ++f) sp[(L::P_T + f) * TT_PLANE + pi] = f == 0 ? c.T_in : c.Y_in[f - 1];
+        sp[L::P_U * TT_PLANE + pi] = (yy >= 0 && yy < ny) ? __ldg(a.inlet_u + yy + ny * zp) : 0.0f;
+        if (sensor) sp[L::P_F * TT_PLANE + pi] = sp[L::P_F * TT_PLANE + row * TT_PX + TT_HX];
+      }
+      if (outlet_tile && xo + col < TT_PX) {
+        const int pi = row * TT_PX + xo + col, pl = row * TT_PX + xo - 1;
+#pragma unroll
+        for (int f = 0; f <= NK; ++f) sp[(L::P_T + f) * TT_PLANE + pi] = sp[(L::P_T + f) * TT_PLANE + pl];
+        sp[L::P_U * TT_PLANE + pi] = sp[L::P_U * TT_PLANE + pl];
+        if (sensor) sp[L::P_F * TT_PLANE + pi] = sp[L::P_F * TT_PLANE + pl];
+      }
+    }
+  };
+  // F mu(T) of the plane in slot sp on the tile and a halo of 1, into the tile buffer fm
+  auto fm_tile = [&](const float* sp, float* fm) {
+    for (int i = tid; i < TT_FX * TT_FY; i += TT_THREADS) {
+      const int px = i % TT_FX, py = i / TT_FX;
+      const int pi = (py + TT_HY - 1) * TT_PX + px + TT_HX - 1;
+      const float Fp = sensor ? sp[L::P_F * TT_PLANE + pi] : c.F;
+      fm[i] = Fp * (c.nu_lat * powr<float>(sp[L::P_T * TT_PLANE + pi] * c.T_ref_inv, c.mu_exp));
+    }
+  };
+
   // ---------------------------------------------------------------- prologue: the -z face of z0
   bool ok = wait(z0) && wait(z0 + 1);
   ok = __syncthreads_and(ok);
@@ -330,6 +361,12 @@ __global__ void __launch_bounds__(TT_THREADS, 2)
     for (int zp = z0; zp <= min(z0 + 2, zlast); ++zp) wait(zp);
     return;
   }
+  // ghosts and F mu tile of plane z0 (each step of the march prepares the plane above it)
+  if (inlet_tile || outlet_tile) {
+    ghosts(z0, slot(z0));
+    __syncthreads();
+  }
+  fm_tile(slot(z0), FMbuf + (z0 & 1) * TT_FX * TT_FY);
   float carF[NK + 1], carD[NK + 1], phim[NK + 1];  // -z face of the plane, phi at z - 1
   {
     const float* s0 = slot(z0);
@@ -367,37 +404,17 @@ __global__ void __launch_bounds__(TT_THREADS, 2)
   for (int z = z0; z < z1; ++z) {
     const bool okz = wait(z + 2);
     float* s0 = slot(z);
-    const float* s1 = slot(z + 1);
+    float* s1 = slot(z + 1);
     const float* s2 = slot(z + 2);
-    // inlet / outlet ghost values into the x halo of plane z (single viewer each)
-    if (inlet_tile || outlet_tile) {
-      if (tid < 2 * TT_PY) {
-        const int row = tid % TT_PY, col = tid / TT_PY;  // col 0, 1: x = -1, -2 or x = nx, nx + 1
-        const int yy = y0 - TT_HY + row;
-        if (inlet_tile) {
-          const int pi = row * TT_PX + TT_HX - 1 - col;
-#pragma unroll
-          for (int f = 0; f <= NK; ++f) s0[(L::P_T + f) * TT_PLANE + pi] = f == 0 ? c.T_in : c.Y_in[f - 1];
-          s0[L::P_U * TT_PLANE + pi] = (yy >= 0 && yy < ny) ? __ldg(a.inlet_u + yy + ny * z) : 0.0f;
-          if (sensor) s0[L::P_F * TT_PLANE + pi] = s0[L::P_F * TT_PLANE + row * TT_PX + TT_HX];
-        }
-        if (outlet_tile && xo + col < TT_PX) {
-          const int pi = row * TT_PX + xo + col, pl = row * TT_PX + xo - 1;
-#pragma unroll
-          for (int f = 0; f <= NK; ++f) s0[(L::P_T + f) * TT_PLANE + pi] = s0[(L::P_T + f) * TT_PLANE + pl];
-          s0[L::P_U * TT_PLANE + pi] = s0[L::P_U * TT_PLANE + pl];
-          if (sensor) s0[L::P_F * TT_PLANE + pi] = s0[L::P_F * TT_PLANE + pl];
-        }
-      }
+    const float* FMs = FMbuf + (z & 1) * TT_FX * TT_FY;      // plane z (prepared one step earlier)
+    float* FMn = FMbuf + ((z + 1) & 1) * TT_FX * TT_FY;      // plane z + 1
+    // ghosts and F mu tile of plane z + 1: its z face with plane z reads them now, plane z + 1
+    // itself in the next step
+    if ((inlet_tile || outlet_tile) && z + 1 < nz) {
+      ghosts(z + 1, s1);
       __syncthreads();
     }
-    // F mu(T) of plane z on the tile and a halo of 1
-    for (int i = tid; i < TT_FX * TT_FY; i += TT_THREADS) {
-      const int px = i % TT_FX, py = i / TT_FX;
-      const int pi = (py + TT_HY - 1) * TT_PX + px + TT_HX - 1;
-      const float Fp = sensor ? s0[L::P_F * TT_PLANE + pi] : c.F;
-      FMs[i] = Fp * (c.nu_lat * powr<float>(s0[L::P_T * TT_PLANE + pi] * c.T_ref_inv, c.mu_exp));
-    }
+    fm_tile(s1, FMn);
     // all threads leave together when a plane load did not arrive
     if (!__syncthreads_and(okz)) {
       if (tid == 0) atomicOr(a.flag, 4);
@@ -470,9 +487,7 @@ __global__ void __launch_bounds__(TT_THREADS, 2)
     float FMz;
     {
       const uint32_t swb = (z + 1 < nz) ? __float_as_uint(s1[L::P_S * TT_PLANE + own]) : 0u;
-      const float Tz = s1[L::P_T * TT_PLANE + own];
-      const float Fz = sensor ? s1[L::P_F * TT_PLANE + own] : c.F;
-      const float FMb = Fz * (c.nu_lat * powr<float>(Tz * c.T_ref_inv, c.mu_exp));
+      const float FMb = FMn[fo];
       const float FMa = FMs[fo];
       const float ub = s1[(L::P_U + 2) * TT_PLANE + own];
       float uown, un, FMown, FMn;
