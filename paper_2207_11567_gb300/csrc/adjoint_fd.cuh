@@ -90,29 +90,26 @@ __device__ __forceinline__ void fd_stencil2(const Geo& g, uint32_t sw, int r, in
 
 // Cells whose stencil point (axis, side, distance) is the fluid cell s: src[2 (2 ax + sd) + dist - 1]
 // is that cell, or -1 where it is not fluid or its point there is a ghost. Its slot 1 + t holds the
-// adjoint of s read through that point.
-__device__ __forceinline__ void slot_sources(const Geo& g, const uint32_t* __restrict__ sword, int s, int x, int y,
-                                             int src[8]) {
+// adjoint of s read through that point. The stencil kinds are symmetric (a point is a real fluid
+// point when both cells are fluid and inside the domain or across a periodic face), so s's own
+// word tells: the cell at distance 1 (2) on the opposite side has s as its point exactly when s's
+// distance-1 point (distance-1 and distance-2 points) on that side are real.
+__device__ __forceinline__ void slot_sources(const Geo& g, uint32_t sw, int s, int x, int y, int src[8]) {
   const int pos[2] = {x, y}, dims[2] = {g.nx, g.ny}, strides[2] = {1, g.nx};
 #pragma unroll
   for (int ax = 0; ax < 2; ++ax)
 #pragma unroll
     for (int sd = 0; sd < 2; ++sd) {
       const int sg = sd ? 1 : -1;
-      const bool per = g.bc_lo[ax] == BC_PERIODIC;
+      const uint32_t opp = (sw >> (4 * (2 * ax + (1 - sd)))) & 15u;  // s's kinds toward -sg
 #pragma unroll
       for (int dist = 1; dist <= 2; ++dist) {
-        int qd = pos[ax] - dist * sg;
-        bool ok = true;
-        if (qd < 0 || qd >= dims[ax]) {
-          if (per) qd = ((qd % dims[ax]) + dims[ax]) % dims[ax];
-          else ok = false;
-        }
+        const bool real = dist == 1 ? (opp & 3u) == 0u : opp == 0u;
         int rc = -1;
-        if (ok) {
-          const int cand = s + (qd - pos[ax]) * strides[ax];
-          const uint32_t w = __ldg(sword + cand);
-          if ((w >> 31) && ((w >> (4 * (2 * ax + sd) + 2 * (dist - 1))) & 3u) == 0u) rc = cand;
+        if (real) {
+          int qd = pos[ax] - dist * sg;
+          if (qd < 0 || qd >= dims[ax]) qd = ((qd % dims[ax]) + dims[ax]) % dims[ax];  // periodic
+          rc = s + (qd - pos[ax]) * strides[ax];
         }
         src[2 * (2 * ax + sd) + dist - 1] = rc;
       }
@@ -160,7 +157,7 @@ __global__ void __launch_bounds__(FDA_BLOCK, sizeof(R) == 4 ? 7 : 1) fd_adjoint_
       if (f <= K) ob[f] = f == 0 ? A.Tbar_out[r] : A.Ybar_out[(size_t)(f - 1) * N + r];
   } else {
     int src[8];
-    slot_sources(g, a.sword, r, x, y, src);
+    slot_sources(g, sw, r, x, y, src);
 #pragma unroll
     for (int f = 0; f < NF; ++f)
       if (f <= K) ob[f] = slot_sum<R>(A.slots_in + (size_t)f * N, fs, r, src);
@@ -417,13 +414,14 @@ __global__ void __launch_bounds__(FDA_BLOCK)
   const int s = blockIdx.x * FDA_BLOCK + threadIdx.x;
   const int N = g.N;
   if (s >= N) return;
-  if (!(__ldg(sword + s) >> 31)) {
+  const uint32_t sw = __ldg(sword + s);
+  if (!(sw >> 31)) {
     Tbar[s] = R(0);
     for (int k = 0; k < K; ++k) Ybar[(size_t)k * N + s] = R(0);
     return;
   }
   int src[8];
-  slot_sources(g, sword, s, s % g.nx, s / g.nx, src);
+  slot_sources(g, sw, s, s % g.nx, s / g.nx, src);
   const size_t fs = (size_t)(K + 1) * N;
   Tbar[s] = slot_sum<R>(slots, fs, s, src);
   for (int k = 0; k < K; ++k) Ybar[(size_t)k * N + s] = slot_sum<R>(slots + (size_t)(k + 1) * N, fs, s, src);
