@@ -73,9 +73,11 @@ cudaError_t fd_tiled_setup(FDTiledMaps& m, const Geo& g, int K, void* const T[2]
   ok = ok && make_map(&m.U, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, u, g, 3);
   ok = ok && make_map(&m.S, CU_TENSOR_MAP_DATA_TYPE_UINT32, sword, g, 1);
   if (!ok) return cudaErrorInvalidValue;
-  // z chunks: about six resident waves of two blocks per SM, at least 8 planes per chunk
+  // z chunks: about eleven waves of two resident blocks per SM (the last, partial wave then costs
+  // little; on the 384x192x192 case 12 chunks of 16 planes ran 0.4% faster than 7 of 28, 4 chunks
+  // 2% slower), at least 8 planes per chunk
   const int gx = (g.nx + TT_X - 1) / TT_X, gy = (g.ny + TT_Y - 1) / TT_Y;
-  int nzc = (6 * 2 * n_sm + gx * gy - 1) / (gx * gy);
+  int nzc = (11 * 2 * n_sm + gx * gy - 1) / (gx * gy);
   nzc = std::max(1, std::min(nzc, g.nz / 8));
   if (const char* s = std::getenv("HLBM_FD_CHUNKS")) nzc = std::max(1, std::min(atoi(s), g.nz));
   m.lz = (g.nz + nzc - 1) / nzc;
