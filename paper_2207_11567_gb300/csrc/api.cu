@@ -55,6 +55,8 @@ struct lbm_ctx {
   FDTiledMaps* tiled = nullptr;  // tiled FD update (3-D FP32), nullptr where it does not apply
   int nblocks_tiled = 0;         // partial slots written by the tiled update
   size_t n_fd_wall_rows = 0;     // cells with ghost-point wall weights (fd_step_kernel, walls only)
+  int* fd_wall_list = nullptr;   // those cells, ascending (the tiled update's walls-only launch)
+  size_t fd_wall_list_cap = 0;
   void* mix = nullptr;           // mixture-averaged diffusion: per-cell G_k and W [(K + 1)][N]
   int nblocks_init = 0;  // partial slots written by the initial-integral kernel
   PthState* pth = nullptr;
@@ -363,7 +365,7 @@ bool use_tiled(const lbm_ctx* c) { return c->tiled && !c->fdc_f.varcp && !c->fdc
 // partial slots of the P_th reduction written by one FD update
 int fd_slots(const lbm_ctx* c) {
   if (!use_tiled(c)) return c->nblocks_fd;
-  return c->nblocks_tiled + (c->n_fd_wall_rows ? c->nblocks_fd : 0);
+  return c->nblocks_tiled + (int)((c->n_fd_wall_rows + FD_BLOCK - 1) / FD_BLOCK);
 }
 
 cudaError_t run_fd(lbm_ctx* c, int cur, bool sensor_pass) {
@@ -375,8 +377,11 @@ cudaError_t run_fd(lbm_ctx* c, int cur, bool sensor_pass) {
   if (!sensor_pass && use_tiled(c)) {
     cudaError_t e = launch_fd_tiled(a, *c->tiled, cur, c->st);
     if (e != cudaSuccess || !c->n_fd_wall_rows) return e;
-    // cells with ghost-point wall weights: the general kernel, partial slots after the tiled ones
+    // cells with ghost-point wall weights: the general kernel over their list, partial slots after
+    // the tiled ones
     a.walls_only = 1;
+    a.wall_list = c->fd_wall_list;
+    a.n_wall_list = (int)c->n_fd_wall_rows;
     a.part_offset = c->nblocks_tiled;
     return launch_fd<3, float>(a, c->st, false);
   }
@@ -1452,8 +1457,20 @@ template <typename R> lbm_status set_fd_walls(lbm_ctx* ctx, const std::vector<in
       if (!(ctx->fd_w = dalloc(ctx, nr * W * sizeof(R)))) return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
       ctx->fd_rows_cap = nr;
     }
+    std::vector<int> list;
+    list.reserve(nr);
     for (size_t r = 0; r < N; ++r)
-      if (frow[r] >= 0) sw[r] |= SW_WALL;
+      if (frow[r] >= 0) {
+        sw[r] |= SW_WALL;
+        list.push_back((int)r);
+      }
+    if (list.size() > ctx->fd_wall_list_cap) {
+      if (!(ctx->fd_wall_list = (int*)dalloc(ctx, list.size() * sizeof(int))))
+        return fail(ctx, LBM_ERR_ALLOC, "allocation failed");
+      ctx->fd_wall_list_cap = list.size();
+    }
+    CK(cudaMemcpyAsync(ctx->fd_wall_list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st),
+       "copy wall list");
     CK(cudaMemcpyAsync(ctx->fd_row, frow.data(), N * sizeof(int), cudaMemcpyHostToDevice, ctx->st), "copy rows");
     CK(cudaMemcpyAsync(ctx->fd_w, w.data(), nr * W * sizeof(R), cudaMemcpyHostToDevice, ctx->st), "copy weights");
   }

@@ -245,6 +245,8 @@ template <typename R> struct FDArgs {
   int* flag;          // error bits: 4 = a plane load of the tiled update did not arrive in time
   const R* mix;       // mixture-averaged diffusion: per cell G_k [K][N] and W [N] (mix_coeff_kernel)
   int walls_only;     // fd_step_kernel: update only the cells flagged SW_WALL
+  const int* wall_list;  // with walls_only: the flagged cells (ascending), one thread each
+  int n_wall_list;
   int part_offset;    // fd_step_kernel: first partial slot it writes
   FDConst<R> c;
 };

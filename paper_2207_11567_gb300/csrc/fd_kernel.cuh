@@ -517,11 +517,23 @@ __global__ void __launch_bounds__(FD_BLOCK, sizeof(R) == 4 ? (VDEG > 0 ? HLBM_FD
     fd_step_kernel(const FDArgs<R> a) {
   const FDConst<R>& c = a.c;
   const Geo& g = a.geo;
-  const int x = blockIdx.x * FDShape<D>::X + threadIdx.x;
-  const int y = blockIdx.y * FDShape<D>::Y + threadIdx.y;
-  const int z = blockIdx.z * FDShape<D>::Z + threadIdx.z;
-  const bool inside = x < g.nx && y < g.ny && z < g.nz;
-  const int r = x + g.nx * (y + g.ny * z);
+  int x, y, z, r;
+  bool inside;
+  if (a.wall_list) {
+    // one thread per listed cell (a 1-D grid of blocks of the same shape)
+    const int wrow = blockIdx.x * FD_BLOCK + threadIdx.x + FDShape<D>::X * (threadIdx.y + FDShape<D>::Y * threadIdx.z);
+    inside = wrow < a.n_wall_list;
+    r = inside ? __ldg(a.wall_list + wrow) : 0;
+    x = r % g.nx;
+    y = (r / g.nx) % g.ny;
+    z = r / (g.nx * g.ny);
+  } else {
+    x = blockIdx.x * FDShape<D>::X + threadIdx.x;
+    y = blockIdx.y * FDShape<D>::Y + threadIdx.y;
+    z = blockIdx.z * FDShape<D>::Z + threadIdx.z;
+    inside = x < g.nx && y < g.ny && z < g.nz;
+    r = x + g.nx * (y + g.ny * z);
+  }
   const uint32_t sw = inside ? __ldg(a.sword + r) : 0u;
   // walls_only: the launch after the tiled update, for the cells with ghost-point wall weights
   const bool active = (sw >> 31) != 0u && (!a.walls_only || (sw & SW_WALL) != 0u);
@@ -607,7 +619,8 @@ cudaError_t launch_fd(const FDArgs<R>& a, cudaStream_t st, bool sensor_pass) {
     const int grid = (a.geo.N + FD_BLOCK - 1) / FD_BLOCK;
     flame_sensor_kernel<D, R><<<grid, FD_BLOCK, 0, st>>>(a);
   } else {
-    const dim3 grid = fd_grid<D>(a.geo), block(FDShape<D>::X, FDShape<D>::Y, FDShape<D>::Z);
+    const dim3 grid = a.wall_list ? dim3((a.n_wall_list + FD_BLOCK - 1) / FD_BLOCK) : fd_grid<D>(a.geo);
+    const dim3 block(FDShape<D>::X, FDShape<D>::Y, FDShape<D>::Z);
     if (a.c.K == 6 && a.c.nrx == 2) fd_step_kernel<D, R, 6, 2><<<grid, block, 0, st>>>(a);
     else if (a.c.K == 4 && a.c.nrx == 1) fd_step_kernel<D, R, 4, 1><<<grid, block, 0, st>>>(a);
     else fd_step_kernel<D, R, 0, 0><<<grid, block, 0, st>>>(a);
